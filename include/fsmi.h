@@ -1,0 +1,196 @@
+/*
+ * fsmi.h - C ABI of libfsmi: batched Shannon mutual information between an occupancy map and
+ * range beams, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Zhang, Henderson, Karaman, Sze, "FSMI: Fast computation of Shannon Mutual Information
+ * for information-theoretic mapping" (IJRR 2019). The six variants of Table 1:
+ *   FSMI (Theorem 1, Algorithm 1), Approx-FSMI (eq. fsmi_approx, Section 3.4),
+ *   Uniform-FSMI (Theorem 4, Algorithm 4), FSMI-RLE (Theorem 3, Algorithm 5),
+ *   Approx-FSMI-RLE (Theorem 5, Algorithm 6), Uniform-FSMI-RLE (Theorem 6).
+ *
+ * Conventions for every entry point:
+ *   - Units: one cell (2D) or one virtual cell / voxel (3D) is the unit of length (w = 1).
+ *   - Mutual information is returned in nats (natural logarithms), as float32.
+ *   - Fixed point: positions are int32 in units of 2^-16 cell (Q16); unit vectors and rotation
+ *     entries are int32 in units of 2^-30 (Q30).
+ *   - Ownership: every array pointer is device memory owned by the caller (for example a torch
+ *     tensor's data_ptr) unless stated otherwise. The library never allocates device memory.
+ *   - Asynchrony: work is enqueued on `stream` (NULL = legacy default stream) and the call
+ *     returns without waiting. Output arrays are valid once the stream reaches that point.
+ *   - Errors: arguments are checked on the host before any launch; on FSMI_ERR_ARG nothing is
+ *     launched and outputs are untouched. A launch failure returns FSMI_ERR_CUDA. Conditions only
+ *     a kernel can see (a beam longer than its capacity, an RLE output buffer too small) set bits
+ *     of a per-device status word that fsmi_device_status() reads; the affected outputs are NaN
+ *     (MI) or truncated (runs), never written out of bounds.
+ *   - Kernels never spin on flags or other kernels; nothing here can hang the device.
+ *   - Results for a beam whose origin lies outside the map are 0 (the beam crosses no cell).
+ */
+#ifndef FSMI_H
+#define FSMI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; declared here so the header needs no CUDA include. */
+typedef struct CUstream_st *fsmi_stream_t;
+
+typedef enum {
+    FSMI_OK = 0,
+    FSMI_ERR_ARG = 1,       /* invalid argument: nothing was launched */
+    FSMI_ERR_CAPACITY = 2,  /* a size exceeds a documented maximum */
+    FSMI_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed */
+    FSMI_ERR_TIMEOUT = 4,   /* reserved for bounded device-side waits */
+    FSMI_ERR_WORKSPACE = 5  /* the caller's workspace is too small */
+} fsmi_status;
+
+typedef enum {
+    FSMI_EXACT = 0,   /* Gaussian noise, every cell pair (O(n^2) / O(n_r^2)) */
+    FSMI_APPROX = 1,  /* Gaussian truncated to +-trunc_delta cells (O(n Delta) / O(n_r Delta)) */
+    FSMI_UNIFORM = 2  /* uniform noise of half-width uniform_h cells (O(n) / O(n_r H)) */
+} fsmi_variant;
+
+/* Noise kernel between virtual cells for the RLE variants. Theorem 3 writes G_{k,j} as the
+ * Gaussian density at the cell-index distance (FSMI_G_PDF, the default); FSMI_G_ERF uses the
+ * Gaussian mass of a unit cell instead, which makes FSMI-RLE on runs equal FSMI on the
+ * decompressed cells. */
+typedef enum { FSMI_G_PDF = 0, FSMI_G_ERF = 1 } fsmi_kernel;
+
+/* Device status word bits (fsmi_device_status). */
+#define FSMI_STATUS_BEAM_OVERFLOW 0x1  /* a beam had more cells than its capacity: its MI is NaN */
+#define FSMI_STATUS_RUN_OVERFLOW 0x2   /* RLE output exceeded run_capacity: runs were truncated */
+#define FSMI_STATUS_BAD_BEAM 0x4       /* an explicit beam or ray exceeded the per-beam maximum */
+
+typedef struct {
+    int variant;        /* fsmi_variant */
+    float sigma;        /* Gaussian range-noise standard deviation, cells, > 0 (EXACT, APPROX) */
+    float delta_occ;    /* odds factor for the cell that stops the beam, eq. (inverse_sensing), > 0 */
+    float delta_emp;    /* odds factor for cells the beam passed, > 0 */
+    int trunc_delta;    /* Delta, cells, >= 0 (APPROX) */
+    int uniform_h;      /* H, cells, >= 0 (UNIFORM) */
+    float max_range;    /* beam length, cells, in (0, FSMI_MAX_RANGE_2D] (2D); 3D: virtual cells per ray */
+    int run_cap;        /* longest run the RLE encoder emits, in [1, 255] */
+    int g_kernel;       /* fsmi_kernel (RLE variants) */
+    int e0_mode;        /* 2D only: 0 drops the no-return event e_0; 1 places it at virtual index 0
+                           (Algorithm 4) with centre l_1 - 1/2 */
+    int approx_reading; /* Approx-FSMI-RLE: 0 = Theorem 5's sub-blocks as printed (default),
+                           1 = strict band |k - j| <= Delta */
+} fsmi_params;
+
+/* Documented maxima. */
+#define FSMI_MAX_GRID 32767        /* W, H (2D) and X, Y, Z (3D) */
+#define FSMI_MAX_RANGE_2D 1024.0f  /* cells; a 2D beam then crosses at most 1451 cells */
+#define FSMI_MAX_CELLS 2048        /* cells of one explicit beam (fsmi_eval_beams) */
+#define FSMI_MAX_SAMPLES_3D 1024   /* virtual cells of one 3D ray (floor(max_range)) */
+#define FSMI_MAX_KERNEL_RADIUS 64  /* RLE noise-kernel support, cells: ceil(7.45 sigma) or H */
+
+/*
+ * fsmi_eval_2d - mutual information of every beam of every pose on a 2D occupancy grid.
+ * Section 2.4 (problem formulation), Section 3: per beam, the integer fixed-point traversal of
+ * the grid gives the ordered cells and their entry distances l_i (l_1 = 0, Section 3.1), then
+ * P(e_j) (Algorithm 2), C_k (Algorithm 3) and the variant's pair sum.
+ *   map    float32 [H][W] row-major, o in [0, 1] (cell (x, y) at map[y*W + x]).
+ *   poses  int32 [P][4]: x, y (Q16, cell units), cos(yaw), sin(yaw) (Q30).
+ *   dirs   int32 [B][2]: beam unit vectors in the sensor frame (Q30). Beam b of pose p points
+ *          along d = floor((Rot(yaw_p) dirs[b] + 2^29) / 2^30).
+ *   out    float32 [P][B], nats.
+ * The traversal is exact integer arithmetic: a cell is entered while its entry distance is
+ * < max_range and it lies inside the grid; simultaneous x/y crossings are one diagonal step.
+ */
+fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, int P,
+                         const int32_t *dirs, int B, const fsmi_params *prm, float *out,
+                         fsmi_stream_t stream);
+
+/*
+ * fsmi_eval_beams - the same pair sums on explicit beams (Theorem 1's inputs: o_i, l_i).
+ *   off    int32 [nbeams+1] CSR offsets; beam b owns cells off[b] .. off[b+1]-1
+ *          (at most FSMI_MAX_CELLS cells).
+ *   o      float32 [off[nbeams]] occupancy probabilities, in beam order.
+ *   l      float32 [off[nbeams]] entry distances, increasing within a beam, first one 0.
+ *   lend   float32 [nbeams] end distance l_{n+1} of each beam.
+ *   out    float32 [nbeams], nats.
+ */
+fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend,
+                            int nbeams, const fsmi_params *prm, float *out, fsmi_stream_t stream);
+
+/*
+ * fsmi_trace_2d - exports the traversal used by fsmi_eval_2d (same inputs) so that cell lists
+ * can be compared bit for bit.
+ *   cells  int32 [P*B][cap]: cell ids y*W + x in beam order.
+ *   l      float32 [P*B][cap+1]: entry distances, then the end distance at index n.
+ *   n      int32 [P*B]: cell count, or -1 if the beam has more than cap cells.
+ */
+fsmi_status fsmi_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                          float max_range, int cap, int32_t *cells, float *l, int32_t *n,
+                          fsmi_stream_t stream);
+
+/*
+ * fsmi_rle_encode_3d - Section 4: each ray is projected onto equal virtual cells (cell i is the
+ * voxel holding o + (i + 1/2) d, i = 0 .. floor(max_range)-1, stopping at the grid boundary),
+ * and the occupancy sequence is run-length encoded (eq. occup_rle) into maximal runs of
+ * bit-identical values, split greedily from the sensor into runs of at most run_cap cells.
+ *   vox      float32 [Z][Y][X], o in [0, 1] (voxel (x, y, z) at vox[(z*Y + y)*X + x]).
+ *   poses    int32 [P][12]: x, y, z (Q16), then the sensor rotation R row-major (Q30).
+ *   dirs     int32 [R][3]: ray unit vectors in the sensor frame (Q30); ray r of pose p points
+ *            along d = floor((R_p dirs[r] + 2^29) / 2^30).
+ *   run_off  int32 [P*R+1] output CSR offsets (ray i = p*R + r).
+ *   run_o    float32 [run_capacity], run_len uint8 [run_capacity]: output runs.
+ *   ws       device workspace of at least fsmi_workspace_size(FSMI_FN_RLE_ENCODE_3D, ...) bytes.
+ * If the runs exceed run_capacity, the status bit FSMI_STATUS_RUN_OVERFLOW is set, run_off
+ * still holds the full offsets and only runs below run_capacity are written.
+ */
+fsmi_status fsmi_rle_encode_3d(const float *vox, int X, int Y, int Z, const int32_t *poses, int P,
+                               const int32_t *dirs, int R, const fsmi_params *prm, int32_t *run_off,
+                               float *run_o, uint8_t *run_len, int run_capacity, void *ws,
+                               size_t ws_bytes, fsmi_stream_t stream);
+
+/*
+ * fsmi_eval_rle - FSMI-RLE (Theorem 3), Approx-FSMI-RLE (Theorem 5) or Uniform-FSMI-RLE
+ * (Theorem 6) of run-length-encoded rays.
+ *   run_off  int32 [nrays+1] CSR offsets; ray r owns runs run_off[r] .. run_off[r+1]-1 whose
+ *            lengths sum to at most FSMI_MAX_SAMPLES_3D virtual cells.
+ *   run_o    float32 occupancy of each run; run_len uint8 length (>= 1) of each run.
+ *   out      float32 [nrays], nats.
+ */
+fsmi_status fsmi_eval_rle(const int32_t *run_off, const float *run_o, const uint8_t *run_len,
+                          int nrays, const fsmi_params *prm, float *out, fsmi_stream_t stream);
+
+/*
+ * fsmi_eval_3d - fused 3D path: sampling, run-length encoding and the RLE variant of every ray,
+ * with the runs kept on chip. Same inputs as fsmi_rle_encode_3d; out float32 [P][R] in nats;
+ * nruns (optional, may be NULL) int32 [P][R] receives each ray's run count.
+ */
+fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *poses, int P,
+                         const int32_t *dirs, int R, const fsmi_params *prm, float *out,
+                         int32_t *nruns, fsmi_stream_t stream);
+
+/* Function ids for fsmi_workspace_size. */
+#define FSMI_FN_EVAL_2D 0
+#define FSMI_FN_EVAL_BEAMS 1
+#define FSMI_FN_RLE_ENCODE_3D 2
+#define FSMI_FN_EVAL_RLE 3
+#define FSMI_FN_EVAL_3D 4
+
+/* Bytes of device workspace entry point `fn` needs for `nitems` beams or rays (0 if none). */
+fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm, size_t *bytes);
+
+/* Waits for `stream`, then returns in *status the current device's status word (FSMI_STATUS_*
+ * bits, 0 if clean) and clears it. *status is host memory. */
+fsmi_status fsmi_device_status(fsmi_stream_t stream, int *status);
+
+/* Human-readable name of a status code (static string). */
+const char *fsmi_status_str(fsmi_status s);
+
+/* The cudaError_t value behind the calling thread's last FSMI_ERR_CUDA (0 if none). */
+int fsmi_last_cuda_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int fsmi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSMI_H */

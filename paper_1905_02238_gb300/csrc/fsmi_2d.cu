@@ -1,0 +1,417 @@
+// 2D hot path: fixed-point ray traversal, first-hit probabilities, C_k and the FSMI /
+// Approx-FSMI / Uniform-FSMI pair sums, one warp per beam.
+//
+// Per beam (Section 3): the traversal lists the cells the beam crosses with entry distances
+// l_1 = 0 < l_2 < ... and end l_{n+1}; Algorithm 2 gives P(e_j) = o_j prod_{i<j}(1 - o_i);
+// Algorithm 3 gives C_k = sum_{i<k} f(delta_emp, r_i) + f(delta_occ, r_k); the variant then sums
+//   FSMI (Theorem 1):      sum_j P(e_j) sum_{k=1..n} C_k G_{k,j}
+//   Approx (eq. fsmi_approx): the same with |k - j| <= Delta
+//   Uniform (Algorithm 4): sum_j P(e_j) (D_{min(n,j+H)} - D_{max(0,j-H-1)}) / (2H + 1)
+//
+// The Gaussian pair sum is evaluated per first-hit cell j in the boundary form
+//   S_j = sum_k C_k (Phi(x_{k+1}) - Phi(x_k)) = C_j + sum_{m=1}^{n+1} (C_m - C_{m-1}) sgn(x_m) T(|x_m|)
+// with x_m = (l_m - mu_j) / sigma, C_0 = C_{n+1} = 0 and T the upper Gaussian tail. This is the
+// same sum regrouped by boundary (summation by parts); every term is a tail mass, so no
+// difference of two values near 1 is ever formed in FP32.
+#include "../../include/fsmi.h"
+#include "fsmi_device.cuh"
+#include "fsmi_internal.h"
+
+namespace fsmi {
+
+// Beam direction: the sensor-frame unit vector u rotated by the pose's (cos, sin), rounded half
+// up: d = floor((Rot u + 2^29) / 2^30). Arithmetic right shift is a floor division by 2^30.
+__device__ __forceinline__ void beam_dir(const int32_t *pose, int32_t ux, int32_t uy, int &dx, int &dy)
+{
+    const long long c = pose[2], s = pose[3];
+    dx = (int)((c * ux - s * uy + (1LL << 29)) >> 30);
+    dy = (int)((s * ux + c * uy + (1LL << 29)) >> 30);
+}
+
+// Integer traversal of one beam. Origin (ox, oy) in Q16 cell units, direction (dx, dy) in Q30.
+// The beam's distance parameter is lambda in o + lambda * d / 2^30. The first cell is the one
+// entered by o + eps * d; a cell is appended while its entry lambda is < R (rfix = R * 2^16) and it
+// lies inside the W x H grid. Crossings are ordered by exact int64 comparison of
+// nx / |dx| versus ny / |dy| (nx, ny: Q16 distances from the origin to the next x / y boundary); a
+// tie is one diagonal step. Writes cells[0..n-1], l[0..n] (l[n] = min(R, grid exit)) and returns n,
+// or -1 if the beam has more than cap cells.
+__device__ int dda_2d(int W, int H, int ox, int oy, int dx, int dy, long long rfix, int cap, int *cells,
+                      float *l)
+{
+    if ((dx | dy) == 0) return 0;
+    int cx = ox >> 16, cy = oy >> 16;
+    if (dx < 0 && (ox & 0xFFFF) == 0) --cx;
+    if (dy < 0 && (oy & 0xFFFF) == 0) --cy;
+    if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) return 0;
+    const long long adx = dx < 0 ? -(long long)dx : dx;
+    const long long ady = dy < 0 ? -(long long)dy : dy;
+    const int sx = dx > 0 ? 1 : -1, sy = dy > 0 ? 1 : -1;
+    long long nx = dx > 0 ? ((long long)(cx + 1) << 16) - ox : (long long)ox - ((long long)cx << 16);
+    long long ny = dy > 0 ? ((long long)(cy + 1) << 16) - oy : (long long)oy - ((long long)cy << 16);
+    const double rx = adx ? 16384.0 / (double)adx : 0.0;
+    const double ry = ady ? 16384.0 / (double)ady : 0.0;
+    if (cap < 1) return -1;
+    cells[0] = cy * W + cx;
+    l[0] = 0.0f;
+    int n = 1;
+    for (;;) {
+        bool stx, sty;
+        if (dx == 0) {
+            stx = false;
+            sty = true;
+        } else if (dy == 0) {
+            stx = true;
+            sty = false;
+        } else {
+            const long long tx = nx * ady, ty = ny * adx;
+            stx = tx <= ty;
+            sty = ty <= tx;
+        }
+        const long long num = stx ? nx : ny, den = stx ? adx : ady;
+        if ((num << 30) >= rfix * den) {
+            l[n] = (float)((double)rfix * (1.0 / 65536.0));
+            break;
+        }
+        const float lam = (float)((double)num * (stx ? rx : ry));
+        if (stx) {
+            cx += sx;
+            nx += 65536;
+        }
+        if (sty) {
+            cy += sy;
+            ny += 65536;
+        }
+        if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) {
+            l[n] = lam;
+            break;
+        }
+        if (n >= cap) return -1;
+        cells[n] = cy * W + cx;
+        l[n] = lam;
+        ++n;
+    }
+    return n;
+}
+
+struct Src2D {
+    // map source
+    const float *map;
+    int W, H;
+    const int32_t *poses;
+    int P;
+    const int32_t *dirs;
+    int B;
+    // explicit-beam source
+    const int32_t *off;
+    const float *o;
+    const float *l;
+    const float *lend;
+};
+
+// One register-blocked pass of the exact pair sum: each lane owns J first-hit slots
+// j = jb + lane + 32 t and streams every boundary m = 0..n from shared memory. Slot n is the
+// no-return event when e0 is set (centre l_1 - 1/2, C_0 = 0).
+template <int J>
+__device__ __forceinline__ float exact_pass(const float *sl, const float *sc, const float *sp, int n, int jb,
+                                            bool e0, float pe0, float inv_s2)
+{
+    const int lane = lane_id();
+    float mu[J], acc[J];
+#pragma unroll
+    for (int t = 0; t < J; ++t) {
+        const int j = jb + lane + 32 * t;
+        mu[t] = (j < n) ? 0.5f * (sl[j] + sl[j + 1]) : ((j == n && e0) ? sl[0] - 0.5f : 3.0e30f);
+        acc[t] = 0.0f;
+    }
+    float cprev = 0.0f;
+    for (int m = 0; m <= n; ++m) {
+        const float lm = sl[m];
+        const float cm = sc[m];  // sc[n] = 0 (C_{n+1})
+        const float dc = cm - cprev;
+        cprev = cm;
+#pragma unroll
+        for (int t = 0; t < J; ++t) {
+            const float d = lm - mu[t];
+            const float T = half_erfc(fabsf(d) * inv_s2);
+            acc[t] = fmaf(copysignf(dc, d), T, acc[t]);
+        }
+    }
+    float r = 0.0f;
+#pragma unroll
+    for (int t = 0; t < J; ++t) {
+        const int j = jb + lane + 32 * t;
+        if (j < n)
+            r = fmaf(sp[j], sc[j] + acc[t], r);
+        else if (j == n && e0)
+            r = fmaf(pe0, acc[t], r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ float exact_sum(const float *sl, const float *sc, const float *sp, int n, bool e0,
+                                           float pe0, float inv_s2)
+{
+    const int nslots = n + (e0 ? 1 : 0);
+    float r = 0.0f;
+    for (int jb = 0; jb < nslots; jb += 32 * 16) {
+        const int cnt = min(16, (nslots - jb + 31) >> 5);
+        switch (cnt) {
+#define FSMI_CASE(J) \
+    case J: r += exact_pass<J>(sl, sc, sp, n, jb, e0, pe0, inv_s2); break;
+            FSMI_CASE(1) FSMI_CASE(2) FSMI_CASE(3) FSMI_CASE(4) FSMI_CASE(5) FSMI_CASE(6) FSMI_CASE(7) FSMI_CASE(8)
+            FSMI_CASE(9) FSMI_CASE(10) FSMI_CASE(11) FSMI_CASE(12) FSMI_CASE(13) FSMI_CASE(14) FSMI_CASE(15)
+            FSMI_CASE(16)
+#undef FSMI_CASE
+            default: break;
+        }
+    }
+    return r;
+}
+
+// Approx-FSMI: for slot j the band k in [klo, khi] = [j - Delta, j + Delta] n [0, n-1] (0-based),
+// i.e. boundaries m in [klo, khi + 1] with C' = C on the band and 0 outside it.
+__device__ __forceinline__ float approx_sum(const float *sl, const float *sc, const float *sp, int n, bool e0,
+                                            float pe0, float inv_s2, int D)
+{
+    const int nslots = n + (e0 ? 1 : 0);
+    float r = 0.0f;
+    for (int j = lane_id(); j < nslots; j += 32) {
+        float mu, Cj, Pj;
+        int klo, khi;
+        if (j < n) {
+            mu = 0.5f * (sl[j] + sl[j + 1]);
+            Cj = sc[j];
+            Pj = sp[j];
+            klo = max(0, j - D);
+            khi = min(n - 1, j + D);
+        } else {  // e_0 at virtual index 0: paper band k in [1, Delta]
+            mu = sl[0] - 0.5f;
+            Cj = 0.0f;
+            Pj = pe0;
+            klo = 0;
+            khi = min(n - 1, D - 1);
+        }
+        float acc = 0.0f;
+        for (int m = klo; m <= khi + 1; ++m) {
+            const float cm = (m <= khi) ? sc[m] : 0.0f;
+            const float cm1 = (m > klo) ? sc[m - 1] : 0.0f;
+            const float d = sl[m] - mu;
+            acc = fmaf(copysignf(cm - cm1, d), half_erfc(fabsf(d) * inv_s2), acc);
+        }
+        r = fmaf(Pj, Cj + acc, r);
+    }
+    return r;
+}
+
+// Uniform-FSMI (Algorithm 4) from D = inclusive prefix of C (sd), with Algorithm 4's clamps.
+__device__ __forceinline__ float uniform_sum(const float *sd, const float *sp, int n, bool e0, float pe0, int H,
+                                             float inv_2h1)
+{
+    float r = 0.0f;
+    for (int j = lane_id(); j < n; j += 32) {
+        const int hi = min(n - 1, j + H);
+        const int lo = j - H - 1;
+        const float S = (sd[hi] - (lo >= 0 ? sd[lo] : 0.0f)) * inv_2h1;
+        r = fmaf(sp[j], S, r);
+    }
+    if (e0 && lane_id() == 0) {
+        const int hi = min(n - 1, H - 1);
+        if (hi >= 0) r = fmaf(pe0, sd[hi] * inv_2h1, r);
+    }
+    return r;
+}
+
+// Chunked warp scan over the n cells held in shared memory. On entry sp = o, sc = f_occ,
+// sx = f_emp. On exit sp = P(e_j), sc = C_j (sc[n] = 0), and for the uniform variant sx = D_j.
+// Returns P(e_0).
+__device__ __forceinline__ float cell_prefixes(float *sp, float *sc, float *sx, int n, bool want_d)
+{
+    const int lane = lane_id();
+    const int K = (n + 31) >> 5;
+    const int lo = min(n, lane * K), hi = min(n, lo + K);
+    float prod = 1.0f, sum = 0.0f;
+    for (int i = lo; i < hi; ++i) {
+        prod *= 1.0f - sp[i];
+        sum += sx[i];
+    }
+    const float iprod = warp_incl_mul(prod);
+    const float isum = warp_incl_add(sum);
+    float E = __shfl_up_sync(kFull, iprod, 1);
+    float q = __shfl_up_sync(kFull, isum, 1);
+    if (lane == 0) {
+        E = 1.0f;
+        q = 0.0f;
+    }
+    const float pe0 = __shfl_sync(kFull, iprod, 31);
+    float csum = 0.0f;
+    for (int i = lo; i < hi; ++i) {
+        const float o = sp[i];
+        sp[i] = E * o;  // Algorithm 2
+        E *= 1.0f - o;
+        const float c = q + sc[i];  // Algorithm 3
+        sc[i] = c;
+        q += sx[i];
+        csum += c;
+    }
+    if (want_d) {  // Algorithm 4: D_k = sum_{i<=k} C_i
+        const float ic = warp_incl_add(csum);
+        float Dacc = __shfl_up_sync(kFull, ic, 1);
+        if (lane == 0) Dacc = 0.0f;
+        for (int i = lo; i < hi; ++i) {
+            Dacc += sc[i];
+            sx[i] = Dacc;
+        }
+    }
+    if (lane == 0) sc[n] = 0.0f;
+    __syncwarp();
+    return pe0;
+}
+
+template <int VAR, bool FROM_MAP>
+__global__ void __launch_bounds__(kWarps2D * 32)
+    k_eval_2d(Src2D src, DevParams p, long long nbeams, int stride, float *__restrict__ out, int *status)
+{
+    extern __shared__ float smem[];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    float *sl = smem + (size_t)warp * 4 * stride;
+    float *sc = sl + stride;
+    float *sp = sc + stride;
+    float *sx = sp + stride;
+    const bool e0 = p.e0 != 0;
+    for (long long beam = (long long)blockIdx.x * kWarps2D + warp; beam < nbeams;
+         beam += (long long)gridDim.x * kWarps2D) {
+        int n;
+        if (FROM_MAP) {
+            const int pi = (int)(beam / src.B), bi = (int)(beam % src.B);
+            if (lane == 0) {
+                const int32_t *pose = src.poses + 4 * (size_t)pi;
+                int dx, dy;
+                beam_dir(pose, src.dirs[2 * bi], src.dirs[2 * bi + 1], dx, dy);
+                n = dda_2d(src.W, src.H, pose[0], pose[1], dx, dy, p.rfix, p.nmax, (int *)sx, sl);
+            }
+            n = __shfl_sync(kFull, n, 0);
+            __syncwarp();
+            if (n < 0) {
+                if (lane == 0) {
+                    out[beam] = __int_as_float(0x7fc00000);
+                    set_status(status, FSMI_STATUS_BEAM_OVERFLOW);
+                }
+                __syncwarp();
+                continue;
+            }
+            for (int i = lane; i < n; i += 32) {
+                const float o = __ldg(src.map + ((const int *)sx)[i]);
+                sp[i] = o;
+                sc[i] = cell_gain(p.docc, o);
+                sx[i] = cell_gain(p.demp, o);
+            }
+        } else {
+            const int base = src.off[beam];
+            n = src.off[beam + 1] - base;
+            if (n < 0 || n > p.nmax) {
+                if (lane == 0) {
+                    out[beam] = __int_as_float(0x7fc00000);
+                    set_status(status, FSMI_STATUS_BAD_BEAM);
+                }
+                continue;
+            }
+            for (int i = lane; i < n; i += 32) {
+                const float o = __ldg(src.o + base + i);
+                sl[i] = __ldg(src.l + base + i);
+                sp[i] = o;
+                sc[i] = cell_gain(p.docc, o);
+                sx[i] = cell_gain(p.demp, o);
+            }
+            if (lane == 0) sl[n] = __ldg(src.lend + beam);
+        }
+        __syncwarp();
+        float I = 0.0f;
+        if (n > 0) {
+            const float pe0 = cell_prefixes(sp, sc, sx, n, VAR == FSMI_UNIFORM);
+            if (VAR == FSMI_EXACT)
+                I = exact_sum(sl, sc, sp, n, e0, pe0, p.inv_s2);
+            else if (VAR == FSMI_APPROX)
+                I = approx_sum(sl, sc, sp, n, e0, pe0, p.inv_s2, p.trunc);
+            else
+                I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
+            I = warp_sum(I);
+        }
+        if (lane == 0) out[beam] = I;
+        __syncwarp();
+    }
+}
+
+__global__ void k_trace_2d(int W, int H, const int32_t *__restrict__ poses, const int32_t *__restrict__ dirs, int B,
+                           long long nbeams, long long rfix, int cap, int32_t *__restrict__ cells, float *__restrict__ l,
+                           int32_t *__restrict__ nout)
+{
+    for (long long beam = (long long)blockIdx.x * blockDim.x + threadIdx.x; beam < nbeams;
+         beam += (long long)gridDim.x * blockDim.x) {
+        const int pi = (int)(beam / B), bi = (int)(beam % B);
+        const int32_t *pose = poses + 4 * (size_t)pi;
+        int dx, dy;
+        beam_dir(pose, dirs[2 * bi], dirs[2 * bi + 1], dx, dy);
+        nout[beam] = dda_2d(W, H, pose[0], pose[1], dx, dy, rfix, cap, cells + beam * cap, l + beam * (cap + 1));
+    }
+}
+
+template <int VAR, bool FROM_MAP>
+static cudaError_t launch_variant(const Src2D &src, const DevParams &p, long long nbeams, float *out, int *status,
+                                  cudaStream_t s)
+{
+    const int stride = ((p.nmax + 2) + 3) & ~3;
+    const size_t smem = (size_t)kWarps2D * 4 * stride * sizeof(float);
+    auto kern = k_eval_2d<VAR, FROM_MAP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps2D * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    long long want = (nbeams + kWarps2D - 1) / kWarps2D;
+    long long grid = (long long)sm_count() * occ;
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kWarps2D * 32, smem, s>>>(src, p, nbeams, stride, out, status);
+    return cudaGetLastError();
+}
+
+template <bool FROM_MAP>
+static cudaError_t dispatch(const Src2D &src, const DevParams &p, long long nbeams, float *out, int *status,
+                            cudaStream_t s)
+{
+    if (nbeams <= 0) return cudaSuccess;
+    switch (p.variant) {
+        case FSMI_EXACT: return launch_variant<FSMI_EXACT, FROM_MAP>(src, p, nbeams, out, status, s);
+        case FSMI_APPROX: return launch_variant<FSMI_APPROX, FROM_MAP>(src, p, nbeams, out, status, s);
+        default: return launch_variant<FSMI_UNIFORM, FROM_MAP>(src, p, nbeams, out, status, s);
+    }
+}
+
+cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                           const DevParams &p, float *out, int *status, cudaStream_t s)
+{
+    Src2D src{map, W, H, poses, P, dirs, B, nullptr, nullptr, nullptr, nullptr};
+    return dispatch<true>(src, p, (long long)P * B, out, status, s);
+}
+
+cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
+                              const DevParams &p, float *out, int *status, cudaStream_t s)
+{
+    Src2D src{nullptr, 0, 0, nullptr, 0, nullptr, 0, off, o, l, lend};
+    return dispatch<false>(src, p, nbeams, out, status, s);
+}
+
+cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,
+                            int cap, int32_t *cells, float *l, int32_t *n, cudaStream_t s)
+{
+    const long long nb = (long long)P * B;
+    if (nb <= 0) return cudaSuccess;
+    long long grid = (nb + 127) / 128;
+    const long long gmax = (long long)sm_count() * 16;
+    if (grid > gmax) grid = gmax;
+    k_trace_2d<<<(unsigned)grid, 128, 0, s>>>(W, H, poses, dirs, B, nb, rfix, cap, cells, l, n);
+    return cudaGetLastError();
+}
+
+}  // namespace fsmi

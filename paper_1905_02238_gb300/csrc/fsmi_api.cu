@@ -1,0 +1,274 @@
+// C ABI of libfsmi (include/fsmi.h): argument checks on the host, derived constants, the
+// per-device status word, and dispatch to the kernel launchers.
+#include <math.h>
+
+#include <mutex>
+
+#include "../../include/fsmi.h"
+#include "fsmi_internal.h"
+
+namespace fsmi {
+
+// Per-device status word (FSMI_STATUS_* bits), set by kernels with atomicOr.
+__device__ int g_status;
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int *g_status_ptr[kMaxDevices];
+int g_sms[kMaxDevices];
+thread_local int g_last_cuda = 0;
+
+int current_device()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    return dev;
+}
+
+// Device address of g_status for the current device (looked up once per device with that
+// device current; host code must not use the symbol itself as an address).
+int *status_ptr()
+{
+    const int dev = current_device();
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) == cudaSuccess) g_status_ptr[dev] = (int *)p;
+    }
+    return g_status_ptr[dev];
+}
+
+fsmi_status cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return FSMI_ERR_CUDA;
+}
+
+bool finite_pos(float v) { return isfinite(v) && v > 0.0f; }
+
+// Support radius of the RLE noise kernel: beyond 7.45 sigma the Gaussian is below 1e-12 of its
+// peak, so the dropped terms change no FP32 result.
+int gauss_radius(float sigma) { return (int)ceilf(7.45f * sigma); }
+
+enum Use { kUse2D, kUseBeams, kUseRLE };
+
+fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
+{
+    if (!prm) return FSMI_ERR_ARG;
+    if (prm->variant < FSMI_EXACT || prm->variant > FSMI_UNIFORM) return FSMI_ERR_ARG;
+    if (!finite_pos(prm->delta_occ) || !finite_pos(prm->delta_emp)) return FSMI_ERR_ARG;
+    if (prm->variant != FSMI_UNIFORM && !finite_pos(prm->sigma)) return FSMI_ERR_ARG;
+    if (prm->variant == FSMI_APPROX && prm->trunc_delta < 0) return FSMI_ERR_ARG;
+    if (prm->variant == FSMI_UNIFORM && prm->uniform_h < 0) return FSMI_ERR_ARG;
+    if (prm->e0_mode != 0 && prm->e0_mode != 1) return FSMI_ERR_ARG;
+    if (prm->g_kernel != FSMI_G_PDF && prm->g_kernel != FSMI_G_ERF) return FSMI_ERR_ARG;
+    if (prm->approx_reading != 0 && prm->approx_reading != 1) return FSMI_ERR_ARG;
+    if (use != kUseBeams && !finite_pos(prm->max_range)) return FSMI_ERR_ARG;
+    d.variant = prm->variant;
+    d.sigma = prm->variant == FSMI_UNIFORM ? 1.0f : prm->sigma;
+    d.inv_s2 = (float)(1.0 / ((double)d.sigma * 1.4142135623730951));
+    d.docc = prm->delta_occ;
+    d.demp = prm->delta_emp;
+    d.trunc = prm->trunc_delta;
+    d.H = prm->uniform_h;
+    d.inv_2h1 = (float)(1.0 / (2.0 * prm->uniform_h + 1.0));
+    d.e0 = prm->e0_mode;
+    d.run_cap = prm->run_cap;
+    d.g_kernel = prm->g_kernel;
+    d.approx_reading = prm->approx_reading;
+    d.rfix = 0;
+    d.K = 0;
+    if (use == kUse2D) {
+        if (prm->max_range > FSMI_MAX_RANGE_2D) return FSMI_ERR_CAPACITY;
+        d.rfix = llrint((double)prm->max_range * 65536.0);
+        // a segment of length R crosses at most R(|cos| + |sin|) + 2 <= R sqrt(2) + 2 cells
+        d.nmax = (int)((double)prm->max_range * 1.41421357) + 3;
+    } else if (use == kUseBeams) {
+        d.nmax = FSMI_MAX_CELLS;
+    } else {
+        const double ns = floor((double)prm->max_range);
+        if (ns < 1.0) return FSMI_ERR_ARG;
+        if (ns > FSMI_MAX_SAMPLES_3D) return FSMI_ERR_CAPACITY;
+        d.nmax = (int)ns;
+        if (prm->run_cap < 1 || prm->run_cap > 255) return FSMI_ERR_ARG;
+        if (prm->variant == FSMI_UNIFORM) {
+            d.K = prm->uniform_h;
+        } else {
+            d.K = gauss_radius(prm->sigma);
+            if (d.K < 1) d.K = 1;
+            if (prm->variant == FSMI_APPROX && prm->approx_reading == 1 && prm->trunc_delta < d.K) d.K = prm->trunc_delta;
+        }
+        if (d.K > FSMI_MAX_KERNEL_RADIUS) return FSMI_ERR_CAPACITY;
+    }
+    return FSMI_OK;
+}
+
+bool grid_ok(int v) { return v >= 1 && v <= FSMI_MAX_GRID; }
+}  // namespace
+
+int sm_count()
+{
+    const int dev = current_device();
+    if (dev < 0 || dev >= kMaxDevices) return 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sms[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = v > 0 ? v : 1;
+    }
+    return g_sms[dev];
+}
+
+}  // namespace fsmi
+
+using namespace fsmi;
+
+extern "C" {
+
+fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                         const fsmi_params *prm, float *out, fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUse2D, d);
+    if (st != FSMI_OK) return st;
+    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0) return FSMI_ERR_ARG;
+    if ((long long)P * B == 0) return FSMI_OK;
+    if (!map || !poses || !dirs || !out) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_eval_2d(map, W, H, poses, P, dirs, B, d, out, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
+                            const fsmi_params *prm, float *out, fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUseBeams, d);
+    if (st != FSMI_OK) return st;
+    if (nbeams < 0) return FSMI_ERR_ARG;
+    if (nbeams == 0) return FSMI_OK;
+    if (!off || !o || !l || !lend || !out) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_eval_beams(off, o, l, lend, nbeams, d, out, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, float max_range,
+                          int cap, int32_t *cells, float *l, int32_t *n, fsmi_stream_t stream)
+{
+    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || cap < 1) return FSMI_ERR_ARG;
+    if (!isfinite(max_range) || max_range <= 0.0f) return FSMI_ERR_ARG;
+    if (max_range > FSMI_MAX_RANGE_2D) return FSMI_ERR_CAPACITY;
+    if ((long long)P * B == 0) return FSMI_OK;
+    if (!poses || !dirs || !cells || !l || !n) return FSMI_ERR_ARG;
+    const long long rfix = llrint((double)max_range * 65536.0);
+    cudaError_t e = launch_trace_2d(W, H, poses, P, dirs, B, rfix, cap, cells, l, n, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+static bool vox_ok(const float *vox, int X, int Y, int Z, const int32_t *poses, int P, const int32_t *dirs, int R)
+{
+    return grid_ok(X) && grid_ok(Y) && grid_ok(Z) && P >= 0 && R >= 0 &&
+           ((long long)P * R == 0 || (vox && poses && dirs));
+}
+
+static long long scan_tiles(long long nitems) { return (nitems + kScanTile - 1) / kScanTile; }
+
+fsmi_status fsmi_rle_encode_3d(const float *vox, int X, int Y, int Z, const int32_t *poses, int P,
+                               const int32_t *dirs, int R, const fsmi_params *prm, int32_t *run_off, float *run_o,
+                               uint8_t *run_len, int run_capacity, void *ws, size_t ws_bytes, fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUseRLE, d);
+    if (st != FSMI_OK) return st;
+    if (!vox_ok(vox, X, Y, Z, poses, P, dirs, R) || run_capacity < 0 || !run_off) return FSMI_ERR_ARG;
+    const long long nrays = (long long)P * R;
+    if (nrays > 0x7ffffffeLL) return FSMI_ERR_CAPACITY;
+    if (run_capacity > 0 && (!run_o || !run_len)) return FSMI_ERR_ARG;
+    const long long ntiles = scan_tiles(nrays);
+    if (ntiles > 0 && (!ws || ws_bytes < (size_t)ntiles * sizeof(int32_t) || ((uintptr_t)ws & 3))) return FSMI_ERR_WORKSPACE;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    Vox3D v{vox, X, Y, Z, poses, P, dirs, R};
+    cudaError_t e = launch_rle_encode_3d(v, d, run_off, run_o, run_len, run_capacity, (int32_t *)ws, (int)ntiles, sp,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_eval_rle(const int32_t *run_off, const float *run_o, const uint8_t *run_len, int nrays,
+                          const fsmi_params *prm, float *out, fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUseRLE, d);
+    if (st != FSMI_OK) return st;
+    if (nrays < 0) return FSMI_ERR_ARG;
+    if (nrays == 0) return FSMI_OK;
+    if (!run_off || !run_o || !run_len || !out) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_eval_rle(run_off, run_o, run_len, nrays, d, out, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *poses, int P, const int32_t *dirs,
+                         int R, const fsmi_params *prm, float *out, int32_t *nruns, fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUseRLE, d);
+    if (st != FSMI_OK) return st;
+    if (!vox_ok(vox, X, Y, Z, poses, P, dirs, R)) return FSMI_ERR_ARG;
+    if ((long long)P * R == 0) return FSMI_OK;
+    if (!out) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    Vox3D v{vox, X, Y, Z, poses, P, dirs, R};
+    cudaError_t e = launch_eval_3d(v, d, out, nruns, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm, size_t *bytes)
+{
+    (void)prm;
+    if (!bytes || nitems < 0) return FSMI_ERR_ARG;
+    *bytes = 0;
+    if (fn == FSMI_FN_RLE_ENCODE_3D) *bytes = (size_t)scan_tiles(nitems) * sizeof(int32_t);
+    else if (fn < FSMI_FN_EVAL_2D || fn > FSMI_FN_EVAL_3D) return FSMI_ERR_ARG;
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_device_status(fsmi_stream_t stream, int *status)
+{
+    if (!status) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, sp, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sp, 0, sizeof(int), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *status = v;
+    return FSMI_OK;
+}
+
+const char *fsmi_status_str(fsmi_status s)
+{
+    switch (s) {
+        case FSMI_OK: return "ok";
+        case FSMI_ERR_ARG: return "invalid argument";
+        case FSMI_ERR_CAPACITY: return "size exceeds a documented maximum";
+        case FSMI_ERR_CUDA: return "CUDA error";
+        case FSMI_ERR_TIMEOUT: return "device wait timed out";
+        case FSMI_ERR_WORKSPACE: return "workspace too small";
+        default: return "unknown status";
+    }
+}
+
+int fsmi_last_cuda_error(void) { return g_last_cuda; }
+
+int fsmi_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+"""GPU parity of the 2D path (fsmi_trace_2d, fsmi_eval_beams, fsmi_eval_2d) against the FP64
+oracle, through the C ABI. Cell lists bit for bit; MI within the tolerance of tests/parity.py."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1905_02238_gb300 import fsmi, synth
+from tests.parity import assert_mi_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_1905_02238_gb300 import build
+
+    build.build()
+    oracle.build()
+    return fsmi.load()
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _variants():
+    return [
+        dict(variant=fsmi.EXACT),
+        dict(variant=fsmi.APPROX, trunc_delta=0),
+        dict(variant=fsmi.APPROX, trunc_delta=3),
+        dict(variant=fsmi.APPROX, trunc_delta=6),
+        dict(variant=fsmi.UNIFORM, uniform_h=0),
+        dict(variant=fsmi.UNIFORM, uniform_h=2),
+        dict(variant=fsmi.UNIFORM, uniform_h=4),
+    ]
+
+
+def _prms(sigma, R, e0=0, **kw):
+    base = dict(sigma=sigma, delta_occ=1.5, delta_emp=0.67, max_range=R, e0_mode=e0)
+    base.update(kw)
+    return fsmi.Params(**base), oracle.Params(**base)
+
+
+# ---- traversal ------------------------------------------------------------------------------------
+
+def _trace_compare(W, H, poses, dirs, R):
+    cap = int(R * 1.5) + 4
+    cells, l, n = fsmi.trace_2d(W, H, _cuda(poses), _cuda(dirs), R, cap)
+    cells, l, n = cells.cpu().numpy(), l.cpu().numpy(), n.cpu().numpy()
+    B = dirs.shape[0]
+    for i in range(poses.shape[0] * B):
+        p, b = divmod(i, B)
+        d = oracle.beam_dir_2d(poses[p], dirs[b])
+        rc, rl = oracle.trace_2d(W, H, int(poses[p, 0]), int(poses[p, 1]), int(d[0]), int(d[1]), R, cap)
+        assert n[i] == len(rc), (i, n[i], len(rc))
+        np.testing.assert_array_equal(cells[i, :n[i]], rc)
+        np.testing.assert_allclose(l[i, :n[i] + 1], rl, rtol=3e-7, atol=1e-6)
+
+
+def test_trace_config1_bit_exact():
+    grid, poses, dirs = synth.config1()
+    _trace_compare(200, 200, poses, dirs, 64.0)
+
+
+def test_trace_random_poses_bit_exact():
+    rng = np.random.default_rng(40)
+    W, H = 61, 47
+    poses = []
+    for k in range(24):
+        x = rng.integers(0, W * 65536) if k % 3 else rng.integers(0, W) * 65536  # some on grid lines
+        y = rng.integers(0, H * 65536) if k % 4 else rng.integers(0, H) * 65536
+        yaw = rng.uniform(0, 2 * np.pi) if k % 5 else 0.0
+        p = synth.pose_2d(0, 0, yaw)
+        p[0], p[1] = x, y
+        poses.append(p)
+    poses = np.stack(poses)
+    dirs = np.concatenate([synth.beam_dirs_2d(72), synth.random_dirs_2d(40, rng)])
+    _trace_compare(W, H, poses, dirs, 40.5)
+
+
+def test_trace_office_map_sampled():
+    grid, poses, dirs = synth.config2(n_poses=16, size=512)
+    _trace_compare(512, 512, poses, dirs, 256.0)
+
+
+# ---- explicit beams ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("sigma", [0.5, 1.5, 2.0, 5.0])
+@pytest.mark.parametrize("e0", [0, 1])
+def test_eval_beams_all_variants(sigma, e0):
+    off, o, l, lend = synth.random_beams(300, 0, 420, seed=int(sigma * 10) + e0)
+    for kw in _variants():
+        gp, op = _prms(sigma, 64.0, e0, **kw)
+        got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
+        ref = oracle.eval_beams(off, o, l, lend, op)
+        assert_mi_close(got, ref, f"beams {kw} sigma={sigma} e0={e0}")
+
+
+def test_eval_beams_edge_cases():
+    # empty beams, single cells, known cells (o in {0, 1}), tiny and wide cells, long beams
+    rng = np.random.default_rng(41)
+    beams = [np.zeros(0), np.array([0.5]), np.array([0.0]), np.array([1.0]), rng.integers(0, 2, 50).astype(float),
+             rng.uniform(0, 1, 1000), np.full(700, 0.1), np.full(64, 0.999)]
+    widths = [np.zeros(0), np.array([1.0]), np.array([0.3]), np.array([2.0]), rng.uniform(0.01, 1.4, 50),
+              rng.uniform(0.001, 1.4, 1000), np.ones(700), rng.uniform(0.5, 1.5, 64)]
+    off = np.concatenate([[0], np.cumsum([len(b) for b in beams])]).astype(np.int32)
+    o = np.concatenate(beams).astype(np.float32)
+    l = np.concatenate([np.concatenate([[0.0], np.cumsum(w)])[:-1] for w in widths]).astype(np.float32)
+    lend = np.array([np.sum(w) for w in widths], np.float32)
+    for kw in _variants():
+        for e0 in (0, 1):
+            gp, op = _prms(1.5, 64.0, e0, **kw)
+            got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
+            ref = oracle.eval_beams(off, o, l, lend, op)
+            assert_mi_close(got, ref, f"edge {kw} e0={e0}")
+            assert got[0] == 0.0 and abs(got[4]) <= 1e-7
+
+
+# ---- full 2D path -----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("e0", [0, 1])
+def test_eval_2d_config1(e0):
+    grid, poses, dirs = synth.config1()
+    for kw in _variants():
+        gp, op = _prms(1.5, 64.0, e0, **kw)
+        got = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy()
+        ref = oracle.eval_2d(grid, poses, dirs, op)
+        assert_mi_close(got, ref, f"config1 {kw}")
+
+
+def test_eval_2d_office_midsize():
+    grid, poses, dirs = synth.config2(n_poses=12, size=512)
+    for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
+        gp, op = _prms(2.0, 256.0, 0, **kw)
+        got = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy()
+        ref = oracle.eval_2d(grid, poses, dirs, op)
+        assert_mi_close(got, ref, f"office512 {kw}")
+
+
+def test_eval_2d_config2_full_size_sampled():
+    # the benchmark's launch: 2048^2 map, 1024 poses x 360 beams, R = 256, sigma = 2; the oracle
+    # checks every beam of four poses spread over the batch
+    grid, poses, dirs = synth.config2()
+    rows = [0, 341, 682, 1023]
+    for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
+        gp, op = _prms(2.0, 256.0, 0, **kw)
+        got = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy()
+        assert got.shape == (1024, 360) and np.all(np.isfinite(got))
+        ref = oracle.eval_2d(grid, poses[rows], dirs, op)
+        assert_mi_close(got[rows], ref, f"config2 {kw}")
+    assert fsmi.device_status() == 0
+
+
+def test_eval_2d_long_beams():
+    # R = 1024 cells: beams of up to ~1450 cells take several register-blocked passes
+    grid = synth.office_grid(2048, seed=5)
+    poses = synth.free_cell_poses_2d(grid, 3, seed=6, margin=700)
+    dirs = synth.beam_dirs_2d(24)
+    for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
+        gp, op = _prms(2.0, 1024.0, 1, **kw)
+        got = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy()
+        ref = oracle.eval_2d(grid, poses, dirs, op)
+        assert_mi_close(got, ref, f"long {kw}")
+
+
+def test_eval_2d_host_buffers_match_device():
+    grid, poses, dirs = synth.config1()
+    gp, _ = _prms(1.5, 64.0)
+    dev = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu()
+    host = fsmi.eval_2d(torch.from_numpy(grid).pin_memory(), torch.from_numpy(poses).pin_memory(),
+                        torch.from_numpy(dirs).pin_memory(), gp)
+    assert not host.is_cuda
+    assert torch.equal(dev, host)
+
+
+def test_invalid_arguments_launch_nothing():
+    grid, poses, dirs = synth.config1()
+    out = torch.full((1, 360), 7.0, device="cuda")
+    for bad in (dict(sigma=0.0), dict(sigma=float("nan")), dict(delta_occ=-1.0), dict(max_range=2000.0),
+                dict(variant=7), dict(e0_mode=3)):
+        gp, _ = _prms(1.5, 64.0)
+        for k, v in bad.items():
+            setattr(gp, k, v)
+        with pytest.raises(fsmi.FsmiError):
+            fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp, out=out)
+    torch.cuda.synchronize()
+    assert torch.all(out == 7.0)
+    # an empty batch is a no-op
+    gp, _ = _prms(1.5, 64.0)
+    assert fsmi.eval_2d(_cuda(grid), _cuda(poses[:0]), _cuda(dirs), gp).shape == (0, 360)
+
+
+def test_bad_explicit_beam_sets_status():
+    off = np.array([0, 3000], np.int32)  # longer than FSMI_MAX_CELLS
+    o = np.full(3000, 0.5, np.float32)
+    l = np.arange(3000, dtype=np.float32)
+    lend = np.array([3000.0], np.float32)
+    gp, _ = _prms(1.5, 64.0)
+    fsmi.device_status()
+    got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
+    assert np.isnan(got[0])
+    assert fsmi.device_status() & fsmi.STATUS_BAD_BEAM
+    assert fsmi.device_status() == 0
