@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsmi.so")
 SOURCES = ["fsmi_api.cu", "fsmi_2d.cu", "fsmi_rle.cu"]
-HEADERS = ["fsmi_internal.h", "fsmi_device.cuh"]
+HEADERS = ["fsmi_internal.h", "fsmi_device.cuh", "gauss_tail.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

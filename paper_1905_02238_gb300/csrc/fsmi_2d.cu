@@ -4,18 +4,19 @@
 // Per beam (Section 3): the traversal lists the cells the beam crosses with entry distances
 // l_1 = 0 < l_2 < ... and end l_{n+1}; Algorithm 2 gives P(e_j) = o_j prod_{i<j}(1 - o_i);
 // Algorithm 3 gives C_k = sum_{i<k} f(delta_emp, r_i) + f(delta_occ, r_k); the variant then sums
-//   FSMI (Theorem 1):      sum_j P(e_j) sum_{k=1..n} C_k G_{k,j}
+//   FSMI (Theorem 1):         sum_j P(e_j) sum_{k=1..n} C_k G_{k,j}
 //   Approx (eq. fsmi_approx): the same with |k - j| <= Delta
-//   Uniform (Algorithm 4): sum_j P(e_j) (D_{min(n,j+H)} - D_{max(0,j-H-1)}) / (2H + 1)
+//   Uniform (Algorithm 4):    sum_j P(e_j) (D_{min(n,j+H)} - D_{max(0,j-H-1)}) / (2H + 1)
 //
-// The Gaussian pair sum is evaluated per first-hit cell j in the boundary form
+// The Gaussian pair sum is evaluated per first-hit cell j in boundary form (summation by parts):
 //   S_j = sum_k C_k (Phi(x_{k+1}) - Phi(x_k)) = C_j + sum_{m=1}^{n+1} (C_m - C_{m-1}) sgn(x_m) T(|x_m|)
-// with x_m = (l_m - mu_j) / sigma, C_0 = C_{n+1} = 0 and T the upper Gaussian tail. This is the
-// same sum regrouped by boundary (summation by parts); every term is a tail mass, so no
-// difference of two values near 1 is ever formed in FP32.
+// with x_m = (l_m - mu_j) / sigma, C_0 = C_{n+1} = 0 and T the upper Gaussian tail. Every term is
+// a tail mass, so no difference of two values near 1 is formed in FP32, and each (j, m) pair costs
+// one tail evaluation (gauss_tail.cuh) instead of the two Phi values of G_{k,j}.
 #include "../../include/fsmi.h"
 #include "fsmi_device.cuh"
 #include "fsmi_internal.h"
+#include "gauss_tail.cuh"
 
 namespace fsmi {
 
@@ -28,70 +29,157 @@ __device__ __forceinline__ void beam_dir(const int32_t *pose, int32_t ux, int32_
     dy = (int)((s * ux + c * uy + (1LL << 29)) >> 30);
 }
 
-// Integer traversal of one beam. Origin (ox, oy) in Q16 cell units, direction (dx, dy) in Q30.
-// The beam's distance parameter is lambda in o + lambda * d / 2^30. The first cell is the one
-// entered by o + eps * d; a cell is appended while its entry lambda is < R (rfix = R * 2^16) and it
-// lies inside the W x H grid. Crossings are ordered by exact int64 comparison of
-// nx / |dx| versus ny / |dy| (nx, ny: Q16 distances from the origin to the next x / y boundary); a
-// tie is one diagonal step. Writes cells[0..n-1], l[0..n] (l[n] = min(R, grid exit)) and returns n,
-// or -1 if the beam has more than cap cells.
-__device__ int dda_2d(int W, int H, int ox, int oy, int dx, int dy, long long rfix, int cap, int *cells,
-                      float *l)
+// ---- traversal ----------------------------------------------------------------------------------
+//
+// The beam is o + lambda * d / 2^30 (o in Q16 cell units, d in Q30); lambda is its distance. Cells
+// change at x crossings lambda_x(a) = (nx0 + a 2^16) 2^14 / |dx| and y crossings likewise, with
+// nx0, ny0 the Q16 distances from o to the far side of the first cell (the cell entered by
+// o + eps d). Crossings are ordered by exact int64 comparison; coinciding crossings are one
+// diagonal step. A cell is entered while its entry lambda < R and it lies inside the grid.
+//
+// Parallel form: along the major axis M (|d_M| >= |d_m|) consecutive M-crossings split the beam
+// into intervals [lambda_M(k), lambda_M(k+1)), k = -1, 0, 1, ... (lambda_M(-1) = 0). Minor
+// crossings are at least as far apart as major ones, so each interval holds the cell entered at
+// its start plus at most one cell entered at a minor crossing strictly inside it. Lane L walks a
+// contiguous block of intervals; its starting minor coordinate is the number of minor crossings
+// at or before lambda_M(k0) (one integer division). A warp scan of per-lane cell counts places the
+// cells; the first lane that meets the range limit or the grid boundary ends the beam.
+
+struct Geo {
+    int sM, sm, cM0, cm0, dimM, dimm, xmaj, W;
+    long long nM0, nm0, aM, am, LM, Lm;
+    float rM, rm, R;
+};
+
+__device__ __forceinline__ long long minor_before(const Geo &g, int k)
 {
+    if (g.am == 0 || k < 0) return 0;
+    const long long num = (g.nM0 + (long long)k * 65536) * g.am - g.nm0 * g.aM;
+    return num < 0 ? 0 : num / (65536LL * g.aM) + 1;
+}
+
+template <bool WRITE>
+__device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int base, int cap, int *ids, float *l, int &cnt,
+                                     bool &ended, float &endl)
+{
+    int cM = g.cM0 + g.sM * (k0 + 1);
+    long long i = minor_before(g, k0);
+    int cm = g.cm0 + g.sm * (int)i;
+    cnt = 0;
+    ended = false;
+    endl = 0.0f;
+#define FSMI_EMIT(lam_)                                                              \
+    do {                                                                             \
+        if (WRITE) {                                                                 \
+            const int pos_ = base + cnt;                                             \
+            if (pos_ < cap) {                                                        \
+                ids[pos_] = g.xmaj ? (cm * g.W + cM) : (cM * g.W + cm);              \
+                l[pos_] = (lam_);                                                    \
+            }                                                                        \
+        }                                                                            \
+        ++cnt;                                                                       \
+    } while (0)
+    for (int k = k0; k <= k1; ++k) {
+        FSMI_EMIT(k < 0 ? 0.0f : (float)(g.nM0 + (long long)k * 65536) * g.rM);
+        const long long nMn = g.nM0 + (long long)(k + 1) * 65536;  // next major crossing
+        long long nmi = g.nm0 + i * 65536;                          // next minor crossing
+        if (g.am && nmi * g.aM < nMn * g.am) {                     // minor crossing inside
+            if (nmi >= g.Lm) {
+                ended = true;
+                endl = g.R;
+                break;
+            }
+            cm += g.sm;
+            if ((unsigned)cm >= (unsigned)g.dimm) {
+                ended = true;
+                endl = (float)nmi * g.rm;
+                break;
+            }
+            FSMI_EMIT((float)nmi * g.rm);
+            ++i;
+            nmi += 65536;
+        }
+        if (nMn >= g.LM) {
+            ended = true;
+            endl = g.R;
+            break;
+        }
+        const bool tie = g.am && (nmi * g.aM == nMn * g.am);
+        cM += g.sM;
+        if (tie) {
+            cm += g.sm;
+            ++i;
+        }
+        if ((unsigned)cM >= (unsigned)g.dimM || (unsigned)cm >= (unsigned)g.dimm) {
+            ended = true;
+            endl = (float)nMn * g.rM;
+            break;
+        }
+    }
+#undef FSMI_EMIT
+}
+
+// All 32 lanes call this. Writes ids[0..n-1] (cell y*W + x) and l[0..n] (entry distances, then
+// the end distance) and returns n; returns -1 (writing nothing) if the beam has more than cap
+// cells. rend = R as float.
+__device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, long long rfix, float rend, int cap, int *ids,
+                        float *l)
+{
+    const int lane = lane_id();
     if ((dx | dy) == 0) return 0;
     int cx = ox >> 16, cy = oy >> 16;
     if (dx < 0 && (ox & 0xFFFF) == 0) --cx;
     if (dy < 0 && (oy & 0xFFFF) == 0) --cy;
     if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) return 0;
-    const long long adx = dx < 0 ? -(long long)dx : dx;
-    const long long ady = dy < 0 ? -(long long)dy : dy;
-    const int sx = dx > 0 ? 1 : -1, sy = dy > 0 ? 1 : -1;
-    long long nx = dx > 0 ? ((long long)(cx + 1) << 16) - ox : (long long)ox - ((long long)cx << 16);
-    long long ny = dy > 0 ? ((long long)(cy + 1) << 16) - oy : (long long)oy - ((long long)cy << 16);
-    const double rx = adx ? 16384.0 / (double)adx : 0.0;
-    const double ry = ady ? 16384.0 / (double)ady : 0.0;
-    if (cap < 1) return -1;
-    cells[0] = cy * W + cx;
-    l[0] = 0.0f;
-    int n = 1;
-    for (;;) {
-        bool stx, sty;
-        if (dx == 0) {
-            stx = false;
-            sty = true;
-        } else if (dy == 0) {
-            stx = true;
-            sty = false;
-        } else {
-            const long long tx = nx * ady, ty = ny * adx;
-            stx = tx <= ty;
-            sty = ty <= tx;
-        }
-        const long long num = stx ? nx : ny, den = stx ? adx : ady;
-        if ((num << 30) >= rfix * den) {
-            l[n] = (float)((double)rfix * (1.0 / 65536.0));
-            break;
-        }
-        const float lam = (float)((double)num * (stx ? rx : ry));
-        if (stx) {
-            cx += sx;
-            nx += 65536;
-        }
-        if (sty) {
-            cy += sy;
-            ny += 65536;
-        }
-        if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) {
-            l[n] = lam;
-            break;
-        }
-        if (n >= cap) return -1;
-        cells[n] = cy * W + cx;
-        l[n] = lam;
-        ++n;
-    }
+    const long long adx = dx < 0 ? -(long long)dx : dx, ady = dy < 0 ? -(long long)dy : dy;
+    Geo g;
+    g.xmaj = adx >= ady;
+    g.W = W;
+    g.aM = g.xmaj ? adx : ady;
+    g.am = g.xmaj ? ady : adx;
+    const int dM = g.xmaj ? dx : dy, dm = g.xmaj ? dy : dx;
+    g.sM = dM > 0 ? 1 : -1;
+    g.sm = dm > 0 ? 1 : -1;
+    g.cM0 = g.xmaj ? cx : cy;
+    g.cm0 = g.xmaj ? cy : cx;
+    g.dimM = g.xmaj ? W : H;
+    g.dimm = g.xmaj ? H : W;
+    const long long oM = g.xmaj ? ox : oy, om = g.xmaj ? oy : ox;
+    g.nM0 = g.sM > 0 ? ((long long)(g.cM0 + 1) << 16) - oM : oM - ((long long)g.cM0 << 16);
+    g.nm0 = g.am == 0 ? 0 : (g.sm > 0 ? ((long long)(g.cm0 + 1) << 16) - om : om - ((long long)g.cm0 << 16));
+    // crossing numerators below these limits have entry lambda < R:
+    //   num * 2^30 < rfix * a  <=>  num < floor((rfix * a - 1) / 2^30) + 1
+    g.LM = ((rfix * g.aM - 1) >> 30) + 1;
+    g.Lm = g.am ? ((rfix * g.am - 1) >> 30) + 1 : 0;
+    g.rM = 16384.0f / (float)g.aM;
+    g.rm = g.am ? 16384.0f / (float)g.am : 0.0f;
+    g.R = rend;
+    // major crossings that stay in range and inside the grid along M
+    const long long KR = g.LM > g.nM0 ? (g.LM - g.nM0 + 65535) >> 16 : 0;
+    const long long KG = g.sM > 0 ? (g.dimM - 1 - g.cM0) : g.cM0;
+    const int K = (int)(KR < KG ? KR : KG);
+    const int NI = K + 1;  // intervals k = -1 .. K-1
+    const int q = (NI + 31) >> 5;
+    const int k0 = -1 + lane * q;
+    const int k1 = min(K - 1, k0 + q - 1);
+    int cnt = 0;
+    bool ended = false;
+    float endl = 0.0f;
+    if (k0 <= k1) walk<false>(g, k0, k1, 0, cap, ids, l, cnt, ended, endl);
+    const unsigned eb = __ballot_sync(kFull, ended);
+    const int first = eb ? __ffs(eb) - 1 : 31;
+    const int c = lane <= first ? cnt : 0;
+    const int inc = warp_incl_add_int(c);
+    const int n = __shfl_sync(kFull, inc, 31);
+    const float lend = __shfl_sync(kFull, endl, first);
+    if (n > cap) return -1;
+    if (lane <= first && k0 <= k1) walk<true>(g, k0, k1, inc - c, cap, ids, l, cnt, ended, endl);
+    if (lane == 0) l[n] = lend;
+    __syncwarp();
     return n;
 }
+
+// ---- pair sums ------------------------------------------------------------------------------------
 
 struct Src2D {
     // map source
@@ -108,19 +196,19 @@ struct Src2D {
     const float *lend;
 };
 
-// One register-blocked pass of the exact pair sum: each lane owns J first-hit slots
-// j = jb + lane + 32 t and streams every boundary m = 0..n from shared memory. Slot n is the
-// no-return event when e0 is set (centre l_1 - 1/2, C_0 = 0).
+// One register-blocked pass of the exact pair sum over scaled distances: each lane owns J
+// first-hit slots j = jb + lane + 32 t and streams every boundary m = 0..n from shared memory.
+// Slot n is the no-return event when e0 is set (centre mu0, C_0 = 0).
 template <int J>
 __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, const float *sp, int n, int jb,
-                                            bool e0, float pe0, float inv_s2)
+                                            bool e0, float pe0, float mu0)
 {
     const int lane = lane_id();
     float mu[J], acc[J];
 #pragma unroll
     for (int t = 0; t < J; ++t) {
         const int j = jb + lane + 32 * t;
-        mu[t] = (j < n) ? 0.5f * (sl[j] + sl[j + 1]) : ((j == n && e0) ? sl[0] - 0.5f : 3.0e30f);
+        mu[t] = (j < n) ? 0.5f * (sl[j] + sl[j + 1]) : ((j == n && e0) ? mu0 : 3.0e30f);
         acc[t] = 0.0f;
     }
     float cprev = 0.0f;
@@ -130,11 +218,7 @@ __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, co
         const float dc = cm - cprev;
         cprev = cm;
 #pragma unroll
-        for (int t = 0; t < J; ++t) {
-            const float d = lm - mu[t];
-            const float T = half_erfc(fabsf(d) * inv_s2);
-            acc[t] = fmaf(copysignf(dc, d), T, acc[t]);
-        }
+        for (int t = 0; t < J; ++t) acc[t] = fmaf(dc, signed_tail(lm - mu[t]), acc[t]);
     }
     float r = 0.0f;
 #pragma unroll
@@ -149,7 +233,7 @@ __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, co
 }
 
 __device__ __forceinline__ float exact_sum(const float *sl, const float *sc, const float *sp, int n, bool e0,
-                                           float pe0, float inv_s2)
+                                           float pe0, float mu0)
 {
     const int nslots = n + (e0 ? 1 : 0);
     float r = 0.0f;
@@ -157,7 +241,7 @@ __device__ __forceinline__ float exact_sum(const float *sl, const float *sc, con
         const int cnt = min(16, (nslots - jb + 31) >> 5);
         switch (cnt) {
 #define FSMI_CASE(J) \
-    case J: r += exact_pass<J>(sl, sc, sp, n, jb, e0, pe0, inv_s2); break;
+    case J: r += exact_pass<J>(sl, sc, sp, n, jb, e0, pe0, mu0); break;
             FSMI_CASE(1) FSMI_CASE(2) FSMI_CASE(3) FSMI_CASE(4) FSMI_CASE(5) FSMI_CASE(6) FSMI_CASE(7) FSMI_CASE(8)
             FSMI_CASE(9) FSMI_CASE(10) FSMI_CASE(11) FSMI_CASE(12) FSMI_CASE(13) FSMI_CASE(14) FSMI_CASE(15)
             FSMI_CASE(16)
@@ -171,7 +255,7 @@ __device__ __forceinline__ float exact_sum(const float *sl, const float *sc, con
 // Approx-FSMI: for slot j the band k in [klo, khi] = [j - Delta, j + Delta] n [0, n-1] (0-based),
 // i.e. boundaries m in [klo, khi + 1] with C' = C on the band and 0 outside it.
 __device__ __forceinline__ float approx_sum(const float *sl, const float *sc, const float *sp, int n, bool e0,
-                                            float pe0, float inv_s2, int D)
+                                            float pe0, float mu0, int D)
 {
     const int nslots = n + (e0 ? 1 : 0);
     float r = 0.0f;
@@ -185,7 +269,7 @@ __device__ __forceinline__ float approx_sum(const float *sl, const float *sc, co
             klo = max(0, j - D);
             khi = min(n - 1, j + D);
         } else {  // e_0 at virtual index 0: paper band k in [1, Delta]
-            mu = sl[0] - 0.5f;
+            mu = mu0;
             Cj = 0.0f;
             Pj = pe0;
             klo = 0;
@@ -195,8 +279,7 @@ __device__ __forceinline__ float approx_sum(const float *sl, const float *sc, co
         for (int m = klo; m <= khi + 1; ++m) {
             const float cm = (m <= khi) ? sc[m] : 0.0f;
             const float cm1 = (m > klo) ? sc[m - 1] : 0.0f;
-            const float d = sl[m] - mu;
-            acc = fmaf(copysignf(cm - cm1, d), half_erfc(fabsf(d) * inv_s2), acc);
+            acc = fmaf(cm - cm1, signed_tail(sl[m] - mu), acc);
         }
         r = fmaf(Pj, Cj + acc, r);
     }
@@ -278,19 +361,16 @@ __global__ void __launch_bounds__(kWarps2D * 32)
     float *sp = sc + stride;
     float *sx = sp + stride;
     const bool e0 = p.e0 != 0;
+    const float cs = p.inv_s2 * (float)kSqrtLog2e;  // distance -> tail variable
     for (long long beam = (long long)blockIdx.x * kWarps2D + warp; beam < nbeams;
          beam += (long long)gridDim.x * kWarps2D) {
         int n;
         if (FROM_MAP) {
             const int pi = (int)(beam / src.B), bi = (int)(beam % src.B);
-            if (lane == 0) {
-                const int32_t *pose = src.poses + 4 * (size_t)pi;
-                int dx, dy;
-                beam_dir(pose, src.dirs[2 * bi], src.dirs[2 * bi + 1], dx, dy);
-                n = dda_2d(src.W, src.H, pose[0], pose[1], dx, dy, p.rfix, p.nmax, (int *)sx, sl);
-            }
-            n = __shfl_sync(kFull, n, 0);
-            __syncwarp();
+            const int32_t *pose = src.poses + 4 * (size_t)pi;
+            int dx, dy;
+            beam_dir(pose, src.dirs[2 * bi], src.dirs[2 * bi + 1], dx, dy);
+            n = dda_warp(src.W, src.H, pose[0], pose[1], dx, dy, p.rfix, p.rend, p.nmax, (int *)sx, sl);
             if (n < 0) {
                 if (lane == 0) {
                     out[beam] = __int_as_float(0x7fc00000);
@@ -327,11 +407,15 @@ __global__ void __launch_bounds__(kWarps2D * 32)
         __syncwarp();
         float I = 0.0f;
         if (n > 0) {
+            if (VAR != FSMI_UNIFORM) {
+                for (int i = lane; i <= n; i += 32) sl[i] *= cs;
+            }
             const float pe0 = cell_prefixes(sp, sc, sx, n, VAR == FSMI_UNIFORM);
+            const float mu0 = sl[0] - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
             if (VAR == FSMI_EXACT)
-                I = exact_sum(sl, sc, sp, n, e0, pe0, p.inv_s2);
+                I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
             else if (VAR == FSMI_APPROX)
-                I = approx_sum(sl, sc, sp, n, e0, pe0, p.inv_s2, p.trunc);
+                I = approx_sum(sl, sc, sp, n, e0, pe0, mu0, p.trunc);
             else
                 I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
             I = warp_sum(I);
@@ -341,18 +425,28 @@ __global__ void __launch_bounds__(kWarps2D * 32)
     }
 }
 
-__global__ void k_trace_2d(int W, int H, const int32_t *__restrict__ poses, const int32_t *__restrict__ dirs, int B,
-                           long long nbeams, long long rfix, int cap, int32_t *__restrict__ cells, float *__restrict__ l,
-                           int32_t *__restrict__ nout)
+__global__ void __launch_bounds__(128)
+    k_trace_2d(int W, int H, const int32_t *__restrict__ poses, const int32_t *__restrict__ dirs, int B,
+               long long nbeams, long long rfix, float rend, int cap, int32_t *__restrict__ cells,
+               float *__restrict__ l, int32_t *__restrict__ nout)
 {
-    for (long long beam = (long long)blockIdx.x * blockDim.x + threadIdx.x; beam < nbeams;
-         beam += (long long)gridDim.x * blockDim.x) {
+    const int warp = threadIdx.x >> 5;
+    for (long long beam = (long long)blockIdx.x * 4 + warp; beam < nbeams; beam += (long long)gridDim.x * 4) {
         const int pi = (int)(beam / B), bi = (int)(beam % B);
         const int32_t *pose = poses + 4 * (size_t)pi;
         int dx, dy;
         beam_dir(pose, dirs[2 * bi], dirs[2 * bi + 1], dx, dy);
-        nout[beam] = dda_2d(W, H, pose[0], pose[1], dx, dy, rfix, cap, cells + beam * cap, l + beam * (cap + 1));
+        const int n = dda_warp(W, H, pose[0], pose[1], dx, dy, rfix, rend, cap, cells + beam * cap,
+                               l + beam * (cap + 1));
+        if (lane_id() == 0) nout[beam] = n;
     }
+}
+
+// Scaled Gaussian tail over an array (exposed for testing the numerical core).
+__global__ void k_gauss_tail(const float *__restrict__ s, float *__restrict__ out, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = gauss_tail(s[i]);
 }
 
 template <int VAR, bool FROM_MAP>
@@ -403,14 +497,24 @@ cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l
 }
 
 cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,
-                            int cap, int32_t *cells, float *l, int32_t *n, cudaStream_t s)
+                            float rend, int cap, int32_t *cells, float *l, int32_t *n, cudaStream_t s)
 {
     const long long nb = (long long)P * B;
     if (nb <= 0) return cudaSuccess;
-    long long grid = (nb + 127) / 128;
+    long long grid = (nb + 3) / 4;
     const long long gmax = (long long)sm_count() * 16;
     if (grid > gmax) grid = gmax;
-    k_trace_2d<<<(unsigned)grid, 128, 0, s>>>(W, H, poses, dirs, B, nb, rfix, cap, cells, l, n);
+    k_trace_2d<<<(unsigned)grid, 128, 0, s>>>(W, H, poses, dirs, B, nb, rfix, rend, cap, cells, l, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_tail(const float *sv, float *out, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long grid = (n + 255) / 256;
+    const long long gmax = (long long)sm_count() * 8;
+    if (grid > gmax) grid = gmax;
+    k_gauss_tail<<<(unsigned)grid, 256, 0, s>>>(sv, out, n);
     return cudaGetLastError();
 }
 

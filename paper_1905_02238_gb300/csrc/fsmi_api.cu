@@ -79,10 +79,12 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     d.g_kernel = prm->g_kernel;
     d.approx_reading = prm->approx_reading;
     d.rfix = 0;
+    d.rend = 0.0f;
     d.K = 0;
     if (use == kUse2D) {
         if (prm->max_range > FSMI_MAX_RANGE_2D) return FSMI_ERR_CAPACITY;
         d.rfix = llrint((double)prm->max_range * 65536.0);
+        d.rend = (float)((double)d.rfix / 65536.0);
         // a segment of length R crosses at most R(|cos| + |sin|) + 2 <= R sqrt(2) + 2 cells
         d.nmax = (int)((double)prm->max_range * 1.41421357) + 3;
     } else if (use == kUseBeams) {
@@ -166,7 +168,8 @@ fsmi_status fsmi_trace_2d(int W, int H, const int32_t *poses, int P, const int32
     if ((long long)P * B == 0) return FSMI_OK;
     if (!poses || !dirs || !cells || !l || !n) return FSMI_ERR_ARG;
     const long long rfix = llrint((double)max_range * 65536.0);
-    cudaError_t e = launch_trace_2d(W, H, poses, P, dirs, B, rfix, cap, cells, l, n, (cudaStream_t)stream);
+    cudaError_t e = launch_trace_2d(W, H, poses, P, dirs, B, rfix, (float)((double)rfix / 65536.0), cap, cells, l, n,
+                                    (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -227,6 +230,15 @@ fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *p
     if (!sp) return cuda_fail(cudaGetLastError());
     Vox3D v{vox, X, Y, Z, poses, P, dirs, R};
     cudaError_t e = launch_eval_3d(v, d, out, nruns, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_gauss_tail(const float *s, float *out, long long n, fsmi_stream_t stream)
+{
+    if (n < 0) return FSMI_ERR_ARG;
+    if (n == 0) return FSMI_OK;
+    if (!s || !out) return FSMI_ERR_ARG;
+    cudaError_t e = launch_gauss_tail(s, out, n, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 

@@ -16,6 +16,7 @@ struct DevParams {
     int H;              // uniform half-width
     float inv_2h1;      // 1 / (2H + 1)
     long long rfix;     // round(max_range * 2^16), 2D range limit in Q16
+    float rend;         // rfix / 2^16 as float: the end distance of a beam cut by the range
     int nmax;           // per-beam capacity: cells (2D) or virtual cells (3D)
     int e0;             // e0_mode
     int run_cap;        // RLE split length
@@ -33,7 +34,8 @@ cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses,
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                               const DevParams &p, float *out, int *status, cudaStream_t s);
 cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,
-                            int cap, int32_t *cells, float *l, int32_t *n, cudaStream_t s);
+                            float rend, int cap, int32_t *cells, float *l, int32_t *n, cudaStream_t s);
+cudaError_t launch_gauss_tail(const float *s, float *out, long long n, cudaStream_t st);
 
 // 3D / RLE (fsmi_rle.cu)
 struct Vox3D {

@@ -97,6 +97,7 @@ def load():
             "fsmi_eval_3d": [p, i, i, i, p, i, p, i, P, p, p, p],
             "fsmi_workspace_size": [i, ll, P, ctypes.POINTER(ctypes.c_size_t)],
             "fsmi_device_status": [p, ctypes.POINTER(ctypes.c_int)],
+            "fsmi_gauss_tail": [p, p, ll, p],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -264,6 +265,16 @@ def eval_3d(vox, poses, dirs, prm: Params, out=None, with_runs: bool = False):
                             _stream()), "fsmi_eval_3d")
     if with_runs:
         return m.out(out), m.out(nr)
+    return m.out(out)
+
+
+def gauss_tail(s: torch.Tensor) -> torch.Tensor:
+    """fsmi_gauss_tail: 0.5 * erfc(s / sqrt(log2 e)) elementwise (float32 CUDA tensor)."""
+    lib = load()
+    m = _Marshal(s)
+    s = m.arg(s, torch.float32, "s")
+    out = torch.empty_like(s)
+    _raise(lib.fsmi_gauss_tail(_ptr(s), _ptr(out), s.numel(), _stream()), "fsmi_gauss_tail")
     return m.out(out)
 
 

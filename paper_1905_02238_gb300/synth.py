@@ -154,6 +154,8 @@ def free_voxel_poses(vox: np.ndarray, n: int, seed: int = 3, zlo: int = 32, zhi:
     zlo, zhi = min(zlo, Z - 1), min(zhi, Z)
     sub = vox[zlo:zhi]
     zs, ys, xs = np.nonzero(sub == np.float32(0.1))
+    if len(xs) == 0:
+        raise ValueError("no free (o == 0.1) voxel in the requested height band")
     idx = rng.choice(len(xs), size=n, replace=len(xs) < n)
     yaws = rng.uniform(0.0, 2.0 * math.pi, n)
     return np.stack([pose_3d(xs[i] + 0.5, ys[i] + 0.5, zs[i] + zlo + 0.5, yaws[k], 0.0)

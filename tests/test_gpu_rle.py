@@ -192,7 +192,7 @@ def test_eval_3d_config3_full_size_sampled():
 
 
 def test_fused_equals_encode_then_eval():
-    vox, poses, dirs = _small_world(4)
+    vox, poses, dirs = _small_world(5)
     for kw in _rle_variants()[:6]:
         gp, _ = _prms(max_range=80.0, run_cap=16, **kw)
         fused = fsmi.eval_3d(_cuda(vox), _cuda(poses), _cuda(dirs), gp).reshape(-1)
