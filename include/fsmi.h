@@ -63,6 +63,7 @@ typedef enum { FSMI_G_PDF = 0, FSMI_G_ERF = 1 } fsmi_kernel;
 #define FSMI_STATUS_BEAM_OVERFLOW 0x1  /* a beam had more cells than its capacity: its MI is NaN */
 #define FSMI_STATUS_RUN_OVERFLOW 0x2   /* RLE output exceeded run_capacity: runs were truncated */
 #define FSMI_STATUS_BAD_BEAM 0x4       /* an explicit beam or ray exceeded the per-beam maximum */
+#define FSMI_STATUS_INTERNAL 0x8       /* a traversal produced a cell outside the map (library bug) */
 
 typedef struct {
     int variant;        /* fsmi_variant */

@@ -379,12 +379,17 @@ __global__ void __launch_bounds__(kWarps2D * 32)
                 __syncwarp();
                 continue;
             }
+            const unsigned ncell = (unsigned)src.W * (unsigned)src.H;
+            bool bad = false;
             for (int i = lane; i < n; i += 32) {
-                const float o = __ldg(src.map + ((const int *)sx)[i]);
+                const unsigned id = (unsigned)((const int *)sx)[i];
+                bad |= id >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
+                const float o = id < ncell ? __ldg(src.map + id) : 0.0f;
                 sp[i] = o;
                 sc[i] = cell_gain(p.docc, o);
                 sx[i] = cell_gain(p.demp, o);
             }
+            if (__any_sync(kFull, bad) && lane == 0) set_status(status, FSMI_STATUS_INTERNAL);
         } else {
             const int base = src.off[beam];
             n = src.off[beam + 1] - base;
