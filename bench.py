@@ -1,0 +1,354 @@
+"""Benchmark of the FSMI hot path on GB300.
+
+Workload (one step): exact FSMI (Theorem 1) of every beam of a batch on the 2D office map:
+2048x2048 grid (background 0.1, 400 obstacles at 0.9, 40% unknown at 0.5), 1024 candidate poses
+x 360 beams, range 256 cells, sigma = 2 cells, delta_occ = 1.5, delta_emp = 0.67, through
+fsmi_eval_2d (traversal, first-hit probabilities, C_k and the full pair sum, all in one kernel).
+Synthetic, seeded inputs (paper_1905_02238_gb300.synth); no dataset is involved.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {fsmi,reference}]
+
+Multi-GPU (torchrun, one process per GPU): every rank evaluates its own 1024 poses (weak scaling,
+the map replicated, no collective on the data path); value = all ranks' beams / the slowest rank's
+time. The reference arm (--impl reference) times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact FSMI beams/s & % roofline; surrogate+rerank poses/s at top-10 recall"
+WORKLOAD = "2D exact FSMI, 2048x2048 office grid, 1024 poses x 360 beams, R=256, sigma=2"
+SIGMA, R_MAX, DOCC, DEMP = 2.0, 256.0, 1.5, 0.67
+N_POSES = 1024
+L2_FLUSH_BYTES = 512 << 20  # > the 126 MB L2
+SM_COUNT_NOMINAL = 152
+SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (ex2, rcp)
+SFU_PER_PAIR = 2  # one ex2 and one rcp per (first-hit cell, boundary) tail term
+
+# DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
+# ncu capture (profiles/k_eval_2d_exact_office2048.md), valid only for the kernel sources whose
+# hash is recorded with it; reported as null once those sources change.
+TRAFFIC = {"sources_sha1": None, "bytes_per_launch": None}
+KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb300/csrc/gauss_tail.cuh",
+                  "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]
+
+
+def kernel_sources_sha1() -> str:
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def workload(rank: int, n_poses: int = N_POSES):
+    from paper_1905_02238_gb300 import synth
+
+    grid, poses, dirs = synth.config2(n_poses=n_poses, pose_seed=1 + rank)
+    return grid, poses, dirs
+
+
+def cpu_baseline(grid, poses, dirs, n_pose_sample: int = 24):
+    """The FP64 oracle as it stands, on all host cores, on the first n_pose_sample poses."""
+    import oracle
+
+    prm = oracle.Params(variant=oracle.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.eval_2d(grid, poses[:n_pose_sample], dirs, prm, nthreads=threads)
+    dt = time.perf_counter() - t0
+    nb = n_pose_sample * dirs.shape[0]
+    return {"value": nb / dt, "unit": "beams/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {n_pose_sample} poses x {dirs.shape[0]} beams ({nb} beams), FP64, {dt:.1f} s wall"}
+
+
+def _time_ms(fn, reps=5):
+    import torch
+
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def other_variants(g, p, d, out):
+    """Throughput of the other variants on the same devices (context; not the headline)."""
+    import torch
+
+    from paper_1905_02238_gb300 import fsmi, synth
+
+    res = {}
+    nb = p.shape[0] * d.shape[0]
+    for name, kw in (("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
+                     ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4))):
+        prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)
+        ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out))
+        res[name] = {"beams_per_s": nb / (ms * 1e-3), "ms": ms}
+    vox, vp, vd = synth.config3()
+    v, vp, vd = (torch.from_numpy(x).to(g.device) for x in (vox, vp, vd))
+    nr = vp.shape[0] * vd.shape[0]
+    out3 = torch.empty((vp.shape[0], vd.shape[0]), dtype=torch.float32, device=g.device)
+    for name, kw in (("fsmi_rle_3d", dict(variant=fsmi.EXACT)), ("approx_fsmi_rle_3d_delta6", dict(variant=fsmi.APPROX)),
+                     ("uniform_fsmi_rle_3d_h4", dict(variant=fsmi.UNIFORM))):
+        prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=384.0, run_cap=64, trunc_delta=6,
+                          uniform_h=4, **kw)
+        ms = _time_ms(lambda: fsmi.eval_3d(v, vp, vd, prm, out=out3))
+        res[name] = {"rays_per_s": nr / (ms * 1e-3), "ms": ms,
+                     "workload": "512x512x128 voxels, 64 poses x 128x128 rays, 384 virtual cells, fused sample+RLE+MI"}
+    return res
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    grid, poses, dirs = workload(0)
+    prm = oracle.Params(variant=oracle.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX)
+    threads = os.cpu_count() or 1
+    per_step = 4  # poses per reference step (a bounded sample of the same batch)
+    times = []
+    for s in range(args.warmup + args.steps):
+        sel = poses[(s * per_step) % N_POSES:(s * per_step) % N_POSES + per_step]
+        t0 = time.perf_counter()
+        oracle.eval_2d(grid, sel, dirs, prm, nthreads=threads)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    nb = per_step * dirs.shape[0]
+    value = nb * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "beams/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": f"{per_step} poses x 360 beams"},
+        "cpu_baseline": {"value": value, "unit": "beams/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} poses x {dirs.shape[0]} beams per step"},
+        "e2e": {"value": value, "unit": "beams/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fsmi(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1905_02238_gb300 import build, fsmi
+
+    build.build()
+    fsmi.load()
+    grid, poses, dirs = workload(rank, args.poses)
+    g = torch.from_numpy(grid).to(dev)
+    p = torch.from_numpy(poses).to(dev)
+    d = torch.from_numpy(dirs).to(dev)
+    P, B = poses.shape[0], dirs.shape[0]
+    out = torch.empty((P, B), dtype=torch.float32, device=dev)
+    prm = fsmi.Params(variant=fsmi.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # algorithmic work of one launch, from the (bit-exact) traversal: n(n+1) tail terms per beam
+    cap = int(R_MAX * 1.5) + 4
+    _, _, n = fsmi.trace_2d(grid.shape[1], grid.shape[0], p, d, R_MAX, cap)
+    n64 = n.to(torch.float64)
+    pairs = float((n64 * (n64 + 1)).sum().item())
+    cells = float(n64.sum().item())
+
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fsmi.eval_2d(g, p, d, prm, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        for i in range(args.steps):
+            flush.fill_(float(i))  # evict the map from L2 between steps (untimed)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(per) / len(per)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    nbeams_all = P * B * ws
+    value = nbeams_all / (ms * 1e-3)
+
+    # end to end through the public call with host buffers: pinned inputs in, result out, per step
+    hg, hp, hd = (torch.from_numpy(x).pin_memory() for x in (grid, poses, dirs))
+    for _ in range(2):
+        fsmi.eval_2d(hg, hp, hd, prm)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res = fsmi.eval_2d(hg, hp, hd, prm)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert res.shape == (P, B) and bool(torch.isfinite(res).all())
+    h2d = grid.nbytes + poses.nbytes + dirs.nbytes
+    d2h = P * B * 4
+
+    if rank == 0:
+        clocks = clk.summary()
+        peaks = measured_peaks()
+        sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_sfu = sms * SFU_PER_SM_CLK * sm_max * 1e6  # SFU ops/s at the maximum SM clock
+        achieved_sfu = pairs * SFU_PER_PAIR / (ms * 1e-3)
+        traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha1"] == kernel_sources_sha1() else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "beams/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "poses_per_gpu": P, "beams_per_pose": B, "cells": cells,
+                       "pair_terms": pairs, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"dp{ws} (poses sharded, map replicated)"},
+            "roofline": {"bound": "alu", "achieved": achieved_sfu / 1e9, "peak": peak_sfu / 1e9,
+                         "unit": "G SFU op/s", "frac": achieved_sfu / peak_sfu, "traffic": traffic,
+                         "kernel": "k_eval_2d<EXACT,map>",
+                         "model": f"{SFU_PER_PAIR} SFU ops (ex2, rcp) per tail term x {pairs:.4g} terms; "
+                                  f"peak = {sms} SMs x {SFU_PER_SM_CLK}/clk x {sm_max:.0f} MHz"},
+            "clocks": clocks,
+            "e2e": {"value": nbeams_all / e2e_s, "unit": "beams/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+        }
+        if ws == 1:
+            line["variants"] = other_variants(g, p, d, out)
+            line["cpu_baseline"] = cpu_baseline(grid, poses, dirs)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["fsmi", "reference"], default="fsmi")
+    ap.add_argument("--poses", type=int, default=N_POSES, help="poses per GPU (smaller for profiling cases)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_fsmi(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
