@@ -32,8 +32,10 @@ SIGMA, R_MAX, DOCC, DEMP = 2.0, 256.0, 1.5, 0.67
 N_POSES = 1024
 L2_FLUSH_BYTES = 512 << 20  # > the 126 MB L2
 SM_COUNT_NOMINAL = 152
-SFU_PER_SM_CLK = 16  # MUFU results per SM per clock (ex2, rcp)
-SFU_PER_PAIR = 2  # one ex2 and one rcp per (first-hit cell, boundary) tail term
+LANES_PER_SM_CLK = 128  # instruction issue: 4 schedulers x 32 lanes per SM per clock
+OPS_PER_TERM = 14  # per boundary tail term (csrc/gauss_tail.cuh): FADD d, FMUL d^2, ex2, FFMA 1+p|d|,
+#                    rcp, 6 FFMA Horner, 2 FMUL, sign, FFMA accumulate: one issue slot each
+TAIL_CUT = 11.3  # scaled distance beyond which the tail term is exactly zero in FP32 (fsmi_2d.cu)
 
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
 # ncu capture (profiles/k_eval_2d_exact_office2048.md), valid only for the kernel sources whose
@@ -138,6 +140,31 @@ def cpu_baseline(grid, poses, dirs, n_pose_sample: int = 24):
             "sample": f"first {n_pose_sample} poses x {dirs.shape[0]} beams ({nb} beams), FP64, {dt:.1f} s wall"}
 
 
+def work_counts(fsmi, grid, p, d, chunk=32768):
+    """(cells, Theorem-1 boundary terms n(n+1), terms the exact kernel evaluates) of one launch."""
+    import torch
+
+    cap = int(R_MAX * 1.5) + 4
+    _, l, n = fsmi.trace_2d(grid.shape[1], grid.shape[0], p, d, R_MAX, cap)
+    cs = float(torch.tensor(1.0 / (SIGMA * 1.4142135623730951), dtype=torch.float32) *
+               torch.tensor(1.2011224087864498, dtype=torch.float32))
+    cells = pairs = terms = 0.0
+    col = torch.arange(cap + 1, device=l.device)
+    for a in range(0, n.shape[0], chunk):
+        nn = n[a:a + chunk].to(torch.int64)
+        ll = l[a:a + chunk] * cs
+        ll = torch.where(col[None, :] <= nn[:, None], ll, torch.full_like(ll, float("inf")))
+        mu = 0.5 * (ll[:, :-1] + ll[:, 1:])
+        valid = col[None, :-1] < nn[:, None]
+        lo = torch.searchsorted(ll, mu - TAIL_CUT)
+        hi = torch.searchsorted(ll, mu + TAIL_CUT)
+        terms += float(torch.where(valid, hi - lo, torch.zeros_like(hi)).sum().item())
+        n64 = nn.to(torch.float64)
+        cells += float(n64.sum().item())
+        pairs += float((n64 * (n64 + 1)).sum().item())
+    return cells, pairs, terms
+
+
 def _time_ms(fn, reps=5):
     import torch
 
@@ -161,7 +188,8 @@ def other_variants(g, p, d, out):
 
     res = {}
     nb = p.shape[0] * d.shape[0]
-    for name, kw in (("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
+    for name, kw in (("exact_fsmi_full_sweep", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP)),
+                     ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
                      ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4))):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)
         ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out))
@@ -241,12 +269,9 @@ def run_fsmi(args):
     prm = fsmi.Params(variant=fsmi.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    # algorithmic work of one launch, from the (bit-exact) traversal: n(n+1) tail terms per beam
-    cap = int(R_MAX * 1.5) + 4
-    _, _, n = fsmi.trace_2d(grid.shape[1], grid.shape[0], p, d, R_MAX, cap)
-    n64 = n.to(torch.float64)
-    pairs = float((n64 * (n64 + 1)).sum().item())
-    cells = float(n64.sum().item())
+    # algorithmic work of one launch, from the (bit-exact) traversal: Theorem 1 has n(n+1)
+    # boundary terms per beam; the kernel evaluates those whose FP32 tail is not flushed to 0
+    cells, pairs, terms = work_counts(fsmi, grid, p, d)
 
     stream = torch.cuda.current_stream()
 
@@ -306,21 +331,22 @@ def run_fsmi(args):
         peaks = measured_peaks()
         sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_sfu = sms * SFU_PER_SM_CLK * sm_max * 1e6  # SFU ops/s at the maximum SM clock
-        achieved_sfu = pairs * SFU_PER_PAIR / (ms * 1e-3)
+        peak_ops = sms * LANES_PER_SM_CLK * sm_max * 1e6  # issue-slot ops/s at the maximum SM clock
+        achieved_ops = terms * OPS_PER_TERM / (ms * 1e-3)
         traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha1"] == kernel_sources_sha1() else None
         line = {
             "metric": METRIC, "value": value, "unit": "beams/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "poses_per_gpu": P, "beams_per_pose": B, "cells": cells,
-                       "pair_terms": pairs, "l2": "flushed between timed steps (512 MB write)",
+                       "theorem1_terms": pairs, "evaluated_terms": terms,
+                       "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"dp{ws} (poses sharded, map replicated)"},
-            "roofline": {"bound": "alu", "achieved": achieved_sfu / 1e9, "peak": peak_sfu / 1e9,
-                         "unit": "G SFU op/s", "frac": achieved_sfu / peak_sfu, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T issue-op/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
                          "kernel": "k_eval_2d<EXACT,map>",
-                         "model": f"{SFU_PER_PAIR} SFU ops (ex2, rcp) per tail term x {pairs:.4g} terms; "
-                                  f"peak = {sms} SMs x {SFU_PER_SM_CLK}/clk x {sm_max:.0f} MHz"},
+                         "model": f"{OPS_PER_TERM} ops per evaluated tail term x {terms:.4g} terms; "
+                                  f"peak = {sms} SMs x {LANES_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz"},
             "clocks": clocks,
             "e2e": {"value": nbeams_all / e2e_s, "unit": "beams/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -79,7 +79,14 @@ typedef struct {
                            (Algorithm 4) with centre l_1 - 1/2 */
     int approx_reading; /* Approx-FSMI-RLE: 0 = Theorem 5's sub-blocks as printed (default),
                            1 = strict band |k - j| <= Delta */
+    int flags;          /* FSMI_FLAG_* bits, 0 by default */
 } fsmi_params;
+
+/* Exact 2D FSMI normally evaluates, for each first-hit cell, only the boundary terms whose
+ * Gaussian tail is non-zero in FP32 (the tail underflows to exactly 0 beyond about 26 sigma/2),
+ * which gives the same result bit for bit as evaluating all n(n+1) terms of Theorem 1. This flag
+ * forces the full sweep (for verification and timing comparisons). */
+#define FSMI_FLAG_FULL_SWEEP 0x1
 
 /* Documented maxima. */
 #define FSMI_MAX_GRID 32767        /* W, H (2D) and X, Y, Z (3D) */

@@ -181,6 +181,11 @@ __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, long long 
 
 // ---- pair sums ------------------------------------------------------------------------------------
 
+// per-warp shared arrays, in units of `stride` floats: l, C, P, scratch (ids / f_emp / D / dC)
+constexpr int kArrays2D = 4;
+// internal variant id of the full n(n+1) exact sweep (FSMI_FLAG_FULL_SWEEP)
+constexpr int kExactFullSweep = 3;
+
 struct Src2D {
     // map source
     const float *map;
@@ -248,6 +253,55 @@ __device__ __forceinline__ float exact_sum(const float *sl, const float *sc, con
 #undef FSMI_CASE
             default: break;
         }
+    }
+    return r;
+}
+
+// Largest scaled distance whose tail is not flushed to zero: beyond |d| = 11.3 the factor
+// 2^(-d^2) <= 2^(-127.69) is subnormal and ex2.approx.ftz returns exactly 0, so the term is +-0.
+constexpr float kTailCut = 11.3f;
+
+__device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
+{
+    int lo = 0, len = n;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (a[lo + half] < x) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+// Exact pair sum over the boundaries whose tail term can be non-zero: for slot j only
+// m with |l_m - mu_j| < kTailCut (scaled) are visited, in increasing m, so every non-zero term
+// of the full sweep is added in the same order and the FP32 result is the same bit for bit.
+// sdc[m] = C_m - C_{m-1} for m = 0..n.
+__device__ __forceinline__ float exact_window_sum(const float *sl, const float *sdc, const float *sc,
+                                                  const float *sp, int n, bool e0, float pe0, float mu0)
+{
+    const int nslots = n + (e0 ? 1 : 0);
+    float r = 0.0f;
+    for (int j = lane_id(); j < nslots; j += 32) {
+        float mu, Cj, Pj;
+        if (j < n) {
+            mu = 0.5f * (sl[j] + sl[j + 1]);
+            Cj = sc[j];
+            Pj = sp[j];
+        } else {
+            mu = mu0;
+            Cj = 0.0f;
+            Pj = pe0;
+        }
+        const int lo = lower_bound_f(sl, n + 1, mu - kTailCut);
+        const int hi = lower_bound_f(sl, n + 1, mu + kTailCut);
+        float acc = 0.0f;
+#pragma unroll 4
+        for (int m = lo; m < hi; ++m) acc = fmaf(sdc[m], signed_tail(sl[m] - mu), acc);
+        r = fmaf(Pj, Cj + acc, r);
     }
     return r;
 }
@@ -356,7 +410,7 @@ __global__ void __launch_bounds__(kWarps2D * 32)
 {
     extern __shared__ float smem[];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    float *sl = smem + (size_t)warp * 4 * stride;
+    float *sl = smem + (size_t)warp * kArrays2D * stride;
     float *sc = sl + stride;
     float *sp = sc + stride;
     float *sx = sp + stride;
@@ -417,12 +471,14 @@ __global__ void __launch_bounds__(kWarps2D * 32)
             }
             const float pe0 = cell_prefixes(sp, sc, sx, n, VAR == FSMI_UNIFORM);
             const float mu0 = sl[0] - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
-            if (VAR == FSMI_EXACT)
-                I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
-            else if (VAR == FSMI_APPROX)
-                I = approx_sum(sl, sc, sp, n, e0, pe0, mu0, p.trunc);
-            else
-                I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
+            if (VAR == kExactFullSweep) I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
+            if (VAR == FSMI_EXACT) {
+                for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
+                __syncwarp();
+                I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0);
+            }
+            if (VAR == FSMI_APPROX) I = approx_sum(sl, sc, sp, n, e0, pe0, mu0, p.trunc);
+            if (VAR == FSMI_UNIFORM) I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
             I = warp_sum(I);
         }
         if (lane == 0) out[beam] = I;
@@ -459,7 +515,7 @@ static cudaError_t launch_variant(const Src2D &src, const DevParams &p, long lon
                                   cudaStream_t s)
 {
     const int stride = ((p.nmax + 2) + 3) & ~3;
-    const size_t smem = (size_t)kWarps2D * 4 * stride * sizeof(float);
+    const size_t smem = (size_t)kWarps2D * kArrays2D * stride * sizeof(float);
     auto kern = k_eval_2d<VAR, FROM_MAP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -481,7 +537,9 @@ static cudaError_t dispatch(const Src2D &src, const DevParams &p, long long nbea
 {
     if (nbeams <= 0) return cudaSuccess;
     switch (p.variant) {
-        case FSMI_EXACT: return launch_variant<FSMI_EXACT, FROM_MAP>(src, p, nbeams, out, status, s);
+        case FSMI_EXACT:
+            if (p.flags & FSMI_FLAG_FULL_SWEEP) return launch_variant<kExactFullSweep, FROM_MAP>(src, p, nbeams, out, status, s);
+            return launch_variant<FSMI_EXACT, FROM_MAP>(src, p, nbeams, out, status, s);
         case FSMI_APPROX: return launch_variant<FSMI_APPROX, FROM_MAP>(src, p, nbeams, out, status, s);
         default: return launch_variant<FSMI_UNIFORM, FROM_MAP>(src, p, nbeams, out, status, s);
     }

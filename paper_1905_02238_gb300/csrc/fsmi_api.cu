@@ -66,6 +66,7 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     if (prm->g_kernel != FSMI_G_PDF && prm->g_kernel != FSMI_G_ERF) return FSMI_ERR_ARG;
     if (prm->approx_reading != 0 && prm->approx_reading != 1) return FSMI_ERR_ARG;
     if (use != kUseBeams && !finite_pos(prm->max_range)) return FSMI_ERR_ARG;
+    if (prm->flags & ~FSMI_FLAG_FULL_SWEEP) return FSMI_ERR_ARG;
     d.variant = prm->variant;
     d.sigma = prm->variant == FSMI_UNIFORM ? 1.0f : prm->sigma;
     d.inv_s2 = (float)(1.0 / ((double)d.sigma * 1.4142135623730951));
@@ -78,6 +79,7 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     d.run_cap = prm->run_cap;
     d.g_kernel = prm->g_kernel;
     d.approx_reading = prm->approx_reading;
+    d.flags = prm->flags;
     d.rfix = 0;
     d.rend = 0.0f;
     d.K = 0;

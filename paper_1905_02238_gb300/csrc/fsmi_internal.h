@@ -23,6 +23,7 @@ struct DevParams {
     int g_kernel;       // FSMI_G_PDF / FSMI_G_ERF
     int approx_reading; // Approx-FSMI-RLE reading
     int K;              // RLE kernel support radius (cells)
+    int flags;          // FSMI_FLAG_* bits
 };
 
 constexpr int kWarps2D = 4;   // warps per block, 2D kernels

@@ -21,6 +21,7 @@ from . import build as _build
 
 EXACT, APPROX, UNIFORM = 0, 1, 2
 G_PDF, G_ERF = 0, 1
+FLAG_FULL_SWEEP = 0x1
 FN_EVAL_2D, FN_EVAL_BEAMS, FN_RLE_ENCODE_3D, FN_EVAL_RLE, FN_EVAL_3D = 0, 1, 2, 3, 4
 STATUS_BEAM_OVERFLOW, STATUS_RUN_OVERFLOW, STATUS_BAD_BEAM = 0x1, 0x2, 0x4
 MAX_RANGE_2D, MAX_CELLS, MAX_SAMPLES_3D = 1024.0, 2048, 1024
@@ -46,6 +47,7 @@ class _CParams(ctypes.Structure):
         ("g_kernel", ctypes.c_int),
         ("e0_mode", ctypes.c_int),
         ("approx_reading", ctypes.c_int),
+        ("flags", ctypes.c_int),
     ]
 
 
@@ -64,11 +66,12 @@ class Params:
     g_kernel: int = G_PDF
     e0_mode: int = 0
     approx_reading: int = 0
+    flags: int = 0
 
     def c(self) -> _CParams:
         return _CParams(int(self.variant), float(self.sigma), float(self.delta_occ), float(self.delta_emp),
                         int(self.trunc_delta), int(self.uniform_h), float(self.max_range), int(self.run_cap),
-                        int(self.g_kernel), int(self.e0_mode), int(self.approx_reading))
+                        int(self.g_kernel), int(self.e0_mode), int(self.approx_reading), int(self.flags))
 
 
 def library_path() -> str:

@@ -213,3 +213,20 @@ def test_gauss_tail_against_cuda_erfc():
     err = (got - ref).abs()
     assert err.max().item() <= 2.5e-7
     assert bool(torch.all(err <= 1.5e-6 * ref + 3e-9))
+
+
+@pytest.mark.parametrize("e0", [0, 1])
+def test_exact_window_is_bit_identical_to_full_sweep(e0):
+    # skipping the tail terms that flush to zero in FP32 must not change a single bit
+    for grid, poses, dirs, R, sigma in (synth.config1() + (64.0, 1.5), synth.config2(n_poses=24, size=512) + (256.0, 2.0),
+                                        synth.config2(n_poses=8, size=512) + (256.0, 0.4)):
+        gp, _ = _prms(sigma, R, e0)
+        win = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp)
+        gp.flags = fsmi.FLAG_FULL_SWEEP
+        full = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp)
+        assert torch.equal(win, full)
+    off, o, l, lend = synth.random_beams(200, 0, 400, seed=77)
+    gp, _ = _prms(3.0, 64.0, e0)
+    win = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp)
+    gp.flags = fsmi.FLAG_FULL_SWEEP
+    assert torch.equal(win, fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp))
