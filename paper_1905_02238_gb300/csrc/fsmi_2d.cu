@@ -12,7 +12,9 @@
 //   S_j = sum_k C_k (Phi(x_{k+1}) - Phi(x_k)) = C_j + sum_{m=1}^{n+1} (C_m - C_{m-1}) sgn(x_m) T(|x_m|)
 // with x_m = (l_m - mu_j) / sigma, C_0 = C_{n+1} = 0 and T the upper Gaussian tail. Every term is
 // a tail mass, so no difference of two values near 1 is formed in FP32, and each (j, m) pair costs
-// one tail evaluation (gauss_tail.cuh) instead of the two Phi values of G_{k,j}.
+// one tail evaluation (gauss_tail.cuh) instead of the two Phi values of G_{k,j}. The sign is taken
+// from the indices (boundaries m <= j lie before the centre of cell j), not from the FP32
+// difference, which is 0 for a cell shorter than the FP32 resolution of its distance.
 #include "../../include/fsmi.h"
 #include "fsmi_device.cuh"
 #include "fsmi_internal.h"
@@ -210,10 +212,12 @@ __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, co
 {
     const int lane = lane_id();
     float mu[J], acc[J];
+    int mid[J];  // boundaries m < mid lie before the centre
 #pragma unroll
     for (int t = 0; t < J; ++t) {
         const int j = jb + lane + 32 * t;
         mu[t] = (j < n) ? 0.5f * (sl[j] + sl[j + 1]) : ((j == n && e0) ? mu0 : 3.0e30f);
+        mid[t] = (j < n) ? j + 1 : 0;
         acc[t] = 0.0f;
     }
     float cprev = 0.0f;
@@ -223,7 +227,7 @@ __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, co
         const float dc = cm - cprev;
         cprev = cm;
 #pragma unroll
-        for (int t = 0; t < J; ++t) acc[t] = fmaf(dc, signed_tail(lm - mu[t]), acc[t]);
+        for (int t = 0; t < J; ++t) acc[t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc[t]);
     }
     float r = 0.0f;
 #pragma unroll
@@ -276,6 +280,35 @@ __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
     return lo;
 }
 
+// Boundary terms m in [a, b) of one first-hit cell, added in increasing m to acc: on the lower
+// side (NEG, boundaries before the centre) the term is -dC_m T(mu - l_m), above it +dC_m T(l_m - mu).
+// Aligned pairs of boundaries go through the packed tail; results equal the scalar path bit for bit.
+template <bool NEG>
+__device__ __forceinline__ float side_terms(const float *sl, const float *sdc, int a, int b, float mu, float acc)
+{
+    int m = a;
+    if (m < b && (m & 1)) {
+        const float d = NEG ? mu - sl[m] : sl[m] - mu;
+        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(d), acc);
+        ++m;
+    }
+    const f32x2 mu2 = pack2(mu, mu);
+#pragma unroll 2
+    for (; m + 1 < b; m += 2) {
+        const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
+        const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
+        float T0, T1;
+        gauss_tail2(NEG ? sub2(mu2, L) : sub2(L, mu2), T0, T1);
+        acc = fmaf(NEG ? -dc.x : dc.x, T0, acc);
+        acc = fmaf(NEG ? -dc.y : dc.y, T1, acc);
+    }
+    if (m < b) {
+        const float d = NEG ? mu - sl[m] : sl[m] - mu;
+        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(d), acc);
+    }
+    return acc;
+}
+
 // Exact pair sum over the boundaries whose tail term can be non-zero: for slot j only
 // m with |l_m - mu_j| < kTailCut (scaled) are visited, in increasing m, so every non-zero term
 // of the full sweep is added in the same order and the FP32 result is the same bit for bit.
@@ -287,20 +320,22 @@ __device__ __forceinline__ float exact_window_sum(const float *sl, const float *
     float r = 0.0f;
     for (int j = lane_id(); j < nslots; j += 32) {
         float mu, Cj, Pj;
+        int mid;
         if (j < n) {
             mu = 0.5f * (sl[j] + sl[j + 1]);
             Cj = sc[j];
             Pj = sp[j];
+            mid = j + 1;
         } else {
             mu = mu0;
             Cj = 0.0f;
             Pj = pe0;
+            mid = 0;
         }
         const int lo = lower_bound_f(sl, n + 1, mu - kTailCut);
         const int hi = lower_bound_f(sl, n + 1, mu + kTailCut);
-        float acc = 0.0f;
-#pragma unroll 4
-        for (int m = lo; m < hi; ++m) acc = fmaf(sdc[m], signed_tail(sl[m] - mu), acc);
+        float acc = side_terms<true>(sl, sdc, lo, min(max(mid, lo), hi), mu, 0.0f);
+        acc = side_terms<false>(sl, sdc, max(mid, lo), hi, mu, acc);
         r = fmaf(Pj, Cj + acc, r);
     }
     return r;
@@ -329,11 +364,13 @@ __device__ __forceinline__ float approx_sum(const float *sl, const float *sc, co
             klo = 0;
             khi = min(n - 1, D - 1);
         }
+        const int mid = (j < n) ? j + 1 : 0;  // boundaries m < mid lie before the centre
         float acc = 0.0f;
         for (int m = klo; m <= khi + 1; ++m) {
             const float cm = (m <= khi) ? sc[m] : 0.0f;
             const float cm1 = (m > klo) ? sc[m - 1] : 0.0f;
-            acc = fmaf(cm - cm1, signed_tail(sl[m] - mu), acc);
+            const float dc = cm - cm1;
+            acc = fmaf(m < mid ? -dc : dc, gauss_tail(sl[m] - mu), acc);
         }
         r = fmaf(Pj, Cj + acc, r);
     }

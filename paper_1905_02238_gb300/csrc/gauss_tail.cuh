@@ -56,7 +56,60 @@ __device__ __forceinline__ float gauss_tail(float d)
     return (e * t) * q;
 }
 
-// sgn(d) T(|d|): the tail mass beyond a boundary, signed by the side it lies on.
-__device__ __forceinline__ float signed_tail(float d) { return copysignf(gauss_tail(d), d); }
+// ---- two tails per instruction (Blackwell packed FP32) ---------------------------------------
+// Each half of an f32x2 operation is the IEEE round-to-nearest result of the scalar operation, so
+// gauss_tail2 returns exactly what two gauss_tail calls return; it only halves the issue slots
+// of the FP32 part.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(f32x2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// T(d0), T(d1) for two non-negative scaled distances packed in d.
+__device__ __forceinline__ void gauss_tail2(f32x2 d, float &T0, float &T1)
+{
+    float dd0, dd1, den0, den1;
+    unpack2(mul2(d, d), dd0, dd1);
+    const float e0 = ex2_approx(-dd0), e1 = ex2_approx(-dd1);
+    unpack2(fma2(pack2(kTailP, kTailP), d, pack2(1.0f, 1.0f)), den0, den1);
+    const f32x2 t = pack2(rcp_approx(den0), rcp_approx(den1));
+    f32x2 q = fma2(pack2(kTailC6, kTailC6), t, pack2(kTailC5, kTailC5));
+    q = fma2(q, t, pack2(kTailC4, kTailC4));
+    q = fma2(q, t, pack2(kTailC3, kTailC3));
+    q = fma2(q, t, pack2(kTailC2, kTailC2));
+    q = fma2(q, t, pack2(kTailC1, kTailC1));
+    q = fma2(q, t, pack2(kTailC0, kTailC0));
+    unpack2(mul2(mul2(pack2(e0, e1), t), q), T0, T1);
+}
 
 }  // namespace fsmi

@@ -39,7 +39,7 @@ def _variants():
 def _prms(sigma, R, e0=0, **kw):
     base = dict(sigma=sigma, delta_occ=1.5, delta_emp=0.67, max_range=R, e0_mode=e0)
     base.update(kw)
-    return fsmi.Params(**base), oracle.Params(**base)
+    return fsmi.Params(**base), oracle.Params(**{k: v for k, v in base.items() if k != "flags"})
 
 
 # ---- traversal ------------------------------------------------------------------------------------
@@ -230,3 +230,30 @@ def test_exact_window_is_bit_identical_to_full_sweep(e0):
     win = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp)
     gp.flags = fsmi.FLAG_FULL_SWEEP
     assert torch.equal(win, fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp))
+
+
+def test_zero_length_cells():
+    # consecutive equal distances (a cell shorter than FP32 resolution, as near-corner traversal
+    # cuts produce): the boundary below the cell centre must still count as below
+    rng = np.random.default_rng(42)
+    beams, dists = [], []
+    for k in range(64):
+        n = int(rng.integers(2, 200))
+        w = rng.uniform(0.2, 1.4, n)
+        w[rng.random(n) < 0.15] = 0.0  # zero-length cells
+        l = np.concatenate([[0.0], np.cumsum(w)]).astype(np.float32)
+        beams.append(rng.uniform(0.02, 0.98, n))
+        dists.append(l)
+    off = np.concatenate([[0], np.cumsum([len(b) for b in beams])]).astype(np.int32)
+    o = np.concatenate(beams).astype(np.float32)
+    l = np.concatenate([d[:-1] for d in dists]).astype(np.float32)
+    lend = np.array([d[-1] for d in dists], np.float32)
+    for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP),
+               dict(variant=fsmi.APPROX, trunc_delta=3)):
+        for e0 in (0, 1):
+            gp, op = _prms(1.0, 64.0, e0, **kw)
+            op_kw = {k: v for k, v in kw.items() if k != "flags"}
+            op = oracle.Params(sigma=1.0, delta_occ=1.5, delta_emp=0.67, max_range=64.0, e0_mode=e0, **op_kw)
+            got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
+            ref = oracle.eval_beams(off, o, l, lend, op)
+            assert_mi_close(got, ref, f"zero-length {kw} e0={e0}")
