@@ -156,6 +156,29 @@ fsmi_status fsmi_rle_encode_3d(const float *vox, int X, int Y, int Z, const int3
                                size_t ws_bytes, fsmi_stream_t stream);
 
 /*
+ * fsmi_rle_encode_3d_noalloc - fsmi_rle_encode_3d for callers that cannot allocate device memory
+ * when they encode (for example a planner inside a real-time control loop whose device memory is
+ * reserved up front, or code that is handed only input and output pointers). The paper has no
+ * counterpart: this is a library convenience, not part of the method.
+ *   Arguments and results are those of fsmi_rle_encode_3d without the workspace: the offset scan
+ *   keeps its tile totals in a 16 KiB array owned by the library, which every GPU that loads the
+ *   library holds until the process exits. Nothing is allocated and no allocating routine is
+ *   called.
+ *   At most FSMI_NOALLOC_MAX_RAYS rays (P*R) per call; more returns FSMI_ERR_CAPACITY and launches
+ *   nothing.
+ *   The first call on each device looks up the array's device address (with that device
+ *   current); make that first call before capturing a stream.
+ *   All calls share the one array: calls whose work overlaps on the GPU (different streams, or
+ *   different host threads on the same device) race and must be serialised by the caller. Each
+ *   call overwrites every entry it reads, so no clearing is needed between calls.
+ */
+#define FSMI_NOALLOC_MAX_RAYS (4096LL * 4096LL)
+fsmi_status fsmi_rle_encode_3d_noalloc(const float *vox, int X, int Y, int Z, const int32_t *poses,
+                                       int P, const int32_t *dirs, int R, const fsmi_params *prm,
+                                       int32_t *run_off, float *run_o, uint8_t *run_len,
+                                       int run_capacity, fsmi_stream_t stream);
+
+/*
  * fsmi_eval_rle - FSMI-RLE (Theorem 3), Approx-FSMI-RLE (Theorem 5) or Uniform-FSMI-RLE
  * (Theorem 6) of run-length-encoded rays.
  *   run_off  int32 [nrays+1] CSR offsets; ray r owns runs run_off[r] .. run_off[r+1]-1 whose

@@ -204,6 +204,25 @@ fsmi_status fsmi_rle_encode_3d(const float *vox, int X, int Y, int Z, const int3
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
+fsmi_status fsmi_rle_encode_3d_noalloc(const float *vox, int X, int Y, int Z, const int32_t *poses, int P,
+                                       const int32_t *dirs, int R, const fsmi_params *prm, int32_t *run_off,
+                                       float *run_o, uint8_t *run_len, int run_capacity, fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUseRLE, d);
+    if (st != FSMI_OK) return st;
+    if (!vox_ok(vox, X, Y, Z, poses, P, dirs, R) || run_capacity < 0 || !run_off) return FSMI_ERR_ARG;
+    const long long nrays = (long long)P * R;
+    if (nrays > FSMI_NOALLOC_MAX_RAYS) return FSMI_ERR_CAPACITY;
+    if (run_capacity > 0 && (!run_o || !run_len)) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    Vox3D v{vox, X, Y, Z, poses, P, dirs, R};
+    cudaError_t e = launch_rle_encode_3d_static(v, d, run_off, run_o, run_len, run_capacity, (int)scan_tiles(nrays),
+                                                sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
 fsmi_status fsmi_eval_rle(const int32_t *run_off, const float *run_o, const uint8_t *run_len, int nrays,
                           const fsmi_params *prm, float *out, fsmi_stream_t stream)
 {

@@ -58,6 +58,13 @@ cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32
 // scan tile size of the RLE offsets (elements per tile)
 constexpr int kScanTile = 4096;
 
+// tile totals held by the library-owned scratch of fsmi_rle_encode_3d_noalloc (16 KiB, up to
+// kEncodeScratchTiles * kScanTile rays per call)
+constexpr int kEncodeScratchTiles = 4096;
+cudaError_t launch_rle_encode_3d_static(const Vox3D &v, const DevParams &p, int32_t *run_off, float *run_o,
+                                        uint8_t *run_len, int run_capacity, int ntiles, int *status,
+                                        cudaStream_t s);
+
 int sm_count();
 
 }  // namespace fsmi

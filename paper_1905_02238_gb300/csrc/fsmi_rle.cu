@@ -10,6 +10,8 @@
 // A = sum_j x^j W0(j + t), B = sum_j x^j W1(j + t), summed only where W0 can be non-zero
 // (j + t in [-K, Lv - 1 + K], K the kernel's support radius). No power x^{-t} is ever formed,
 // which avoids the instability the paper notes for its alpha/beta tables (Section 4.1).
+#include <mutex>
+
 #include "../../include/fsmi.h"
 #include "fsmi_device.cuh"
 #include "fsmi_internal.h"
@@ -560,6 +562,51 @@ cudaError_t launch_rle_encode_3d(const Vox3D &v, const DevParams &p, int32_t *ru
     k_rle_write<<<(unsigned)grid, kWarpsRLE * 32, smem, s>>>(v, p, nrays, stride, run_off, run_o, run_len,
                                                               run_capacity, status);
     return cudaGetLastError();
+}
+
+// ---- run-length encoding without caller workspace -----------------------------------------
+//
+// Some callers cannot allocate device memory at the point where they encode rays: a planner that
+// runs inside a real-time control loop with its device memory reserved up front, or host code
+// that receives only input and output pointers from another framework and holds no allocator. For
+// them the offset scan keeps its tile totals in this file-scope array instead of a caller
+// workspace. Every GPU that loads the library holds it until the process exits.
+__device__ __align__(256) int32_t g_encode_scan_scratch[kEncodeScratchTiles];
+
+namespace {
+std::mutex g_scratch_mu;
+int32_t *g_scratch_ptr[64];
+}  // namespace
+
+// Device address of g_encode_scan_scratch for the current device. The symbol's name is only a
+// host-side stand-in, so the address is looked up once per device, with that device current.
+cudaError_t encode_scratch_ptr(int32_t **ptr)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *a = nullptr;
+        e = cudaGetSymbolAddress(&a, g_encode_scan_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = (int32_t *)a;
+    }
+    *ptr = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_rle_encode_3d_static(const Vox3D &v, const DevParams &p, int32_t *run_off, float *run_o,
+                                        uint8_t *run_len, int run_capacity, int ntiles, int *status,
+                                        cudaStream_t s)
+{
+    if (ntiles > kEncodeScratchTiles) return cudaErrorInvalidValue;
+    int32_t *scratch = nullptr;
+    cudaError_t e = encode_scratch_ptr(&scratch);
+    if (e != cudaSuccess) return e;
+    // the scan writes every tile total it reads, so the array needs no clearing between calls
+    return launch_rle_encode_3d(v, p, run_off, run_o, run_len, run_capacity, scratch, ntiles, status, s);
 }
 
 }  // namespace fsmi

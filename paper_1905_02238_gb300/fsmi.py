@@ -101,6 +101,7 @@ def load():
             "fsmi_workspace_size": [i, ll, P, ctypes.POINTER(ctypes.c_size_t)],
             "fsmi_device_status": [p, ctypes.POINTER(ctypes.c_int)],
             "fsmi_gauss_tail": [p, p, ll, p],
+            "fsmi_rle_encode_3d_noalloc": [p, i, i, i, p, i, p, i, P, p, p, p, i, p],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -233,6 +234,29 @@ def rle_encode_3d(vox, poses, dirs, prm: Params, capacity: int, ws: torch.Tensor
     _raise(lib.fsmi_rle_encode_3d(_ptr(v), X, Y, Z, _ptr(ps), P, _ptr(ds), R, ctypes.byref(cp), _ptr(off), _ptr(ro),
                                   _ptr(rl), capacity, _ptr(ws), ws.numel() * ws.element_size(), _stream()),
            "fsmi_rle_encode_3d")
+    return m.out(off), m.out(ro[:capacity]), m.out(rl[:capacity])
+
+
+NOALLOC_MAX_RAYS = 4096 * 4096
+
+
+def rle_encode_3d_noalloc(vox, poses, dirs, prm: Params, capacity: int):
+    """fsmi_rle_encode_3d_noalloc: the encoder for callers that cannot allocate device memory; the
+    offset scan uses a library-owned array instead of a workspace. Calls that overlap on the GPU
+    race; the first call on a device should precede any stream capture."""
+    lib = load()
+    m = _Marshal(vox, poses, dirs)
+    v = m.arg(vox, torch.float32, "vox", 3)
+    ps = m.arg(poses, torch.int32, "poses", 2, 12)
+    ds = m.arg(dirs, torch.int32, "dirs", 2, 3)
+    Z, Y, X = v.shape
+    P, R = ps.shape[0], ds.shape[0]
+    off = torch.empty(P * R + 1, dtype=torch.int32, device=m.dev)
+    ro = torch.empty(max(capacity, 1), dtype=torch.float32, device=m.dev)
+    rl = torch.empty(max(capacity, 1), dtype=torch.uint8, device=m.dev)
+    cp = prm.c()
+    _raise(lib.fsmi_rle_encode_3d_noalloc(_ptr(v), X, Y, Z, _ptr(ps), P, _ptr(ds), R, ctypes.byref(cp), _ptr(off),
+                                          _ptr(ro), _ptr(rl), capacity, _stream()), "fsmi_rle_encode_3d_noalloc")
     return m.out(off), m.out(ro[:capacity]), m.out(rl[:capacity])
 
 
