@@ -32,9 +32,11 @@ SIGMA, R_MAX, DOCC, DEMP = 2.0, 256.0, 1.5, 0.67
 N_POSES = 1024
 L2_FLUSH_BYTES = 512 << 20  # > the 126 MB L2
 SM_COUNT_NOMINAL = 152
-LANES_PER_SM_CLK = 128  # instruction issue: 4 schedulers x 32 lanes per SM per clock
-OPS_PER_TERM = 14  # per boundary tail term (csrc/gauss_tail.cuh): FADD d, FMUL d^2, ex2, FFMA 1+p|d|,
-#                    rcp, 6 FFMA Horner, 2 FMUL, sign, FFMA accumulate: one issue slot each
+FMA_LANES_PER_SM_CLK = 128  # FP32 FMA-pipe lane operations per SM per clock (4 x 32)
+SFU_PER_SM_CLK = 32  # SFU (ex2, rcp) results per SM per clock, measured by a throughput probe
+OPS_PER_TERM = 12  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh):
+#                    distance, square, 1 + p|d|, 6 Horner FMAs, two products, accumulate;
+#                    plus 2 SFU operations (ex2, rcp), for which the SFU has room to spare
 TAIL_CUT = 11.3  # scaled distance beyond which the tail term is exactly zero in FP32 (fsmi_2d.cu)
 
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
@@ -117,6 +119,23 @@ def measured_peaks():
             return json.load(f)
     except (OSError, ValueError):
         return {}
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The slowest rank's value (all ranks take part); x itself when ws == 1."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
+    """Weak scaling: every rank processes units_per_rank; the job takes the slowest rank's time."""
+    return units_per_rank * ws / seconds
 
 
 def workload(rank: int, n_poses: int = N_POSES):
@@ -297,13 +316,9 @@ def run_fsmi(args):
     if ws > 1:
         torch.distributed.barrier()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(per) / len(per)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(per) / len(per), ws, dev)
     nbeams_all = P * B * ws
-    value = nbeams_all / (ms * 1e-3)
+    value = whole_job_rate(P * B, ws, ms * 1e-3)
 
     # end to end through the public call with host buffers: pinned inputs in, result out, per step
     hg, hp, hd = (torch.from_numpy(x).pin_memory() for x in (grid, poses, dirs))
@@ -317,11 +332,7 @@ def run_fsmi(args):
     for _ in range(e2e_steps):
         res = fsmi.eval_2d(hg, hp, hd, prm)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws, dev)
     assert res.shape == (P, B) and bool(torch.isfinite(res).all())
     h2d = grid.nbytes + poses.nbytes + dirs.nbytes
     d2h = P * B * 4
@@ -331,7 +342,7 @@ def run_fsmi(args):
         peaks = measured_peaks()
         sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_ops = sms * LANES_PER_SM_CLK * sm_max * 1e6  # issue-slot ops/s at the maximum SM clock
+        peak_ops = sms * FMA_LANES_PER_SM_CLK * sm_max * 1e6  # FMA-pipe ops/s at the maximum SM clock
         achieved_ops = terms * OPS_PER_TERM / (ms * 1e-3)
         traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha1"] == kernel_sources_sha1() else None
         line = {
@@ -343,12 +354,13 @@ def run_fsmi(args):
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"dp{ws} (poses sharded, map replicated)"},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "T issue-op/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
+                         "unit": "T FP32-op/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
                          "kernel": "k_eval_2d<EXACT,map>",
-                         "model": f"{OPS_PER_TERM} ops per evaluated tail term x {terms:.4g} terms; "
-                                  f"peak = {sms} SMs x {LANES_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz"},
+                         "model": f"{OPS_PER_TERM} FMA-pipe ops per evaluated tail term x {terms:.4g} terms; "
+                                  f"peak = {sms} SMs x {FMA_LANES_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz "
+                                  f"(SFU: 2 ops/term of {SFU_PER_SM_CLK}/clk/SM, not binding)"},
             "clocks": clocks,
-            "e2e": {"value": nbeams_all / e2e_s, "unit": "beams/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": whole_job_rate(P * B, ws, e2e_s), "unit": "beams/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
         }
