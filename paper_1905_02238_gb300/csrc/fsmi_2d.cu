@@ -283,6 +283,10 @@ __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
 // Boundary terms m in [a, b) of one first-hit cell, added in increasing m to acc: on the lower
 // side (NEG, boundaries before the centre) the term is -dC_m T(mu - l_m), above it +dC_m T(l_m - mu).
 // Aligned pairs of boundaries go through the packed tail; results equal the scalar path bit for bit.
+#ifndef FSMI_PAIR_UNROLL
+#define FSMI_PAIR_UNROLL 2  // boundary pairs in flight per lane in the exact window loop
+#endif
+
 template <bool NEG>
 __device__ __forceinline__ float side_terms(const float *sl, const float *sdc, int a, int b, float mu, float acc)
 {
@@ -293,7 +297,7 @@ __device__ __forceinline__ float side_terms(const float *sl, const float *sdc, i
         ++m;
     }
     const f32x2 mu2 = pack2(mu, mu);
-#pragma unroll 2
+#pragma unroll FSMI_PAIR_UNROLL
     for (; m + 1 < b; m += 2) {
         const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
         const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
@@ -441,8 +445,12 @@ __device__ __forceinline__ float cell_prefixes(float *sp, float *sc, float *sx, 
     return pe0;
 }
 
+#ifndef FSMI_MIN_BLOCKS_2D
+#define FSMI_MIN_BLOCKS_2D 1  // minimum resident blocks per SM requested from the register allocator
+#endif
+
 template <int VAR, bool FROM_MAP>
-__global__ void __launch_bounds__(kWarps2D * 32)
+__global__ void __launch_bounds__(kWarps2D * 32, FSMI_MIN_BLOCKS_2D)
     k_eval_2d(Src2D src, DevParams p, long long nbeams, int stride, float *__restrict__ out, int *status)
 {
     extern __shared__ float smem[];

@@ -86,9 +86,10 @@ def load():
             return _lib
         if not torch.cuda.is_available():
             raise FsmiError("no CUDA device: libfsmi runs only on the GPU (there is no CPU fallback)")
-        if not os.path.exists(_build.LIB):
-            raise FsmiError(f"{_build.LIB} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
-        lib = ctypes.CDLL(_build.LIB)
+        path = os.environ.get("FSMI_LIBRARY", _build.LIB)
+        if not os.path.exists(path):
+            raise FsmiError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(path)
         i, p, ll = ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong
         P = ctypes.POINTER(_CParams)
         sig = {
