@@ -284,8 +284,9 @@ __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
 // side (NEG, boundaries before the centre) the term is -dC_m T(mu - l_m), above it +dC_m T(l_m - mu).
 // Aligned pairs of boundaries go through the packed tail; results equal the scalar path bit for bit.
 #ifndef FSMI_PAIR_UNROLL
-#define FSMI_PAIR_UNROLL 2  // boundary pairs in flight per lane in the exact window loop
+#define FSMI_PAIR_UNROLL 2
 #endif
+constexpr int kPairUnroll = FSMI_PAIR_UNROLL;  // boundary pairs in flight per lane, exact window loop
 
 template <bool NEG>
 __device__ __forceinline__ float side_terms(const float *sl, const float *sdc, int a, int b, float mu, float acc)
@@ -297,7 +298,7 @@ __device__ __forceinline__ float side_terms(const float *sl, const float *sdc, i
         ++m;
     }
     const f32x2 mu2 = pack2(mu, mu);
-#pragma unroll FSMI_PAIR_UNROLL
+#pragma unroll kPairUnroll
     for (; m + 1 < b; m += 2) {
         const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
         const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
