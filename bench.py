@@ -199,7 +199,7 @@ def _time_ms(fn, reps=5):
     return s.elapsed_time(e) / reps
 
 
-def other_variants(g, p, d, out):
+def other_variants(g, p, d, out):  # noqa: C901
     """Throughput of the other variants on the same devices (context; not the headline)."""
     import torch
 
@@ -211,7 +211,8 @@ def other_variants(g, p, d, out):
                      ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
                      ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4))):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)
-        ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out))
+        ws = torch.empty(16 * g.numel(), dtype=torch.uint8, device=g.device)
+        ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out, ws=ws))
         res[name] = {"beams_per_s": nb / (ms * 1e-3), "ms": ms}
     vox, vp, vd = synth.config3()
     v, vp, vd = (torch.from_numpy(x).to(g.device) for x in (vox, vp, vd))
@@ -294,8 +295,10 @@ def run_fsmi(args):
 
     stream = torch.cuda.current_stream()
 
+    ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, grid.size), dtype=torch.uint8, device=dev)
+
     def step():
-        fsmi.eval_2d(g, p, d, prm, out=out)
+        fsmi.eval_2d(g, p, d, prm, out=out, ws=ws)
 
     for _ in range(args.warmup):
         step()
@@ -362,7 +365,7 @@ def run_fsmi(args):
             "clocks": clocks,
             "e2e": {"value": whole_job_rate(P * B, ws, e2e_s), "unit": "beams/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,  # per step: per-cell gains of the map, then the beams
         }
         if ws == 1:
             line["variants"] = other_variants(g, p, d, out)

@@ -105,12 +105,17 @@ typedef struct {
  *   dirs   int32 [B][2]: beam unit vectors in the sensor frame (Q30). Beam b of pose p points
  *          along d = floor((Rot(yaw_p) dirs[b] + 2^29) / 2^30).
  *   out    float32 [P][B], nats.
+ *   ws     optional device workspace (NULL allowed), 16-byte aligned, of at least
+ *          fsmi_workspace_size(FSMI_FN_EVAL_2D, W*H) bytes. With it, when the batch visits more
+ *          cells than the map holds, the per-cell gains f(delta_occ, r), f(delta_emp, r) are
+ *          computed once per map cell (like the paper's look-up table of f, Section 3.3, but exact
+ *          per cell) instead of once per visit; the results are the same bit for bit.
  * The traversal is exact integer arithmetic: a cell is entered while its entry distance is
  * < max_range and it lies inside the grid; simultaneous x/y crossings are one diagonal step.
  */
 fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, int P,
                          const int32_t *dirs, int B, const fsmi_params *prm, float *out,
-                         fsmi_stream_t stream);
+                         void *ws, size_t ws_bytes, fsmi_stream_t stream);
 
 /*
  * fsmi_eval_beams - the same pair sums on explicit beams (Theorem 1's inputs: o_i, l_i).
@@ -214,7 +219,8 @@ fsmi_status fsmi_gauss_tail(const float *s, float *out, long long n, fsmi_stream
 #define FSMI_FN_EVAL_RLE 3
 #define FSMI_FN_EVAL_3D 4
 
-/* Bytes of device workspace entry point `fn` needs for `nitems` beams or rays (0 if none). */
+/* Bytes of device workspace entry point `fn` can use for `nitems` items (0 if none): map cells
+ * for FSMI_FN_EVAL_2D (optional gains), rays for FSMI_FN_RLE_ENCODE_3D (required offset scan). */
 fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm, size_t *bytes);
 
 /* Waits for `stream`, then returns in *status the current device's status word (FSMI_STATUS_*

@@ -49,15 +49,29 @@ __device__ __forceinline__ void beam_dir(const int32_t *pose, int32_t ux, int32_
 
 struct Geo {
     int sM, sm, cM0, cm0, dimM, dimm, xmaj, W;
-    long long nM0, nm0, aM, am, LM, Lm;
+    unsigned nM0, nm0;  // Q16 distances to the first major / minor boundary (< 2^31 + 2^16 with k)
+    unsigned aM, am;    // |d| along the major / minor axis (Q30, <= 2^31)
+    unsigned LM, Lm;    // crossing numerators below these have entry distance < R
     float rM, rm, R;
 };
 
-__device__ __forceinline__ long long minor_before(const Geo &g, int k)
+__device__ __forceinline__ unsigned long long mulw(unsigned a, unsigned b) { return (unsigned long long)a * b; }
+
+// Number of minor crossings at or before the major crossing k: #{i >= 0 : nm(i) aM <= nM(k) am}
+// = floor((nM(k) am - nm0 aM) / (2^16 aM)) + 1 when that numerator is >= 0. The quotient (< 2^11
+// for ranges up to 1024 cells) is estimated in FP32 and corrected exactly in integers.
+__device__ __forceinline__ int minor_before(const Geo &g, int k)
 {
     if (g.am == 0 || k < 0) return 0;
-    const long long num = (g.nM0 + (long long)k * 65536) * g.am - g.nm0 * g.aM;
-    return num < 0 ? 0 : num / (65536LL * g.aM) + 1;
+    const long long num = (long long)mulw(g.nM0 + (unsigned)k * 65536u, g.am) - (long long)mulw(g.nm0, g.aM);
+    if (num < 0) return 0;
+    const long long hi = num >> 16;  // floor(num / 2^16); floor(hi / aM) = floor(num / (2^16 aM))
+    long long q = (long long)((float)hi * (1.0f / (float)g.aM));
+    q -= (q * (long long)g.aM > hi);
+    q -= (q * (long long)g.aM > hi);
+    q += ((q + 1) * (long long)g.aM <= hi);
+    q += ((q + 1) * (long long)g.aM <= hi);
+    return (int)q + 1;
 }
 
 template <bool WRITE>
@@ -65,8 +79,8 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int base, int
                                      bool &ended, float &endl)
 {
     int cM = g.cM0 + g.sM * (k0 + 1);
-    long long i = minor_before(g, k0);
-    int cm = g.cm0 + g.sm * (int)i;
+    int i = minor_before(g, k0);
+    int cm = g.cm0 + g.sm * i;
     cnt = 0;
     ended = false;
     endl = 0.0f;
@@ -82,10 +96,10 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int base, int
         ++cnt;                                                                       \
     } while (0)
     for (int k = k0; k <= k1; ++k) {
-        FSMI_EMIT(k < 0 ? 0.0f : (float)(g.nM0 + (long long)k * 65536) * g.rM);
-        const long long nMn = g.nM0 + (long long)(k + 1) * 65536;  // next major crossing
-        long long nmi = g.nm0 + i * 65536;                          // next minor crossing
-        if (g.am && nmi * g.aM < nMn * g.am) {                     // minor crossing inside
+        FSMI_EMIT(k < 0 ? 0.0f : (float)(g.nM0 + (unsigned)k * 65536u) * g.rM);
+        const unsigned nMn = g.nM0 + (unsigned)(k + 1) * 65536u;  // next major crossing
+        unsigned nmi = g.nm0 + (unsigned)i * 65536u;              // next minor crossing
+        if (g.am && mulw(nmi, g.aM) < mulw(nMn, g.am)) {         // minor crossing inside
             if (nmi >= g.Lm) {
                 ended = true;
                 endl = g.R;
@@ -99,14 +113,14 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int base, int
             }
             FSMI_EMIT((float)nmi * g.rm);
             ++i;
-            nmi += 65536;
+            nmi += 65536u;
         }
         if (nMn >= g.LM) {
             ended = true;
             endl = g.R;
             break;
         }
-        const bool tie = g.am && (nmi * g.aM == nMn * g.am);
+        const bool tie = g.am && (mulw(nmi, g.aM) == mulw(nMn, g.am));
         cM += g.sM;
         if (tie) {
             cm += g.sm;
@@ -133,7 +147,7 @@ __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, long long 
     if (dx < 0 && (ox & 0xFFFF) == 0) --cx;
     if (dy < 0 && (oy & 0xFFFF) == 0) --cy;
     if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) return 0;
-    const long long adx = dx < 0 ? -(long long)dx : dx, ady = dy < 0 ? -(long long)dy : dy;
+    const unsigned adx = dx < 0 ? 0u - (unsigned)dx : (unsigned)dx, ady = dy < 0 ? 0u - (unsigned)dy : (unsigned)dy;
     Geo g;
     g.xmaj = adx >= ady;
     g.W = W;
@@ -147,17 +161,18 @@ __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, long long 
     g.dimM = g.xmaj ? W : H;
     g.dimm = g.xmaj ? H : W;
     const long long oM = g.xmaj ? ox : oy, om = g.xmaj ? oy : ox;
-    g.nM0 = g.sM > 0 ? ((long long)(g.cM0 + 1) << 16) - oM : oM - ((long long)g.cM0 << 16);
-    g.nm0 = g.am == 0 ? 0 : (g.sm > 0 ? ((long long)(g.cm0 + 1) << 16) - om : om - ((long long)g.cm0 << 16));
+    g.nM0 = (unsigned)(g.sM > 0 ? ((long long)(g.cM0 + 1) << 16) - oM : oM - ((long long)g.cM0 << 16));
+    g.nm0 = g.am == 0 ? 0u
+                      : (unsigned)(g.sm > 0 ? ((long long)(g.cm0 + 1) << 16) - om : om - ((long long)g.cm0 << 16));
     // crossing numerators below these limits have entry lambda < R:
     //   num * 2^30 < rfix * a  <=>  num < floor((rfix * a - 1) / 2^30) + 1
-    g.LM = ((rfix * g.aM - 1) >> 30) + 1;
-    g.Lm = g.am ? ((rfix * g.am - 1) >> 30) + 1 : 0;
+    g.LM = (unsigned)((((unsigned long long)rfix * g.aM - 1) >> 30) + 1);
+    g.Lm = g.am ? (unsigned)((((unsigned long long)rfix * g.am - 1) >> 30) + 1) : 0u;
     g.rM = 16384.0f / (float)g.aM;
     g.rm = g.am ? 16384.0f / (float)g.am : 0.0f;
     g.R = rend;
     // major crossings that stay in range and inside the grid along M
-    const long long KR = g.LM > g.nM0 ? (g.LM - g.nM0 + 65535) >> 16 : 0;
+    const long long KR = g.LM > g.nM0 ? ((long long)g.LM - g.nM0 + 65535) >> 16 : 0;
     const long long KG = g.sM > 0 ? (g.dimM - 1 - g.cM0) : g.cM0;
     const int K = (int)(KR < KG ? KR : KG);
     const int NI = K + 1;  // intervals k = -1 .. K-1
@@ -196,6 +211,7 @@ struct Src2D {
     int P;
     const int32_t *dirs;
     int B;
+    const float4 *gains;  // optional per-map-cell (o, f_occ, f_emp, 0)
     // explicit-beam source
     const int32_t *off;
     const float *o;
@@ -481,13 +497,24 @@ __global__ void __launch_bounds__(kWarps2D * 32, FSMI_MIN_BLOCKS_2D)
             }
             const unsigned ncell = (unsigned)src.W * (unsigned)src.H;
             bool bad = false;
-            for (int i = lane; i < n; i += 32) {
-                const unsigned id = (unsigned)((const int *)sx)[i];
-                bad |= id >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
-                const float o = id < ncell ? __ldg(src.map + id) : 0.0f;
-                sp[i] = o;
-                sc[i] = cell_gain(p.docc, o);
-                sx[i] = cell_gain(p.demp, o);
+            if (src.gains) {
+                for (int i = lane; i < n; i += 32) {
+                    const unsigned id = (unsigned)((const int *)sx)[i];
+                    bad |= id >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
+                    const float4 v = id < ncell ? __ldg(src.gains + id) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    sp[i] = v.x;
+                    sc[i] = v.y;
+                    sx[i] = v.z;
+                }
+            } else {
+                for (int i = lane; i < n; i += 32) {
+                    const unsigned id = (unsigned)((const int *)sx)[i];
+                    bad |= id >= ncell;
+                    const float o = id < ncell ? __ldg(src.map + id) : 0.0f;
+                    sp[i] = o;
+                    sc[i] = cell_gain(p.docc, o);
+                    sx[i] = cell_gain(p.demp, o);
+                }
             }
             if (__any_sync(kFull, bad) && lane == 0) set_status(status, FSMI_STATUS_INTERNAL);
         } else {
@@ -549,6 +576,17 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// Per-cell gains of the whole map: (o, f(delta_occ, r), f(delta_emp, r), 0), the same values the
+// beam kernel would compute at each visit.
+__global__ void k_map_gains(const float *__restrict__ map, long long ncell, float docc, float demp,
+                            float4 *__restrict__ gains)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += (long long)gridDim.x * blockDim.x) {
+        const float o = __ldg(map + i);
+        gains[i] = make_float4(o, cell_gain(docc, o), cell_gain(demp, o), 0.0f);
+    }
+}
+
 // Scaled Gaussian tail over an array (exposed for testing the numerical core).
 __global__ void k_gauss_tail(const float *__restrict__ s, float *__restrict__ out, long long n)
 {
@@ -592,16 +630,25 @@ static cudaError_t dispatch(const Src2D &src, const DevParams &p, long long nbea
 }
 
 cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
-                           const DevParams &p, float *out, int *status, cudaStream_t s)
+                           const DevParams &p, float *out, float4 *gains, int *status, cudaStream_t s)
 {
-    Src2D src{map, W, H, poses, P, dirs, B, nullptr, nullptr, nullptr, nullptr};
+    if (gains) {
+        const long long ncell = (long long)W * H;
+        long long grid = (ncell + 255) / 256;
+        const long long gmax = (long long)sm_count() * 16;
+        if (grid > gmax) grid = gmax;
+        k_map_gains<<<(unsigned)grid, 256, 0, s>>>(map, ncell, p.docc, p.demp, gains);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr};
     return dispatch<true>(src, p, (long long)P * B, out, status, s);
 }
 
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                               const DevParams &p, float *out, int *status, cudaStream_t s)
 {
-    Src2D src{nullptr, 0, 0, nullptr, 0, nullptr, 0, off, o, l, lend};
+    Src2D src{nullptr, 0, 0, nullptr, 0, nullptr, 0, nullptr, off, o, l, lend};
     return dispatch<false>(src, p, nbeams, out, status, s);
 }
 

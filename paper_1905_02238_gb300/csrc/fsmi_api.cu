@@ -132,7 +132,7 @@ using namespace fsmi;
 extern "C" {
 
 fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
-                         const fsmi_params *prm, float *out, fsmi_stream_t stream)
+                         const fsmi_params *prm, float *out, void *ws, size_t ws_bytes, fsmi_stream_t stream)
 {
     DevParams d;
     fsmi_status st = make_params(prm, kUse2D, d);
@@ -142,7 +142,14 @@ fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, i
     if (!map || !poses || !dirs || !out) return FSMI_ERR_ARG;
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
-    cudaError_t e = launch_eval_2d(map, W, H, poses, P, dirs, B, d, out, sp, (cudaStream_t)stream);
+    // per-cell gains once per map cell when the workspace fits and the batch visits more cells
+    // (up to P*B*nmax) than the map holds
+    const long long cells = (long long)W * H;
+    float4 *gains = nullptr;
+    if (ws && ((uintptr_t)ws & 15) == 0 && ws_bytes >= (size_t)cells * sizeof(float4) &&
+        (long long)P * B * (d.nmax / 2) >= cells)
+        gains = (float4 *)ws;
+    cudaError_t e = launch_eval_2d(map, W, H, poses, P, dirs, B, d, out, gains, sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -269,6 +276,7 @@ fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm
     if (!bytes || nitems < 0) return FSMI_ERR_ARG;
     *bytes = 0;
     if (fn == FSMI_FN_RLE_ENCODE_3D) *bytes = (size_t)scan_tiles(nitems) * sizeof(int32_t);
+    else if (fn == FSMI_FN_EVAL_2D) *bytes = (size_t)nitems * 4 * sizeof(float);
     else if (fn < FSMI_FN_EVAL_2D || fn > FSMI_FN_EVAL_3D) return FSMI_ERR_ARG;
     return FSMI_OK;
 }

@@ -31,7 +31,7 @@ constexpr int kWarpsRLE = 4;  // warps per block, RLE kernels
 
 // 2D (fsmi_2d.cu)
 cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs,
-                           int B, const DevParams &p, float *out, int *status, cudaStream_t s);
+                           int B, const DevParams &p, float *out, float4 *gains, int *status, cudaStream_t s);
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                               const DevParams &p, float *out, int *status, cudaStream_t s);
 cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,

@@ -93,7 +93,7 @@ def load():
         i, p, ll = ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong
         P = ctypes.POINTER(_CParams)
         sig = {
-            "fsmi_eval_2d": [p, i, i, p, i, p, i, P, p, p],
+            "fsmi_eval_2d": [p, i, i, p, i, p, i, P, p, p, ctypes.c_size_t, p],
             "fsmi_eval_beams": [p, p, p, p, i, P, p, p],
             "fsmi_trace_2d": [i, i, p, i, p, i, ctypes.c_float, i, p, p, p, p],
             "fsmi_rle_encode_3d": [p, i, i, i, p, i, p, i, P, p, p, p, i, p, ctypes.c_size_t, p],
@@ -160,8 +160,10 @@ class _Marshal:
 
 
 def eval_2d(grid: torch.Tensor, poses: torch.Tensor, dirs: torch.Tensor, prm: Params,
-            out: torch.Tensor | None = None) -> torch.Tensor:
-    """fsmi_eval_2d: grid float32 [H, W]; poses int32 [P, 4]; dirs int32 [B, 2] -> float32 [P, B]."""
+            out: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """fsmi_eval_2d: grid float32 [H, W]; poses int32 [P, 4]; dirs int32 [B, 2] -> float32 [P, B].
+    ws: optional device workspace (uint8, >= workspace_size(FN_EVAL_2D, H*W) bytes) for per-cell
+    gains; by default one is taken from torch's allocator. Pass an empty tensor to use none."""
     lib = load()
     m = _Marshal(grid, poses, dirs)
     g = m.arg(grid, torch.float32, "grid", 2)
@@ -170,9 +172,12 @@ def eval_2d(grid: torch.Tensor, poses: torch.Tensor, dirs: torch.Tensor, prm: Pa
     P, B = ps.shape[0], ds.shape[0]
     if out is None or m.host:
         out = torch.empty((P, B), dtype=torch.float32, device=m.dev)
+    if ws is None:
+        ws = torch.empty(16 * g.numel(), dtype=torch.uint8, device=m.dev)
     cp = prm.c()
     _raise(lib.fsmi_eval_2d(_ptr(g), g.shape[1], g.shape[0], _ptr(ps), P, _ptr(ds), B, ctypes.byref(cp),
-                            _ptr(out), _stream()), "fsmi_eval_2d")
+                            _ptr(out), _ptr(ws) if ws.numel() else None, ws.numel() * ws.element_size(),
+                            _stream()), "fsmi_eval_2d")
     return m.out(out)
 
 

@@ -46,7 +46,8 @@ def test_host_only_entry_points(lib_path):
     lib.fsmi_workspace_size.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     assert lib.fsmi_workspace_size(2, 4096 * 3 + 1, None, ctypes.byref(b)) == 0
     assert b.value == 4 * 4
-    assert lib.fsmi_workspace_size(0, 100, None, ctypes.byref(b)) == 0 and b.value == 0
+    assert lib.fsmi_workspace_size(0, 100, None, ctypes.byref(b)) == 0 and b.value == 1600
+    assert lib.fsmi_workspace_size(3, 100, None, ctypes.byref(b)) == 0 and b.value == 0
     assert lib.fsmi_workspace_size(9, 100, None, ctypes.byref(b)) == 1
 
 

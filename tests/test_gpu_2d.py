@@ -257,3 +257,13 @@ def test_zero_length_cells():
             got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
             ref = oracle.eval_beams(off, o, l, lend, op)
             assert_mi_close(got, ref, f"zero-length {kw} e0={e0}")
+
+
+def test_map_gains_workspace_is_bit_identical():
+    # per-map-cell gains (workspace) against per-visit gains (no workspace), all three variants
+    grid, poses, dirs = synth.config2(n_poses=64, size=1024)
+    for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
+        gp, _ = _prms(2.0, 256.0, 0, **kw)
+        a = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp)
+        b = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp, ws=torch.empty(0, dtype=torch.uint8, device="cuda"))
+        assert torch.equal(a, b)
