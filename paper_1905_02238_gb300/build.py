@@ -37,9 +37,9 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
-          out: str | None = None) -> str:
-    """Compile (if stale) and return the path of libfsmi.so. `out` and `extra_flags` (e.g. -D
-    tunables) build a separate copy elsewhere, always from scratch."""
+          out: str | None = None, src_dir: str | None = None) -> str:
+    """Compile (if stale) and return the path of libfsmi.so. `out`, `extra_flags` (e.g. -D
+    tunables) and `src_dir` (another copy of csrc/) build a separate library elsewhere."""
     if out is None and not force and not _stale():
         return LIB
     target = out or LIB
@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     def compile_one(src: str) -> str:
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc] + flags + ["-c", os.path.join(src_dir or CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -300,7 +300,7 @@ __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
 // side (NEG, boundaries before the centre) the term is -dC_m T(mu - l_m), above it +dC_m T(l_m - mu).
 // Aligned pairs of boundaries go through the packed tail; results equal the scalar path bit for bit.
 #ifndef FSMI_PAIR_UNROLL
-#define FSMI_PAIR_UNROLL 2
+#define FSMI_PAIR_UNROLL 4
 #endif
 constexpr int kPairUnroll = FSMI_PAIR_UNROLL;  // boundary pairs in flight per lane, exact window loop
 
