@@ -219,12 +219,7 @@ struct Src2D {
     const float *lend;
 };
 
-// Summation order shared by both exact paths (so that they agree bit for bit): for each
-// first-hit slot the boundary terms are accumulated in four partial sums by boundary index
-// m mod 4, each in increasing m, then combined as (a0 + a1) + (a2 + a3).
-__device__ __forceinline__ float combine4(float a0, float a1, float a2, float a3) { return (a0 + a1) + (a2 + a3); }
-
-// One register-blocked pass of the full exact sweep over scaled distances: each lane owns J
+// One register-blocked pass of the exact pair sum over scaled distances: each lane owns J
 // first-hit slots j = jb + lane + 32 t and streams every boundary m = 0..n from shared memory.
 // Slot n is the no-return event when e0 is set (centre mu0, C_0 = 0).
 template <int J>
@@ -232,39 +227,32 @@ __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, co
                                             bool e0, float pe0, float mu0)
 {
     const int lane = lane_id();
-    float mu[J], acc[4][J];
+    float mu[J], acc[J];
     int mid[J];  // boundaries m < mid lie before the centre
 #pragma unroll
     for (int t = 0; t < J; ++t) {
         const int j = jb + lane + 32 * t;
         mu[t] = (j < n) ? 0.5f * (sl[j] + sl[j + 1]) : ((j == n && e0) ? mu0 : 3.0e30f);
         mid[t] = (j < n) ? j + 1 : 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q][t] = 0.0f;
+        acc[t] = 0.0f;
     }
     float cprev = 0.0f;
-    for (int m0 = 0; m0 <= n; m0 += 4) {
+    for (int m = 0; m <= n; ++m) {
+        const float lm = sl[m];
+        const float cm = sc[m];  // sc[n] = 0 (C_{n+1})
+        const float dc = cm - cprev;
+        cprev = cm;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int m = m0 + q;
-            if (m > n) break;
-            const float lm = sl[m];
-            const float cm = sc[m];  // sc[n] = 0 (C_{n+1})
-            const float dc = cm - cprev;
-            cprev = cm;
-#pragma unroll
-            for (int t = 0; t < J; ++t) acc[q][t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc[q][t]);
-        }
+        for (int t = 0; t < J; ++t) acc[t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc[t]);
     }
     float r = 0.0f;
 #pragma unroll
     for (int t = 0; t < J; ++t) {
         const int j = jb + lane + 32 * t;
-        const float a = combine4(acc[0][t], acc[1][t], acc[2][t], acc[3][t]);
         if (j < n)
-            r = fmaf(sp[j], sc[j] + a, r);
+            r = fmaf(sp[j], sc[j] + acc[t], r);
         else if (j == n && e0)
-            r = fmaf(pe0, a, r);
+            r = fmaf(pe0, acc[t], r);
     }
     return r;
 }
@@ -274,12 +262,14 @@ __device__ __forceinline__ float exact_sum(const float *sl, const float *sc, con
 {
     const int nslots = n + (e0 ? 1 : 0);
     float r = 0.0f;
-    for (int jb = 0; jb < nslots; jb += 32 * 8) {
-        const int cnt = min(8, (nslots - jb + 31) >> 5);
+    for (int jb = 0; jb < nslots; jb += 32 * 16) {
+        const int cnt = min(16, (nslots - jb + 31) >> 5);
         switch (cnt) {
 #define FSMI_CASE(J) \
     case J: r += exact_pass<J>(sl, sc, sp, n, jb, e0, pe0, mu0); break;
             FSMI_CASE(1) FSMI_CASE(2) FSMI_CASE(3) FSMI_CASE(4) FSMI_CASE(5) FSMI_CASE(6) FSMI_CASE(7) FSMI_CASE(8)
+            FSMI_CASE(9) FSMI_CASE(10) FSMI_CASE(11) FSMI_CASE(12) FSMI_CASE(13) FSMI_CASE(14) FSMI_CASE(15)
+            FSMI_CASE(16)
 #undef FSMI_CASE
             default: break;
         }
@@ -309,18 +299,41 @@ __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
 // Boundary terms m in [a, b) of one first-hit cell, added in increasing m to acc: on the lower
 // side (NEG, boundaries before the centre) the term is -dC_m T(mu - l_m), above it +dC_m T(l_m - mu).
 // Aligned pairs of boundaries go through the packed tail; results equal the scalar path bit for bit.
-#ifndef FSMI_QUAD_UNROLL
-#define FSMI_QUAD_UNROLL 2
+#ifndef FSMI_PAIR_UNROLL
+#define FSMI_PAIR_UNROLL 4
 #endif
-constexpr int kQuadUnroll = FSMI_QUAD_UNROLL;  // groups of 4 boundaries in flight per lane
+constexpr int kPairUnroll = FSMI_PAIR_UNROLL;  // boundary pairs in flight per lane, exact window loop
 
-__device__ __forceinline__ f32x2 abs2(f32x2 v) { return v & 0x7fffffff7fffffffull; }
+template <bool NEG>
+__device__ __forceinline__ float side_terms(const float *sl, const float *sdc, int a, int b, float mu, float acc)
+{
+    int m = a;
+    if (m < b && (m & 1)) {
+        const float d = NEG ? mu - sl[m] : sl[m] - mu;
+        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(d), acc);
+        ++m;
+    }
+    const f32x2 mu2 = pack2(mu, mu);
+#pragma unroll kPairUnroll
+    for (; m + 1 < b; m += 2) {
+        const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
+        const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
+        float T0, T1;
+        gauss_tail2(NEG ? sub2(mu2, L) : sub2(L, mu2), T0, T1);
+        acc = fmaf(NEG ? -dc.x : dc.x, T0, acc);
+        acc = fmaf(NEG ? -dc.y : dc.y, T1, acc);
+    }
+    if (m < b) {
+        const float d = NEG ? mu - sl[m] : sl[m] - mu;
+        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(d), acc);
+    }
+    return acc;
+}
 
-// Exact pair sum over the boundaries whose tail term can be non-zero: for slot j only the
-// 4-aligned range covering |l_m - mu_j| < kTailCut (scaled) is visited. Every term outside it is
-// exactly +-0 (its 2^(-s^2) underflows; padding boundaries beyond l_{n+1} are +inf with dC = 0), so
-// the four partial sums see the same non-zero terms in the same order as the full sweep and the
-// result is the same bit for bit. sdc[m] = C_m - C_{m-1}; sl, sdc are padded to n + 4.
+// Exact pair sum over the boundaries whose tail term can be non-zero: for slot j only
+// m with |l_m - mu_j| < kTailCut (scaled) are visited, in increasing m, so every non-zero term
+// of the full sweep is added in the same order and the FP32 result is the same bit for bit.
+// sdc[m] = C_m - C_{m-1} for m = 0..n.
 __device__ __forceinline__ float exact_window_sum(const float *sl, const float *sdc, const float *sc,
                                                   const float *sp, int n, bool e0, float pe0, float mu0)
 {
@@ -328,7 +341,7 @@ __device__ __forceinline__ float exact_window_sum(const float *sl, const float *
     float r = 0.0f;
     for (int j = lane_id(); j < nslots; j += 32) {
         float mu, Cj, Pj;
-        int mid;  // boundaries m < mid lie before the centre
+        int mid;
         if (j < n) {
             mu = 0.5f * (sl[j] + sl[j + 1]);
             Cj = sc[j];
@@ -340,23 +353,11 @@ __device__ __forceinline__ float exact_window_sum(const float *sl, const float *
             Pj = pe0;
             mid = 0;
         }
-        const int lo = lower_bound_f(sl, n + 1, mu - kTailCut) & ~3;
-        const int hi = (lower_bound_f(sl, n + 1, mu + kTailCut) + 3) & ~3;
-        const f32x2 mu2 = pack2(mu, mu);
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-#pragma unroll kQuadUnroll
-        for (int m = lo; m < hi; m += 4) {
-            const float4 L = *reinterpret_cast<const float4 *>(sl + m);
-            const float4 D = *reinterpret_cast<const float4 *>(sdc + m);
-            float T0, T1, T2, T3;
-            gauss_tail2(abs2(sub2(pack2(L.x, L.y), mu2)), T0, T1);
-            gauss_tail2(abs2(sub2(pack2(L.z, L.w), mu2)), T2, T3);
-            a0 = fmaf(m < mid ? -D.x : D.x, T0, a0);
-            a1 = fmaf(m + 1 < mid ? -D.y : D.y, T1, a1);
-            a2 = fmaf(m + 2 < mid ? -D.z : D.z, T2, a2);
-            a3 = fmaf(m + 3 < mid ? -D.w : D.w, T3, a3);
-        }
-        r = fmaf(Pj, Cj + combine4(a0, a1, a2, a3), r);
+        const int lo = lower_bound_f(sl, n + 1, mu - kTailCut);
+        const int hi = lower_bound_f(sl, n + 1, mu + kTailCut);
+        float acc = side_terms<true>(sl, sdc, lo, min(max(mid, lo), hi), mu, 0.0f);
+        acc = side_terms<false>(sl, sdc, max(mid, lo), hi, mu, acc);
+        r = fmaf(Pj, Cj + acc, r);
     }
     return r;
 }
@@ -545,10 +546,7 @@ __global__ void __launch_bounds__(kWarps2D * 32, FSMI_MIN_BLOCKS_2D)
             const float mu0 = sl[0] - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
             if (VAR == kExactFullSweep) I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
             if (VAR == FSMI_EXACT) {
-                for (int m = lane; m <= n + 4; m += 32) {
-                    sx[m] = m <= n ? sc[m] - (m > 0 ? sc[m - 1] : 0.0f) : 0.0f;
-                    if (m > n) sl[m] = __int_as_float(0x7f800000);  // +inf padding
-                }
+                for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
                 __syncwarp();
                 I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0);
             }
@@ -600,7 +598,7 @@ template <int VAR, bool FROM_MAP>
 static cudaError_t launch_variant(const Src2D &src, const DevParams &p, long long nbeams, float *out, int *status,
                                   cudaStream_t s)
 {
-    const int stride = ((p.nmax + 5) + 3) & ~3;  // n + 1 boundaries plus padding to n + 4
+    const int stride = ((p.nmax + 2) + 3) & ~3;
     const size_t smem = (size_t)kWarps2D * kArrays2D * stride * sizeof(float);
     auto kern = k_eval_2d<VAR, FROM_MAP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
