@@ -92,6 +92,52 @@ __device__ __forceinline__ float ipowf(float x, int k)
     return r;
 }
 
+// Chunked warp scan over the n cells held in shared memory. On entry sp = o, sc = f_occ,
+// sx = f_emp. On exit sp = P(e_j), sc = C_j (sc[n] = 0), and for the uniform variant sx = D_j.
+// Returns P(e_0).
+__device__ __forceinline__ float cell_prefixes(float *sp, float *sc, float *sx, int n, bool want_d)
+{
+    const int lane = lane_id();
+    const int K = (n + 31) >> 5;
+    const int lo = min(n, lane * K), hi = min(n, lo + K);
+    float prod = 1.0f, sum = 0.0f;
+    for (int i = lo; i < hi; ++i) {
+        prod *= 1.0f - sp[i];
+        sum += sx[i];
+    }
+    const float iprod = warp_incl_mul(prod);
+    const float isum = warp_incl_add(sum);
+    float E = __shfl_up_sync(kFull, iprod, 1);
+    float q = __shfl_up_sync(kFull, isum, 1);
+    if (lane == 0) {
+        E = 1.0f;
+        q = 0.0f;
+    }
+    const float pe0 = __shfl_sync(kFull, iprod, 31);
+    float csum = 0.0f;
+    for (int i = lo; i < hi; ++i) {
+        const float o = sp[i];
+        sp[i] = E * o;  // Algorithm 2
+        E *= 1.0f - o;
+        const float c = q + sc[i];  // Algorithm 3
+        sc[i] = c;
+        q += sx[i];
+        csum += c;
+    }
+    if (want_d) {  // Algorithm 4: D_k = sum_{i<=k} C_i
+        const float ic = warp_incl_add(csum);
+        float Dacc = __shfl_up_sync(kFull, ic, 1);
+        if (lane == 0) Dacc = 0.0f;
+        for (int i = lo; i < hi; ++i) {
+            Dacc += sc[i];
+            sx[i] = Dacc;
+        }
+    }
+    if (lane == 0) sc[n] = 0.0f;
+    __syncwarp();
+    return pe0;
+}
+
 __device__ __forceinline__ void set_status(int *status, int bits)
 {
     if (status) atomicOr(status, bits);

@@ -10,6 +10,13 @@
 // A = sum_j x^j W0(j + t), B = sum_j x^j W1(j + t), summed only where W0 can be non-zero
 // (j + t in [-K, Lv - 1 + K], K the kernel's support radius). No power x^{-t} is ever formed,
 // which avoids the instability the paper notes for its alpha/beta tables (Section 4.1).
+//
+// Short runs. The run-pair sum is Theorem 3's regrouping of the cell-level double sum
+// sum_j sum_k P(e_j) C_k g(k - j) over the virtual cells (eq. eqn_from_fsmi). When a ray's runs
+// are short (mean length below kCellRunLen) that cell-level form, a banded convolution of width
+// 2K + 1, costs less than the run pairs, so the ray is decompressed in shared memory and
+// evaluated that way -- the switch Section 5.4 recommends between the RLE algorithm and the
+// algorithm on the decompressed sequence. Both forms give the same value (pinned in the tests).
 #include <mutex>
 
 #include "../../include/fsmi.h"
@@ -24,7 +31,7 @@ namespace fsmi {
 // kind: 0 Gaussian density (Theorem 3), 1 Gaussian cell mass, 2 box 1[|d| <= H] (Theorem 6).
 // band >= 0 zeroes |d| > band (strict-band reading of Approx-FSMI-RLE). The normalisation
 // (1/(sqrt(2 pi) sigma), 1 or 1/(2H+1)) is folded into g. Built in double, stored as float.
-__device__ void build_table(float2 *tab, double *gs, int K, int kind, double sigma, int H, int band)
+__device__ void build_table(float2 *tab, double *gs, float *gtab, int K, int kind, double sigma, int H, int band)
 {
     for (int a = threadIdx.x; a <= K; a += blockDim.x) {  // g(|d|), d = a
         double g;
@@ -36,6 +43,8 @@ __device__ void build_table(float2 *tab, double *gs, int K, int kind, double sig
             g = exp(-(double)a * a / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
         if (band >= 0 && a > band) g = 0.0;
         gs[a] = g;
+        gtab[K + a] = (float)g;  // gtab[K + d] = g(d), d in [-K, K]
+        gtab[K - a] = (float)g;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -101,9 +110,8 @@ __device__ __forceinline__ RunSmem run_smem(float *base, int stride)
     return r;
 }
 
-// Run prefixes (Algorithms for P_E(u) and D_E(v)): P_E(u) = prod_{i<u} (1 - o_i)^{L_i},
-// D_E(u) = sum_{i<u} L_i f(delta_emp, r_i). On entry O, L (and S if have_s) are set.
-__device__ void run_prefixes(const RunSmem &r, int nr, float docc, float demp, bool have_s)
+// Run starts s_u = sum_{i<u} L_i (and S[nr] = n) from the lengths, or lengths from the starts.
+__device__ void run_starts(const RunSmem &r, int nr, bool have_s)
 {
     const int lane = lane_id();
     const int K = (nr + 31) >> 5;
@@ -122,6 +130,16 @@ __device__ void run_prefixes(const RunSmem &r, int nr, float docc, float demp, b
     } else {
         for (int u = lo; u < hi; ++u) r.L[u] = r.S[u + 1] - r.S[u];
     }
+    __syncwarp();
+}
+
+// Run prefixes (Algorithms for P_E(u) and D_E(v)): P_E(u) = prod_{i<u} (1 - o_i)^{L_i},
+// D_E(u) = sum_{i<u} L_i f(delta_emp, r_i). On entry O, L and S are set.
+__device__ void run_prefixes(const RunSmem &r, int nr, float docc, float demp)
+{
+    const int lane = lane_id();
+    const int K = (nr + 31) >> 5;
+    const int lo = min(nr, lane * K), hi = min(nr, lo + K);
     float prod = 1.0f, sum = 0.0f;
     for (int u = lo; u < hi; ++u) {
         const float o = r.O[u];
@@ -214,16 +232,108 @@ __device__ float pairs_thm5(const RunSmem &r, int nr, const float2 *tab, int K, 
     return tot;
 }
 
-__device__ __forceinline__ float ray_mi(const RunSmem &r, int nr, const DevParams &p, const float2 *tab, int K,
-                                        bool have_s)
+#ifndef FSMI_CELL_RUNLEN
+#define FSMI_CELL_RUNLEN 16
+#endif
+constexpr int kCellRunLen = FSMI_CELL_RUNLEN;  // mean run length below which a ray is evaluated per cell
+constexpr int kArraysRLE = 7;                  // per-warp shared arrays (each `stride` floats)
+
+// run containing virtual cell i: the last u with S[u] <= i
+__device__ __forceinline__ int run_of(const int *S, int nr, int i)
+{
+    int lo = 0, len = nr;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (S[lo + half] <= i) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo - 1;
+}
+
+// Cell-level evaluation (eq. eqn_from_fsmi) of one ray: decompress the runs into the n virtual
+// cells, form P(e_j) and C_k by warp scans (Algorithms 2 and 3), then
+// I = sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d}. For Theorem 5 as printed, a pair (j, k) in runs
+// u != v is kept only inside the sub-blocks s', L' of eqs. (su')-(Lv'); diagonal blocks are whole.
+// Arrays: 0 run o / run start per cell, 1 run f_occ / run end per cell, 2 run f_emp, 3 P,
+// 4 run starts S, 5 f_emp per cell, 6 C padded by K zeros on both sides.
+__device__ float ray_mi_cells(float *base, int stride, int nr, int n, const DevParams &p, const float *gtab, int K)
+{
+    const int lane = lane_id();
+    float *O = base, *RFO = base + stride, *RFE = base + 2 * stride, *CP = base + 3 * stride;
+    const int *S = (const int *)(base + 4 * stride);
+    float *CF = base + 5 * stride, *CC = base + 6 * stride;
+    for (int u = lane; u < nr; u += 32) {
+        const float o = O[u];
+        RFO[u] = cell_gain(p.docc, o);
+        RFE[u] = cell_gain(p.demp, o);
+    }
+    for (int i = lane; i < K; i += 32) {
+        CC[i] = 0.0f;
+        CC[K + n + i] = 0.0f;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const int u = run_of(S, nr, i);
+        CP[i] = O[u];
+        CC[K + i] = RFO[u];
+        CF[i] = RFE[u];
+    }
+    __syncwarp();
+    cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
+    const bool thm5 = p.variant == FSMI_APPROX && p.approx_reading == 0;
+    int *RS = (int *)O, *RE = (int *)RFO;
+    if (thm5) {
+        for (int i = lane; i < n; i += 32) {
+            const int u = run_of(S, nr, i);
+            RS[i] = S[u];
+            RE[i] = S[u + 1] - 1;
+        }
+        __syncwarp();
+    }
+    const int D = p.trunc;
+    float tot = 0.0f;
+    for (int j = lane; j < n; j += 32) {
+        float acc = 0.0f;
+        if (!thm5) {
+            for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
+        } else {
+            const int rsj = RS[j], rej = RE[j];
+            for (int d = -K; d <= K; ++d) {
+                const int k = j + d;
+                if ((unsigned)k >= (unsigned)n) continue;
+                const int rsk = RS[k];
+                const bool keep = rsk == rsj ? true
+                                  : rsk > rej ? (j >= rsk - D && k <= rej + D)  // run of k after run of j
+                                              : (j <= RE[k] + D && k >= rsj - D);
+                if (keep) acc = fmaf(gtab[K + d], CC[K + k], acc);
+            }
+        }
+        tot = fmaf(CP[j], acc, tot);
+    }
+    return tot;
+}
+
+__device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const DevParams &p, const float2 *tab,
+                                        const float *gtab, int K, bool have_s)
 {
     if (nr <= 0) return 0.0f;
-    run_prefixes(r, nr, p.docc, p.demp, have_s);
+    const RunSmem r = run_smem(base, stride);
+    run_starts(r, nr, have_s);
+    const int n = r.S[nr];
     float v;
-    if (p.variant == FSMI_APPROX && p.approx_reading == 0)
-        v = pairs_thm5(r, nr, tab, K, p.trunc);
-    else
-        v = pairs_all(r, nr, tab, K);
+    if (n < kCellRunLen * nr) {
+        v = ray_mi_cells(base, stride, nr, n, p, gtab, K);
+    } else {
+        run_prefixes(r, nr, p.docc, p.demp);
+        if (p.variant == FSMI_APPROX && p.approx_reading == 0)
+            v = pairs_thm5(r, nr, tab, K, p.trunc);
+        else
+            v = pairs_all(r, nr, tab, K);
+    }
     return warp_sum(v);
 }
 
@@ -311,10 +421,11 @@ __host__ __device__ inline TabSpec table_spec(const DevParams &p)
     return t;
 }
 
-// shared memory: [table float2 (2K+2)] [g scratch double (K+1)] [per-warp run arrays 6 x stride]
+// shared memory: [table float2 (2K+2)] [g scratch double (K+1)] [g float (2K+1)] [per-warp arrays]
 __host__ __device__ inline size_t rle_table_bytes(int K)
 {
-    return (((size_t)(2 * K + 2) * sizeof(float2) + (size_t)(K + 1) * sizeof(double)) + 15) & ~(size_t)15;
+    return (((size_t)(2 * K + 2) * sizeof(float2) + (size_t)(K + 1) * sizeof(double) +
+             (size_t)(2 * K + 1) * sizeof(float)) + 15) & ~(size_t)15;
 }
 
 __global__ void __launch_bounds__(kWarpsRLE * 32)
@@ -325,13 +436,14 @@ __global__ void __launch_bounds__(kWarpsRLE * 32)
     const TabSpec ts = table_spec(p);
     float2 *tab = (float2 *)smem_raw;
     double *gs = (double *)(smem_raw + (size_t)(2 * ts.K + 2) * sizeof(float2));
-    build_table(tab, gs, ts.K, ts.kind, ts.sigma, ts.H, ts.band);
+    float *gtab = (float *)(gs + ts.K + 1);
+    build_table(tab, gs, gtab, ts.K, ts.kind, ts.sigma, ts.H, ts.band);
     const int warp = threadIdx.x >> 5;
-    float *base = (float *)(smem_raw + rle_table_bytes(ts.K)) + (size_t)warp * 6 * stride;
+    float *base = (float *)(smem_raw + rle_table_bytes(ts.K)) + (size_t)warp * kArraysRLE * stride;
     const RunSmem r = run_smem(base, stride);
     for (long long ray = (long long)blockIdx.x * kWarpsRLE + warp; ray < nrays; ray += (long long)gridDim.x * kWarpsRLE) {
         const int nr = sample_encode(vx, ray, p.nmax, p.run_cap, r.O, r.S);
-        const float I = ray_mi(r, nr, p, tab, ts.K, true);
+        const float I = ray_mi(base, stride, nr, p, tab, gtab, ts.K, true);
         if (lane_id() == 0) {
             out[ray] = I;
             if (nruns) nruns[ray] = nr;
@@ -348,9 +460,10 @@ __global__ void __launch_bounds__(kWarpsRLE * 32)
     const TabSpec ts = table_spec(p);
     float2 *tab = (float2 *)smem_raw;
     double *gs = (double *)(smem_raw + (size_t)(2 * ts.K + 2) * sizeof(float2));
-    build_table(tab, gs, ts.K, ts.kind, ts.sigma, ts.H, ts.band);
+    float *gtab = (float *)(gs + ts.K + 1);
+    build_table(tab, gs, gtab, ts.K, ts.kind, ts.sigma, ts.H, ts.band);
     const int warp = threadIdx.x >> 5, lane = lane_id();
-    float *base = (float *)(smem_raw + rle_table_bytes(ts.K)) + (size_t)warp * 6 * stride;
+    float *base = (float *)(smem_raw + rle_table_bytes(ts.K)) + (size_t)warp * kArraysRLE * stride;
     const RunSmem r = run_smem(base, stride);
     for (long long ray = (long long)blockIdx.x * kWarpsRLE + warp; ray < nrays; ray += (long long)gridDim.x * kWarpsRLE) {
         const int b = off[ray];
@@ -377,7 +490,7 @@ __global__ void __launch_bounds__(kWarpsRLE * 32)
             __syncwarp();
             continue;
         }
-        const float I = ray_mi(r, nr, p, tab, ts.K, false);
+        const float I = ray_mi(base, stride, nr, p, tab, gtab, ts.K, false);
         if (lane == 0) out[ray] = I;
         __syncwarp();
     }
@@ -489,7 +602,7 @@ __global__ void k_scan_add(int32_t *a, long long n, const int32_t *tot)
 
 // ---- launchers ---------------------------------------------------------------------------------
 
-static int rle_stride(int nmax) { return ((nmax + 2) + 3) & ~3; }
+static int rle_stride(int nmax, int K) { return ((nmax + 2 * K + 4) + 3) & ~3; }  // cells + 2K padding
 
 template <typename Kern>
 static cudaError_t grid_for(Kern k, size_t smem, long long nitems, long long &grid)
@@ -512,8 +625,8 @@ cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32
 {
     const long long nrays = (long long)v.P * v.R;
     if (nrays <= 0) return cudaSuccess;
-    const int stride = rle_stride(p.nmax);
-    const size_t smem = rle_table_bytes(p.K) + (size_t)kWarpsRLE * 6 * stride * sizeof(float);
+    const int stride = rle_stride(p.nmax, p.K);
+    const size_t smem = rle_table_bytes(p.K) + (size_t)kWarpsRLE * kArraysRLE * stride * sizeof(float);
     long long grid;
     cudaError_t e = grid_for(k_eval_3d, smem, nrays, grid);
     if (e != cudaSuccess) return e;
@@ -525,8 +638,8 @@ cudaError_t launch_eval_rle(const int32_t *run_off, const float *run_o, const ui
                             const DevParams &p, float *out, int *status, cudaStream_t s)
 {
     if (nrays <= 0) return cudaSuccess;
-    const int stride = rle_stride(p.nmax);
-    const size_t smem = rle_table_bytes(p.K) + (size_t)kWarpsRLE * 6 * stride * sizeof(float);
+    const int stride = rle_stride(p.nmax, p.K);
+    const size_t smem = rle_table_bytes(p.K) + (size_t)kWarpsRLE * kArraysRLE * stride * sizeof(float);
     long long grid;
     cudaError_t e = grid_for(k_eval_rle, smem, nrays, grid);
     if (e != cudaSuccess) return e;
@@ -542,7 +655,7 @@ cudaError_t launch_rle_encode_3d(const Vox3D &v, const DevParams &p, int32_t *ru
     if (nrays <= 0) {
         return cudaMemsetAsync(run_off, 0, sizeof(int32_t), s);
     }
-    const int stride = rle_stride(p.nmax);
+    const int stride = rle_stride(p.nmax, 0);
     const size_t smem = (size_t)kWarpsRLE * 2 * stride * sizeof(float);
     long long grid;
     cudaError_t e = grid_for(k_rle_count, smem, nrays, grid);
