@@ -256,10 +256,10 @@ __device__ __forceinline__ int run_of(const int *S, int nr, int i)
 
 // Cell-level evaluation (eq. eqn_from_fsmi) of one ray: decompress the runs into the n virtual
 // cells, form P(e_j) and C_k by warp scans (Algorithms 2 and 3), then
-// I = sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d}. For Theorem 5 as printed, a pair (j, k) in runs
-// u != v is kept only inside the sub-blocks s', L' of eqs. (su')-(Lv'); diagonal blocks are whole.
-// Arrays: 0 run o / run start per cell, 1 run f_occ / run end per cell, 2 run f_emp, 3 P,
-// 4 run starts S, 5 f_emp per cell, 6 C padded by K zeros on both sides.
+// I = sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d} (FSMI-RLE, Uniform-FSMI-RLE, strict-band
+// Approx-FSMI-RLE; Theorem 5's sub-blocks stay on the run-pair path, which is O(n_r Delta)).
+// Arrays: 0 run o, 1 run f_occ, 2 run f_emp, 3 P, 4 run starts S, 5 f_emp per cell,
+// 6 C padded by K zeros on both sides.
 __device__ float ray_mi_cells(float *base, int stride, int nr, int n, const DevParams &p, const float *gtab, int K)
 {
     const int lane = lane_id();
@@ -284,34 +284,10 @@ __device__ float ray_mi_cells(float *base, int stride, int nr, int n, const DevP
     }
     __syncwarp();
     cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
-    const bool thm5 = p.variant == FSMI_APPROX && p.approx_reading == 0;
-    int *RS = (int *)O, *RE = (int *)RFO;
-    if (thm5) {
-        for (int i = lane; i < n; i += 32) {
-            const int u = run_of(S, nr, i);
-            RS[i] = S[u];
-            RE[i] = S[u + 1] - 1;
-        }
-        __syncwarp();
-    }
-    const int D = p.trunc;
     float tot = 0.0f;
     for (int j = lane; j < n; j += 32) {
         float acc = 0.0f;
-        if (!thm5) {
-            for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
-        } else {
-            const int rsj = RS[j], rej = RE[j];
-            for (int d = -K; d <= K; ++d) {
-                const int k = j + d;
-                if ((unsigned)k >= (unsigned)n) continue;
-                const int rsk = RS[k];
-                const bool keep = rsk == rsj ? true
-                                  : rsk > rej ? (j >= rsk - D && k <= rej + D)  // run of k after run of j
-                                              : (j <= RE[k] + D && k >= rsj - D);
-                if (keep) acc = fmaf(gtab[K + d], CC[K + k], acc);
-            }
-        }
+        for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
         tot = fmaf(CP[j], acc, tot);
     }
     return tot;
@@ -324,8 +300,9 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
     const RunSmem r = run_smem(base, stride);
     run_starts(r, nr, have_s);
     const int n = r.S[nr];
+    const bool thm5 = p.variant == FSMI_APPROX && p.approx_reading == 0;
     float v;
-    if (n < kCellRunLen * nr) {
+    if (!thm5 && n < kCellRunLen * nr) {
         v = ray_mi_cells(base, stride, nr, n, p, gtab, K);
     } else {
         run_prefixes(r, nr, p.docc, p.demp);
