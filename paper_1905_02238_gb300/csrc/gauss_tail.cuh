@@ -4,9 +4,10 @@
 //   T(s) = 0.5 * erfc(s / sqrt(log2 e)) ~= 2^(-s^2) * t * P(t),  t = 1 / (1 + p s),  s >= 0,
 //
 // the rational-substitution form of erfc (Hastings; Abramowitz and Stegun 7.1.26) with our own
-// degree-6 coefficients, fitted for minimum absolute error of T by csrc/fit_gauss_tail.py:
-// |T - exact| <= 5.1e-10 in exact arithmetic, <= 1.6e-7 (about 2 ulp of T(0) = 0.5) when
-// evaluated in FP32, and <= 1e-6 T + 2e-9 everywhere. The variable s is a distance scaled by
+// degree-5 coefficients, fitted for minimum absolute error of T by csrc/fit_gauss_tail.py:
+// |T - exact| <= 4.0e-9 in exact arithmetic, <= 1.6e-7 (about 2 ulp of T(0) = 0.5) when
+// evaluated in FP32, and <= 1e-6 T + 2e-8 everywhere. A pair sum adds at most a few dozen such
+// terms per cell with bounded weights, so the tail contributes < 1e-6 relative error to an MI. The variable s is a distance scaled by
 // sqrt(log2 e) / (sigma sqrt 2), so that exp(-z^2) = 2^(-s^2).
 #pragma once
 
@@ -14,15 +15,14 @@
 
 namespace fsmi {
 
-// p = 0.3725, fit max |T error| = 5.06e-10, FP32 max |T error| = 1.57e-07
-constexpr float kTailP = 0.3725000023841858f;
-constexpr float kTailC0 = 0.12908168137073517f;
-constexpr float kTailC1 = 0.097091443836689f;
-constexpr float kTailC2 = 0.23891545832157135f;
-constexpr float kTailC3 = -0.20453312993049622f;
-constexpr float kTailC4 = 0.44375884532928467f;
-constexpr float kTailC5 = -0.2505171000957489f;
-constexpr float kTailC6 = 0.046202804893255234f;
+// p = 0.325, fit max |T error| = 3.95e-09, FP32 max |T error| = 1.59e-07
+constexpr float kTailP = 0.32499998807907104f;
+constexpr float kTailC0 = 0.11761387437582016f;
+constexpr float kTailC1 = 0.046889495104551315f;
+constexpr float kTailC2 = 0.32172489166259766f;
+constexpr float kTailC3 = -0.31325554847717285f;
+constexpr float kTailC4 = 0.44042205810546875f;
+constexpr float kTailC5 = -0.11339477449655533f;
 
 // sqrt(log2(e)): converts z = x / (sigma sqrt 2) into s = z sqrt(log2 e).
 constexpr double kSqrtLog2e = 1.2011224087864498;
@@ -46,8 +46,7 @@ __device__ __forceinline__ float gauss_tail(float d)
 {
     const float e = ex2_approx(-(d * d));
     const float t = rcp_approx(fmaf(kTailP, fabsf(d), 1.0f));
-    float q = kTailC6;
-    q = fmaf(q, t, kTailC5);
+    float q = kTailC5;
     q = fmaf(q, t, kTailC4);
     q = fmaf(q, t, kTailC3);
     q = fmaf(q, t, kTailC2);
@@ -103,8 +102,7 @@ __device__ __forceinline__ void gauss_tail2(f32x2 d, float &T0, float &T1)
     const float e0 = ex2_approx(-dd0), e1 = ex2_approx(-dd1);
     unpack2(fma2(pack2(kTailP, kTailP), d, pack2(1.0f, 1.0f)), den0, den1);
     const f32x2 t = pack2(rcp_approx(den0), rcp_approx(den1));
-    f32x2 q = fma2(pack2(kTailC6, kTailC6), t, pack2(kTailC5, kTailC5));
-    q = fma2(q, t, pack2(kTailC4, kTailC4));
+    f32x2 q = fma2(pack2(kTailC5, kTailC5), t, pack2(kTailC4, kTailC4));
     q = fma2(q, t, pack2(kTailC3, kTailC3));
     q = fma2(q, t, pack2(kTailC2, kTailC2));
     q = fma2(q, t, pack2(kTailC1, kTailC1));
