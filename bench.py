@@ -211,7 +211,7 @@ def other_variants(g, p, d, out):  # noqa: C901
                      ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
                      ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4))):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)
-        gains_ws = torch.empty(16 * g.numel(), dtype=torch.uint8, device=g.device)
+        gains_ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=g.device)
         ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out, ws=gains_ws))
         res[name] = {"beams_per_s": nb / (ms * 1e-3), "ms": ms}
     vox, vp, vd = synth.config3()

@@ -88,6 +88,33 @@ typedef struct {
  * forces the full sweep (for verification and timing comparisons). */
 #define FSMI_FLAG_FULL_SWEEP 0x1
 
+/*
+ * Launch schedule of the evaluation kernels (fsmi_eval_2d, fsmi_eval_2d_sets, fsmi_eval_beams,
+ * fsmi_eval_rle, fsmi_eval_3d). The paper fixes no schedule; this one only changes how beams are
+ * dealt to warps and how many warps share a block, never which terms are summed (the RLE cell
+ * form below sums the same terms as the run-pair form, in another order). One warp evaluates one
+ * beam (or ray) at a time in every schedule; the kernels are persistent (at most as many blocks
+ * as fit on the GPU at once), so a grid never depends on the batch beyond its size.
+ */
+typedef struct {
+    int warps_per_block; /* 1 .. 8 warps per block; 0 = default (4). Lowered for a call whose
+                            per-warp shared arrays would not fit in one block */
+    int blocks_per_sm;   /* cap on resident blocks per SM; 0 = as many as fit */
+    int queue_chunk;     /* > 0: warps take beams from an atomic work queue, this many consecutive
+                            beams per grab, which balances beams of very different lengths; needs a
+                            workspace (without one, beams are dealt statically). 0 = static
+                            grid-stride assignment (default) */
+    int cell_runlen;     /* RLE variants other than Theorem 5's sub-blocks: a ray whose mean run
+                            length is below this is evaluated per virtual cell (a banded
+                            convolution, O(n K)) instead of per run pair (O(n_r^2)); 0 = default (16) */
+} fsmi_schedule;
+
+/* Sets the calling thread's schedule (NULL restores the defaults). FSMI_ERR_ARG if a field is out
+ * of range. The schedule is read when a call enqueues its kernels. */
+fsmi_status fsmi_set_schedule(const fsmi_schedule *sched);
+/* The calling thread's schedule, defaults filled in. */
+fsmi_status fsmi_get_schedule(fsmi_schedule *sched);
+
 /* Documented maxima. */
 #define FSMI_MAX_GRID 32767        /* W, H (2D) and X, Y, Z (3D) */
 #define FSMI_MAX_RANGE_2D 1024.0f  /* cells; a 2D beam then crosses at most 1451 cells */
@@ -105,17 +132,50 @@ typedef struct {
  *   dirs   int32 [B][2]: beam unit vectors in the sensor frame (Q30). Beam b of pose p points
  *          along d = floor((Rot(yaw_p) dirs[b] + 2^29) / 2^30).
  *   out    float32 [P][B], nats.
- *   ws     optional device workspace (NULL allowed), 16-byte aligned, of at least
- *          fsmi_workspace_size(FSMI_FN_EVAL_2D, W*H) bytes. With it, when the batch visits more
- *          cells than the map holds, the per-cell gains f(delta_occ, r), f(delta_emp, r) are
- *          computed once per map cell (like the paper's look-up table of f, Section 3.3, but exact
- *          per cell) instead of once per visit; the results are the same bit for bit.
+ *   ws     optional device workspace (NULL allowed), 16-byte aligned. Its first
+ *          FSMI_QUEUE_BYTES hold the work-queue counter (fsmi_schedule.queue_chunk). With
+ *          fsmi_workspace_size(FSMI_FN_EVAL_2D, W*H) bytes, when the batch visits more cells than
+ *          the map holds, the per-cell gains f(delta_occ, r), f(delta_emp, r) are computed once
+ *          per map cell (like the paper's look-up table of f, Section 3.3, but exact per cell)
+ *          instead of once per visit; the results are the same bit for bit. Calls that share a
+ *          workspace must not overlap on the GPU.
  * The traversal is exact integer arithmetic: a cell is entered while its entry distance is
  * < max_range and it lies inside the grid; simultaneous x/y crossings are one diagonal step.
  */
 fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, int P,
                          const int32_t *dirs, int B, const fsmi_params *prm, float *out,
                          void *ws, size_t ws_bytes, fsmi_stream_t stream);
+
+/*
+ * fsmi_eval_2d_sets - fsmi_eval_2d over several candidate sets in one launch: each set has its
+ * own poses, beam directions, beam count and range (beams of very different lengths, Table 1's
+ * O(n^2) cost per beam, share one persistent kernel; pair it with a work queue).
+ *   poses  int32 [P][4], dirs int32 [B][2]: as fsmi_eval_2d; sets index into them.
+ *   sets   device array of nsets descriptors (below), in increasing beam_offset order with
+ *          sets[0].beam_offset = 0 and beam_offset[s+1] = beam_offset[s] + npose[s] * nbeam[s];
+ *          nbeams = the sum of npose * nbeam.
+ *   prm    as fsmi_eval_2d; prm->max_range bounds every set's max_range (it sizes the per-beam
+ *          capacity).
+ *   out    float32 [nbeams]: out[beam_offset + p * nbeam + b] for pose p and beam b of a set.
+ *   ws     as fsmi_eval_2d (workspace size from fsmi_workspace_size(FSMI_FN_EVAL_2D, W*H)).
+ * The descriptors live in device memory and are checked by the kernel: a beam whose set indexes
+ * past P or B, has a max_range outside (0, prm->max_range], or is not covered by its set, gets NaN
+ * and sets FSMI_STATUS_BAD_BEAM.
+ */
+typedef struct {
+    int pose_offset;       /* first pose of the set in `poses` */
+    int npose;             /* poses in the set, >= 0 */
+    int dir_offset;        /* first beam direction of the set in `dirs` */
+    int nbeam;             /* beams per pose, >= 0 */
+    float max_range;       /* beam length of this set, cells */
+    int reserved;          /* 0 */
+    long long beam_offset; /* first output index of the set */
+} fsmi_set_2d;
+
+fsmi_status fsmi_eval_2d_sets(const float *map, int W, int H, const int32_t *poses, int P,
+                              const int32_t *dirs, int B, const fsmi_set_2d *sets, int nsets,
+                              long long nbeams, const fsmi_params *prm, float *out, void *ws,
+                              size_t ws_bytes, fsmi_stream_t stream);
 
 /*
  * fsmi_eval_beams - the same pair sums on explicit beams (Theorem 1's inputs: o_i, l_i).
@@ -125,9 +185,11 @@ fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, i
  *   l      float32 [off[nbeams]] entry distances, increasing within a beam, first one 0.
  *   lend   float32 [nbeams] end distance l_{n+1} of each beam.
  *   out    float32 [nbeams], nats.
+ *   ws     optional workspace of FSMI_QUEUE_BYTES (16-byte aligned) for the work queue.
  */
 fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend,
-                            int nbeams, const fsmi_params *prm, float *out, fsmi_stream_t stream);
+                            int nbeams, const fsmi_params *prm, float *out, void *ws,
+                            size_t ws_bytes, fsmi_stream_t stream);
 
 /*
  * fsmi_trace_2d - exports the traversal used by fsmi_eval_2d (same inputs) so that cell lists
@@ -190,18 +252,21 @@ fsmi_status fsmi_rle_encode_3d_noalloc(const float *vox, int X, int Y, int Z, co
  *            lengths sum to at most FSMI_MAX_SAMPLES_3D virtual cells.
  *   run_o    float32 occupancy of each run; run_len uint8 length (>= 1) of each run.
  *   out      float32 [nrays], nats.
+ *   ws       optional workspace of FSMI_QUEUE_BYTES (16-byte aligned) for the work queue.
  */
 fsmi_status fsmi_eval_rle(const int32_t *run_off, const float *run_o, const uint8_t *run_len,
-                          int nrays, const fsmi_params *prm, float *out, fsmi_stream_t stream);
+                          int nrays, const fsmi_params *prm, float *out, void *ws, size_t ws_bytes,
+                          fsmi_stream_t stream);
 
 /*
  * fsmi_eval_3d - fused 3D path: sampling, run-length encoding and the RLE variant of every ray,
  * with the runs kept on chip. Same inputs as fsmi_rle_encode_3d; out float32 [P][R] in nats;
- * nruns (optional, may be NULL) int32 [P][R] receives each ray's run count.
+ * nruns (optional, may be NULL) int32 [P][R] receives each ray's run count; ws optional
+ * workspace of FSMI_QUEUE_BYTES (16-byte aligned) for the work queue.
  */
 fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *poses, int P,
                          const int32_t *dirs, int R, const fsmi_params *prm, float *out,
-                         int32_t *nruns, fsmi_stream_t stream);
+                         int32_t *nruns, void *ws, size_t ws_bytes, fsmi_stream_t stream);
 
 /*
  * fsmi_gauss_tail - the library's Gaussian tail, exposed so its accuracy can be tested:
@@ -219,9 +284,47 @@ fsmi_status fsmi_gauss_tail(const float *s, float *out, long long n, fsmi_stream
 #define FSMI_FN_EVAL_RLE 3
 #define FSMI_FN_EVAL_3D 4
 
-/* Bytes of device workspace entry point `fn` can use for `nitems` items (0 if none): map cells
- * for FSMI_FN_EVAL_2D (optional gains), rays for FSMI_FN_RLE_ENCODE_3D (required offset scan). */
+/* Bytes at the front of an evaluation workspace that hold the work-queue counter. */
+#define FSMI_QUEUE_BYTES 256
+
+/* Bytes of device workspace entry point `fn` can use for `nitems` items: map cells for
+ * FSMI_FN_EVAL_2D (queue counter + optional gains; also fsmi_eval_2d_sets), rays for
+ * FSMI_FN_RLE_ENCODE_3D (required offset scan), FSMI_QUEUE_BYTES for the other evaluations. */
 fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm, size_t *bytes);
+
+/*
+ * Native schedule tuning and CUDA-graph helpers (library conveniences; the paper has none).
+ *
+ * fsmi_autotune - times `fn(ctx, stream)` (which makes one or more fsmi_* calls on `stream`) under
+ * each of the ncands schedules: one untimed call, then `reps` calls between two CUDA events. On
+ * return the calling thread's schedule is the fastest one, copied to *best; ms (optional, host
+ * float [ncands]) receives each candidate's mean milliseconds per call, or -1 where fn failed.
+ * FSMI_ERR_ARG if every candidate failed. fn must not capture or synchronise other streams.
+ */
+typedef fsmi_status (*fsmi_tune_fn)(void *ctx, fsmi_stream_t stream);
+fsmi_status fsmi_autotune(fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands, int ncands,
+                          int reps, fsmi_stream_t stream, fsmi_schedule *best, float *ms);
+
+/* Default candidate schedules for fsmi_autotune (every field filled in, as fsmi_get_schedule
+ * reports them): kind 0 = 2D evaluations (2, 4, 8 warps x static, chunk 1, chunk 4), 1 = RLE / 3D
+ * evaluations (the same x cell_runlen 8, 16, 32). Writes at most `max` entries to out (host) and
+ * their number to *n. */
+fsmi_status fsmi_schedule_candidates(int kind, fsmi_schedule *out, int max, int *n);
+
+/* Does every per-device lookup and kernel load of the library on the current device, so that
+ * fsmi_* calls can then be captured into a CUDA graph. */
+fsmi_status fsmi_prepare(void);
+
+/* Stream capture of fsmi_* calls into a replayable graph. `stream` must not be the legacy
+ * default stream (NULL). Between begin and end, make only asynchronous calls on `stream`
+ * (fsmi_device_status synchronises and is not allowed). Workspace queue counters are reset by a
+ * captured memset, so a graph can be replayed any number of times; replays of one graph, or of
+ * graphs sharing a workspace, must not overlap on the GPU. */
+typedef struct fsmi_graph_st *fsmi_graph;
+fsmi_status fsmi_capture_begin(fsmi_stream_t stream);
+fsmi_status fsmi_capture_end(fsmi_stream_t stream, fsmi_graph *graph);
+fsmi_status fsmi_graph_launch(fsmi_graph graph, fsmi_stream_t stream);
+fsmi_status fsmi_graph_destroy(fsmi_graph graph);
 
 /* Waits for `stream`, then returns in *status the current device's status word (FSMI_STATUS_*
  * bits, 0 if clean) and clears it. *status is host memory. */

@@ -203,8 +203,10 @@ constexpr int kArrays2D = 4;
 // internal variant id of the full n(n+1) exact sweep (FSMI_FLAG_FULL_SWEEP)
 constexpr int kExactFullSweep = 3;
 
+enum { kSrcMap = 0, kSrcBeams = 1, kSrcSets = 2 };
+
 struct Src2D {
-    // map source
+    // map source (kSrcMap, kSrcSets)
     const float *map;
     int W, H;
     const int32_t *poses;
@@ -212,11 +214,14 @@ struct Src2D {
     const int32_t *dirs;
     int B;
     const float4 *gains;  // optional per-map-cell (o, f_occ, f_emp, 0)
-    // explicit-beam source
+    // explicit-beam source (kSrcBeams)
     const int32_t *off;
     const float *o;
     const float *l;
     const float *lend;
+    // candidate sets (kSrcSets): device array of nsets descriptors
+    const fsmi_set_2d *sets;
+    int nsets;
 };
 
 // One register-blocked pass of the exact pair sum over scaled distances: each lane owns J
@@ -420,97 +425,162 @@ __device__ __forceinline__ float uniform_sum(const float *sd, const float *sp, i
 #define FSMI_MIN_BLOCKS_2D 1  // minimum resident blocks per SM requested from the register allocator
 #endif
 
-template <int VAR, bool FROM_MAP>
-__global__ void __launch_bounds__(kWarps2D * 32, FSMI_MIN_BLOCKS_2D)
-    k_eval_2d(Src2D src, DevParams p, long long nbeams, int stride, float *__restrict__ out, int *status)
+// the candidate set holding flat beam index `beam` (sets sorted by beam_offset)
+__device__ __forceinline__ int set_of(const fsmi_set_2d *sets, int nsets, long long beam)
 {
-    extern __shared__ float smem[];
-    const int lane = lane_id(), warp = threadIdx.x >> 5;
-    float *sl = smem + (size_t)warp * kArrays2D * stride;
-    float *sc = sl + stride;
-    float *sp = sc + stride;
-    float *sx = sp + stride;
+    int lo = 0, len = nsets;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (__ldg(&sets[lo + half].beam_offset) <= beam) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo - 1;
+}
+
+// One beam: traversal (or explicit cells), gains, prefixes, the variant's pair sum, store.
+template <int VAR, int SRC>
+__device__ __forceinline__ void eval_beam(const Src2D &src, const DevParams &p, long long beam, float *sl, float *sc,
+                                          float *sp, float *sx, float *__restrict__ out, int *status)
+{
+    const int lane = lane_id();
     const bool e0 = p.e0 != 0;
     const float cs = p.inv_s2 * (float)kSqrtLog2e;  // distance -> tail variable
-    for (long long beam = (long long)blockIdx.x * kWarps2D + warp; beam < nbeams;
-         beam += (long long)gridDim.x * kWarps2D) {
-        int n;
-        if (FROM_MAP) {
+    int n;
+    if (SRC != kSrcBeams) {
+        const int32_t *pose;
+        int ux, uy;
+        long long rfix = p.rfix;
+        float rend = p.rend;
+        int cap = p.nmax;
+        if (SRC == kSrcMap) {
             const int pi = (int)(beam / src.B), bi = (int)(beam % src.B);
-            const int32_t *pose = src.poses + 4 * (size_t)pi;
-            int dx, dy;
-            beam_dir(pose, src.dirs[2 * bi], src.dirs[2 * bi + 1], dx, dy);
-            n = dda_warp(src.W, src.H, pose[0], pose[1], dx, dy, p.rfix, p.rend, p.nmax, (int *)sx, sl);
-            if (n < 0) {
-                if (lane == 0) {
-                    out[beam] = __int_as_float(0x7fc00000);
-                    set_status(status, FSMI_STATUS_BEAM_OVERFLOW);
-                }
-                __syncwarp();
-                continue;
-            }
-            const unsigned ncell = (unsigned)src.W * (unsigned)src.H;
-            bool bad = false;
-            if (src.gains) {
-                for (int i = lane; i < n; i += 32) {
-                    const unsigned id = (unsigned)((const int *)sx)[i];
-                    bad |= id >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
-                    const float4 v = id < ncell ? __ldg(src.gains + id) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    sp[i] = v.x;
-                    sc[i] = v.y;
-                    sx[i] = v.z;
-                }
-            } else {
-                for (int i = lane; i < n; i += 32) {
-                    const unsigned id = (unsigned)((const int *)sx)[i];
-                    bad |= id >= ncell;
-                    const float o = id < ncell ? __ldg(src.map + id) : 0.0f;
-                    sp[i] = o;
-                    sc[i] = cell_gain(p.docc, o);
-                    sx[i] = cell_gain(p.demp, o);
-                }
-            }
-            if (__any_sync(kFull, bad) && lane == 0) set_status(status, FSMI_STATUS_INTERNAL);
+            pose = src.poses + 4 * (size_t)pi;
+            ux = src.dirs[2 * bi];
+            uy = src.dirs[2 * bi + 1];
         } else {
-            const int base = src.off[beam];
-            n = src.off[beam + 1] - base;
-            if (n < 0 || n > p.nmax) {
+            const int si = set_of(src.sets, src.nsets, beam);
+            bool ok = si >= 0;
+            fsmi_set_2d st{};
+            if (ok) st = src.sets[si];
+            const long long k = beam - st.beam_offset;
+            const long long nb = (long long)st.npose * st.nbeam;
+            ok = ok && st.npose >= 0 && st.nbeam > 0 && k >= 0 && k < nb;
+            long long pi = 0, bi = 0;
+            if (ok) {
+                pi = st.pose_offset + k / st.nbeam;
+                bi = st.dir_offset + k % st.nbeam;
+                ok = st.pose_offset >= 0 && st.dir_offset >= 0 && pi < src.P && bi < src.B;
+            }
+            if (ok) {
+                ok = st.max_range > 0.0f && st.max_range <= p.rmax;
+                rfix = __double2ll_rn((double)st.max_range * 65536.0);
+                rend = (float)((double)rfix * (1.0 / 65536.0));
+            }
+            if (!ok) {  // malformed descriptor: never index with it
                 if (lane == 0) {
                     out[beam] = __int_as_float(0x7fc00000);
                     set_status(status, FSMI_STATUS_BAD_BEAM);
                 }
-                continue;
+                return;
             }
+            pose = src.poses + 4 * (size_t)pi;
+            ux = src.dirs[2 * bi];
+            uy = src.dirs[2 * bi + 1];
+        }
+        int dx, dy;
+        beam_dir(pose, ux, uy, dx, dy);
+        n = dda_warp(src.W, src.H, pose[0], pose[1], dx, dy, rfix, rend, cap, (int *)sx, sl);
+        if (n < 0) {
+            if (lane == 0) {
+                out[beam] = __int_as_float(0x7fc00000);
+                set_status(status, FSMI_STATUS_BEAM_OVERFLOW);
+            }
+            __syncwarp();
+            return;
+        }
+        const unsigned ncell = (unsigned)src.W * (unsigned)src.H;
+        bool bad = false;
+        if (src.gains) {
             for (int i = lane; i < n; i += 32) {
-                const float o = __ldg(src.o + base + i);
-                sl[i] = __ldg(src.l + base + i);
+                const unsigned id = (unsigned)((const int *)sx)[i];
+                bad |= id >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
+                const float4 v = id < ncell ? __ldg(src.gains + id) : make_float4(0.f, 0.f, 0.f, 0.f);
+                sp[i] = v.x;
+                sc[i] = v.y;
+                sx[i] = v.z;
+            }
+        } else {
+            for (int i = lane; i < n; i += 32) {
+                const unsigned id = (unsigned)((const int *)sx)[i];
+                bad |= id >= ncell;
+                const float o = id < ncell ? __ldg(src.map + id) : 0.0f;
                 sp[i] = o;
                 sc[i] = cell_gain(p.docc, o);
                 sx[i] = cell_gain(p.demp, o);
             }
-            if (lane == 0) sl[n] = __ldg(src.lend + beam);
         }
-        __syncwarp();
-        float I = 0.0f;
-        if (n > 0) {
-            if (VAR != FSMI_UNIFORM) {
-                for (int i = lane; i <= n; i += 32) sl[i] *= cs;
+        if (__any_sync(kFull, bad) && lane == 0) set_status(status, FSMI_STATUS_INTERNAL);
+    } else {
+        const int base = src.off[beam];
+        n = src.off[beam + 1] - base;
+        if (n < 0 || n > p.nmax) {
+            if (lane == 0) {
+                out[beam] = __int_as_float(0x7fc00000);
+                set_status(status, FSMI_STATUS_BAD_BEAM);
             }
-            const float pe0 = cell_prefixes(sp, sc, sx, n, VAR == FSMI_UNIFORM);
-            const float mu0 = sl[0] - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
-            if (VAR == kExactFullSweep) I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
-            if (VAR == FSMI_EXACT) {
-                for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
-                __syncwarp();
-                I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0);
-            }
-            if (VAR == FSMI_APPROX) I = approx_sum(sl, sc, sp, n, e0, pe0, mu0, p.trunc);
-            if (VAR == FSMI_UNIFORM) I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
-            I = warp_sum(I);
+            return;
         }
-        if (lane == 0) out[beam] = I;
-        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const float o = __ldg(src.o + base + i);
+            sl[i] = __ldg(src.l + base + i);
+            sp[i] = o;
+            sc[i] = cell_gain(p.docc, o);
+            sx[i] = cell_gain(p.demp, o);
+        }
+        if (lane == 0) sl[n] = __ldg(src.lend + beam);
     }
+    __syncwarp();
+    float I = 0.0f;
+    if (n > 0) {
+        if (VAR != FSMI_UNIFORM) {
+            for (int i = lane; i <= n; i += 32) sl[i] *= cs;
+        }
+        const float pe0 = cell_prefixes(sp, sc, sx, n, VAR == FSMI_UNIFORM);
+        const float mu0 = sl[0] - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
+        if (VAR == kExactFullSweep) I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
+        if (VAR == FSMI_EXACT) {
+            for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
+            __syncwarp();
+            I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0);
+        }
+        if (VAR == FSMI_APPROX) I = approx_sum(sl, sc, sp, n, e0, pe0, mu0, p.trunc);
+        if (VAR == FSMI_UNIFORM) I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
+        I = warp_sum(I);
+    }
+    if (lane == 0) out[beam] = I;
+    __syncwarp();
+}
+
+// Persistent kernel: each warp evaluates beams one at a time, either in a static grid-stride
+// order or, with a work queue, taking `chunk` consecutive beams per atomic grab (balances beams
+// of very different lengths). The queue counter must be zero at launch.
+template <int VAR, int SRC>
+__global__ void __launch_bounds__(kMaxWarps * 32, FSMI_MIN_BLOCKS_2D)
+    k_eval_2d(Src2D src, DevParams p, long long nbeams, int stride, float *__restrict__ out, int *status,
+              unsigned long long *queue, int chunk)
+{
+    extern __shared__ float smem[];
+    const int lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    float *sl = smem + (size_t)warp * kArrays2D * stride;
+    float *sc = sl + stride;
+    float *sp = sc + stride;
+    float *sx = sp + stride;
+    for_each_item(nbeams, queue, chunk,
+                  [&](long long beam) { eval_beam<VAR, SRC>(src, p, beam, sl, sc, sp, sx, out, status); });
 }
 
 __global__ void __launch_bounds__(128)
@@ -548,62 +618,114 @@ __global__ void k_gauss_tail(const float *__restrict__ s, float *__restrict__ ou
         out[i] = gauss_tail(s[i]);
 }
 
-template <int VAR, bool FROM_MAP>
+
+template <int VAR, int SRC>
 static cudaError_t launch_variant(const Src2D &src, const DevParams &p, long long nbeams, float *out, int *status,
-                                  cudaStream_t s)
+                                  unsigned long long *queue, cudaStream_t s)
 {
+    const Schedule &sc = current_schedule();
     const int stride = ((p.nmax + 2) + 3) & ~3;
-    const size_t smem = (size_t)kWarps2D * kArrays2D * stride * sizeof(float);
-    auto kern = k_eval_2d<VAR, FROM_MAP>;
+    const size_t per_warp = (size_t)kArrays2D * stride * sizeof(float);
+    const int wpb = fit_warps(sc.warps_per_block, per_warp, 0);
+    const size_t smem = (size_t)wpb * per_warp;
+    auto kern = k_eval_2d<VAR, SRC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps2D * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    long long want = (nbeams + kWarps2D - 1) / kWarps2D;
+    if (sc.blocks_per_sm > 0 && sc.blocks_per_sm < occ) occ = sc.blocks_per_sm;
+    long long want = (nbeams + wpb - 1) / wpb;
     long long grid = (long long)sm_count() * occ;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kWarps2D * 32, smem, s>>>(src, p, nbeams, stride, out, status);
+    if (queue) {
+        e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(src, p, nbeams, stride, out, status, queue,
+                                                 sc.queue_chunk > 0 ? sc.queue_chunk : 1);
     return cudaGetLastError();
 }
 
-template <bool FROM_MAP>
+template <int SRC>
 static cudaError_t dispatch(const Src2D &src, const DevParams &p, long long nbeams, float *out, int *status,
-                            cudaStream_t s)
+                            unsigned long long *queue, cudaStream_t s)
 {
     if (nbeams <= 0) return cudaSuccess;
     switch (p.variant) {
         case FSMI_EXACT:
-            if (p.flags & FSMI_FLAG_FULL_SWEEP) return launch_variant<kExactFullSweep, FROM_MAP>(src, p, nbeams, out, status, s);
-            return launch_variant<FSMI_EXACT, FROM_MAP>(src, p, nbeams, out, status, s);
-        case FSMI_APPROX: return launch_variant<FSMI_APPROX, FROM_MAP>(src, p, nbeams, out, status, s);
-        default: return launch_variant<FSMI_UNIFORM, FROM_MAP>(src, p, nbeams, out, status, s);
+            if (p.flags & FSMI_FLAG_FULL_SWEEP) return launch_variant<kExactFullSweep, SRC>(src, p, nbeams, out, status, queue, s);
+            return launch_variant<FSMI_EXACT, SRC>(src, p, nbeams, out, status, queue, s);
+        case FSMI_APPROX: return launch_variant<FSMI_APPROX, SRC>(src, p, nbeams, out, status, queue, s);
+        default: return launch_variant<FSMI_UNIFORM, SRC>(src, p, nbeams, out, status, queue, s);
     }
+}
+
+static cudaError_t map_gains(const float *map, int W, int H, const DevParams &p, float4 *gains, cudaStream_t s)
+{
+    const long long ncell = (long long)W * H;
+    long long grid = (ncell + 255) / 256;
+    const long long gmax = (long long)sm_count() * 16;
+    if (grid > gmax) grid = gmax;
+    k_map_gains<<<(unsigned)grid, 256, 0, s>>>(map, ncell, p.docc, p.demp, gains);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
-                           const DevParams &p, float *out, float4 *gains, int *status, cudaStream_t s)
+                           const DevParams &p, float *out, float4 *gains, unsigned long long *queue, int *status,
+                           cudaStream_t s)
 {
     if (gains) {
-        const long long ncell = (long long)W * H;
-        long long grid = (ncell + 255) / 256;
-        const long long gmax = (long long)sm_count() * 16;
-        if (grid > gmax) grid = gmax;
-        k_map_gains<<<(unsigned)grid, 256, 0, s>>>(map, ncell, p.docc, p.demp, gains);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = map_gains(map, W, H, p, gains, s);
         if (e != cudaSuccess) return e;
     }
-    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr};
-    return dispatch<true>(src, p, (long long)P * B, out, status, s);
+    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    return dispatch<kSrcMap>(src, p, (long long)P * B, out, status, queue, s);
+}
+
+cudaError_t launch_eval_2d_sets(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs,
+                                int B, const fsmi_set_2d *sets, int nsets, long long nbeams, const DevParams &p, float *out,
+                                float4 *gains, unsigned long long *queue, int *status, cudaStream_t s)
+{
+    if (gains) {
+        cudaError_t e = map_gains(map, W, H, p, gains, s);
+        if (e != cudaSuccess) return e;
+    }
+    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr, sets, nsets};
+    return dispatch<kSrcSets>(src, p, nbeams, out, status, queue, s);
 }
 
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
-                              const DevParams &p, float *out, int *status, cudaStream_t s)
+                              const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s)
 {
-    Src2D src{nullptr, 0, 0, nullptr, 0, nullptr, 0, nullptr, off, o, l, lend};
-    return dispatch<false>(src, p, nbeams, out, status, s);
+    Src2D src{nullptr, 0, 0, nullptr, 0, nullptr, 0, nullptr, off, o, l, lend, nullptr, 0};
+    return dispatch<kSrcBeams>(src, p, nbeams, out, status, queue, s);
+}
+
+// Loads every 2D kernel on the current device (a kernel's first use loads it lazily).
+template <int SRC>
+static cudaError_t prepare_src()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_2d<FSMI_EXACT, SRC>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_2d<kExactFullSweep, SRC>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_2d<FSMI_APPROX, SRC>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_2d<FSMI_UNIFORM, SRC>);
+    return e;
+}
+
+cudaError_t prepare_2d()
+{
+    cudaError_t e = prepare_src<kSrcMap>();
+    if (e == cudaSuccess) e = prepare_src<kSrcBeams>();
+    if (e == cudaSuccess) e = prepare_src<kSrcSets>();
+    cudaFuncAttributes a;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_map_gains);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_trace_2d);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_gauss_tail);
+    return e;
 }
 
 cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,

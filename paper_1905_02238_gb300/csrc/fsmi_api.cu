@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <new>
 
 #include "../../include/fsmi.h"
 #include "fsmi_internal.h"
@@ -17,7 +18,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 int *g_status_ptr[kMaxDevices];
 int g_sms[kMaxDevices];
+int g_smem_optin[kMaxDevices];
 thread_local int g_last_cuda = 0;
+
+constexpr Schedule kDefaultSchedule{4, 0, 0, 16};
+thread_local Schedule g_schedule = kDefaultSchedule;
 
 int current_device()
 {
@@ -80,6 +85,8 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     d.g_kernel = prm->g_kernel;
     d.approx_reading = prm->approx_reading;
     d.flags = prm->flags;
+    d.cell_runlen = g_schedule.cell_runlen;
+    d.rmax = prm->max_range;
     d.rfix = 0;
     d.rend = 0.0f;
     d.K = 0;
@@ -110,7 +117,54 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
 }
 
 bool grid_ok(int v) { return v >= 1 && v <= FSMI_MAX_GRID; }
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+// Work-queue counter at the front of a workspace, when the schedule asks for a queue and the
+// workspace holds one.
+unsigned long long *queue_of(void *ws, size_t ws_bytes)
+{
+    if (g_schedule.queue_chunk <= 0 || !ws || !aligned16(ws) || ws_bytes < kQueueBytes) return nullptr;
+    return (unsigned long long *)ws;
+}
+
+// Per-map-cell gains behind the queue counter, when the workspace fits them and the batch visits
+// more cells (up to nbeams * nmax, half that on average) than the map holds.
+float4 *gains_of(void *ws, size_t ws_bytes, long long cells, long long nbeams, int nmax)
+{
+    if (!ws || !aligned16(ws) || ws_bytes < kQueueBytes + (size_t)cells * sizeof(float4)) return nullptr;
+    if (nbeams * (nmax / 2) < cells) return nullptr;
+    return (float4 *)((char *)ws + kQueueBytes);
+}
+
+bool schedule_ok(const fsmi_schedule &s)
+{
+    return s.warps_per_block >= 0 && s.warps_per_block <= kMaxWarps && s.blocks_per_sm >= 0 && s.blocks_per_sm <= 64 &&
+           s.queue_chunk >= 0 && s.queue_chunk <= 1 << 20 && s.cell_runlen >= 0 && s.cell_runlen <= 1 << 20;
+}
+
+Schedule to_internal(const fsmi_schedule &s)
+{
+    Schedule r;
+    r.warps_per_block = s.warps_per_block ? s.warps_per_block : kDefaultSchedule.warps_per_block;
+    r.blocks_per_sm = s.blocks_per_sm;
+    r.queue_chunk = s.queue_chunk;
+    r.cell_runlen = s.cell_runlen ? s.cell_runlen : kDefaultSchedule.cell_runlen;
+    return r;
+}
+
+fsmi_schedule to_public(const Schedule &s)
+{
+    fsmi_schedule r;
+    r.warps_per_block = s.warps_per_block;
+    r.blocks_per_sm = s.blocks_per_sm;
+    r.queue_chunk = s.queue_chunk;
+    r.cell_runlen = s.cell_runlen;
+    return r;
+}
 }  // namespace
+
+const Schedule &current_schedule() { return g_schedule; }
 
 int sm_count()
 {
@@ -123,6 +177,23 @@ int sm_count()
         g_sms[dev] = v > 0 ? v : 1;
     }
     return g_sms[dev];
+}
+
+int fit_warps(int warps, size_t per_warp, size_t fixed)
+{
+    const int dev = current_device();
+    int cap = 0;
+    if (dev >= 0 && dev < kMaxDevices) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_smem_optin[dev]) {
+            int v = 0;
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            g_smem_optin[dev] = v > 0 ? v : 48 * 1024;
+        }
+        cap = g_smem_optin[dev];
+    }
+    while (warps > 1 && fixed + (size_t)warps * per_warp > (size_t)cap) --warps;
+    return warps;
 }
 
 }  // namespace fsmi
@@ -142,19 +213,33 @@ fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, i
     if (!map || !poses || !dirs || !out) return FSMI_ERR_ARG;
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
-    // per-cell gains once per map cell when the workspace fits and the batch visits more cells
-    // (up to P*B*nmax) than the map holds
-    const long long cells = (long long)W * H;
-    float4 *gains = nullptr;
-    if (ws && ((uintptr_t)ws & 15) == 0 && ws_bytes >= (size_t)cells * sizeof(float4) &&
-        (long long)P * B * (d.nmax / 2) >= cells)
-        gains = (float4 *)ws;
-    cudaError_t e = launch_eval_2d(map, W, H, poses, P, dirs, B, d, out, gains, sp, (cudaStream_t)stream);
+    const long long nbeams = (long long)P * B;
+    cudaError_t e = launch_eval_2d(map, W, H, poses, P, dirs, B, d, out,
+                                   gains_of(ws, ws_bytes, (long long)W * H, nbeams, d.nmax), queue_of(ws, ws_bytes), sp,
+                                   (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_eval_2d_sets(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                              const fsmi_set_2d *sets, int nsets, long long nbeams, const fsmi_params *prm, float *out,
+                              void *ws, size_t ws_bytes, fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUse2D, d);
+    if (st != FSMI_OK) return st;
+    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || nsets < 0 || nbeams < 0) return FSMI_ERR_ARG;
+    if (nbeams == 0) return FSMI_OK;
+    if (nsets == 0 || !map || !poses || !dirs || !sets || !out) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_eval_2d_sets(map, W, H, poses, P, dirs, B, sets, nsets, nbeams, d, out,
+                                        gains_of(ws, ws_bytes, (long long)W * H, nbeams, d.nmax),
+                                        queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
 fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
-                            const fsmi_params *prm, float *out, fsmi_stream_t stream)
+                            const fsmi_params *prm, float *out, void *ws, size_t ws_bytes, fsmi_stream_t stream)
 {
     DevParams d;
     fsmi_status st = make_params(prm, kUseBeams, d);
@@ -164,7 +249,7 @@ fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, 
     if (!off || !o || !l || !lend || !out) return FSMI_ERR_ARG;
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
-    cudaError_t e = launch_eval_beams(off, o, l, lend, nbeams, d, out, sp, (cudaStream_t)stream);
+    cudaError_t e = launch_eval_beams(off, o, l, lend, nbeams, d, out, queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -231,7 +316,7 @@ fsmi_status fsmi_rle_encode_3d_noalloc(const float *vox, int X, int Y, int Z, co
 }
 
 fsmi_status fsmi_eval_rle(const int32_t *run_off, const float *run_o, const uint8_t *run_len, int nrays,
-                          const fsmi_params *prm, float *out, fsmi_stream_t stream)
+                          const fsmi_params *prm, float *out, void *ws, size_t ws_bytes, fsmi_stream_t stream)
 {
     DevParams d;
     fsmi_status st = make_params(prm, kUseRLE, d);
@@ -241,12 +326,14 @@ fsmi_status fsmi_eval_rle(const int32_t *run_off, const float *run_o, const uint
     if (!run_off || !run_o || !run_len || !out) return FSMI_ERR_ARG;
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
-    cudaError_t e = launch_eval_rle(run_off, run_o, run_len, nrays, d, out, sp, (cudaStream_t)stream);
+    cudaError_t e =
+        launch_eval_rle(run_off, run_o, run_len, nrays, d, out, queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
 fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *poses, int P, const int32_t *dirs,
-                         int R, const fsmi_params *prm, float *out, int32_t *nruns, fsmi_stream_t stream)
+                         int R, const fsmi_params *prm, float *out, int32_t *nruns, void *ws, size_t ws_bytes,
+                         fsmi_stream_t stream)
 {
     DevParams d;
     fsmi_status st = make_params(prm, kUseRLE, d);
@@ -257,7 +344,7 @@ fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *p
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
     Vox3D v{vox, X, Y, Z, poses, P, dirs, R};
-    cudaError_t e = launch_eval_3d(v, d, out, nruns, sp, (cudaStream_t)stream);
+    cudaError_t e = launch_eval_3d(v, d, out, nruns, queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -275,9 +362,10 @@ fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm
     (void)prm;
     if (!bytes || nitems < 0) return FSMI_ERR_ARG;
     *bytes = 0;
+    if (fn < FSMI_FN_EVAL_2D || fn > FSMI_FN_EVAL_3D) return FSMI_ERR_ARG;
     if (fn == FSMI_FN_RLE_ENCODE_3D) *bytes = (size_t)scan_tiles(nitems) * sizeof(int32_t);
-    else if (fn == FSMI_FN_EVAL_2D) *bytes = (size_t)nitems * 4 * sizeof(float);
-    else if (fn < FSMI_FN_EVAL_2D || fn > FSMI_FN_EVAL_3D) return FSMI_ERR_ARG;
+    else if (fn == FSMI_FN_EVAL_2D) *bytes = kQueueBytes + (size_t)nitems * sizeof(float4);
+    else *bytes = kQueueBytes;
     return FSMI_OK;
 }
 
@@ -308,8 +396,149 @@ const char *fsmi_status_str(fsmi_status s)
     }
 }
 
+fsmi_status fsmi_set_schedule(const fsmi_schedule *sched)
+{
+    if (!sched) {
+        g_schedule = kDefaultSchedule;
+        return FSMI_OK;
+    }
+    if (!schedule_ok(*sched)) return FSMI_ERR_ARG;
+    g_schedule = to_internal(*sched);
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_get_schedule(fsmi_schedule *sched)
+{
+    if (!sched) return FSMI_ERR_ARG;
+    *sched = to_public(g_schedule);
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_schedule_candidates(int kind, fsmi_schedule *out, int max, int *n)
+{
+    if ((kind != 0 && kind != 1) || max < 0 || !n || (max > 0 && !out)) return FSMI_ERR_ARG;
+    static const int kWpb[] = {2, 4, 8};
+    static const int kChunk[] = {0, 1, 4};
+    static const int kRunlen[] = {8, 16, 32};
+    const int nrun = kind == 1 ? 3 : 1;
+    int k = 0;
+    for (int w : kWpb)
+        for (int c : kChunk)
+            for (int r = 0; r < nrun; ++r) {
+                if (k < max) out[k] = fsmi_schedule{w, 0, c, kind == 1 ? kRunlen[r] : kDefaultSchedule.cell_runlen};
+                ++k;
+            }
+    *n = k < max ? k : max;
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_autotune(fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands, int ncands, int reps,
+                          fsmi_stream_t stream, fsmi_schedule *best, float *ms)
+{
+    if (!fn || !cands || ncands < 1 || reps < 1 || !best) return FSMI_ERR_ARG;
+    for (int i = 0; i < ncands; ++i)
+        if (!schedule_ok(cands[i])) return FSMI_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e);
+    }
+    const Schedule saved = g_schedule;
+    int ibest = -1;
+    float tbest = 0.0f;
+    for (int i = 0; i < ncands; ++i) {
+        g_schedule = to_internal(cands[i]);
+        float t = -1.0f;
+        bool ok = fn(ctx, stream) == FSMI_OK;
+        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+        for (int r = 0; ok && r < reps; ++r) ok = fn(ctx, stream) == FSMI_OK;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+        t = ok ? t / reps : -1.0f;
+        if (ms) ms[i] = t;
+        if (ok && (ibest < 0 || t < tbest)) {
+            ibest = i;
+            tbest = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ibest < 0) {
+        g_schedule = saved;
+        return FSMI_ERR_ARG;
+    }
+    g_schedule = to_internal(cands[ibest]);
+    *best = to_public(g_schedule);
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_prepare(void)
+{
+    if (!status_ptr()) return cuda_fail(cudaGetLastError());
+    (void)sm_count();
+    (void)fit_warps(1, 0, 0);
+    cudaError_t e = prepare_2d();
+    if (e == cudaSuccess) e = prepare_rle();
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+struct fsmi_graph_st {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+fsmi_status fsmi_capture_begin(fsmi_stream_t stream)
+{
+    if (!stream) return FSMI_ERR_ARG;
+    cudaError_t e = cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_capture_end(fsmi_stream_t stream, fsmi_graph *graph)
+{
+    if (!stream || !graph) return FSMI_ERR_ARG;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture((cudaStream_t)stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    fsmi_graph_st *h = new (std::nothrow) fsmi_graph_st{g, x};
+    if (!h) {
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        return FSMI_ERR_CAPACITY;
+    }
+    *graph = h;
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_graph_launch(fsmi_graph graph, fsmi_stream_t stream)
+{
+    if (!graph) return FSMI_ERR_ARG;
+    cudaError_t e = cudaGraphLaunch(graph->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_graph_destroy(fsmi_graph graph)
+{
+    if (!graph) return FSMI_ERR_ARG;
+    cudaError_t e = cudaGraphExecDestroy(graph->exec);
+    cudaError_t e2 = cudaGraphDestroy(graph->graph);
+    delete graph;
+    if (e == cudaSuccess) e = e2;
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
 int fsmi_last_cuda_error(void) { return g_last_cuda; }
 
-int fsmi_version(void) { return 100; }
+int fsmi_version(void) { return 200; }
 
 }  // extern "C"

@@ -138,6 +138,28 @@ __device__ __forceinline__ float cell_prefixes(float *sp, float *sc, float *sx, 
     return pe0;
 }
 
+// Warp-level work loop of the persistent evaluation kernels: calls f(item) for items 0 .. n-1,
+// one warp per item. Without a queue the items are dealt out grid-stride; with one, each warp
+// takes `chunk` consecutive items per atomic grab on the 64-bit counter, which must be zero at
+// launch (the counter then ends at n + chunk * (number of warps)).
+template <typename F>
+__device__ __forceinline__ void for_each_item(long long n, unsigned long long *queue, int chunk, F &&f)
+{
+    const int lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    if (queue) {
+        for (;;) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(queue, (unsigned long long)chunk);
+            b0 = __shfl_sync(kFull, b0, 0);
+            if ((long long)b0 >= n) break;
+            const long long b1 = min((long long)b0 + chunk, n);
+            for (long long i = (long long)b0; i < b1; ++i) f(i);
+        }
+    } else {
+        for (long long i = (long long)blockIdx.x * wpb + warp; i < n; i += (long long)gridDim.x * wpb) f(i);
+    }
+}
+
 __device__ __forceinline__ void set_status(int *status, int bits)
 {
     if (status) atomicOr(status, bits);

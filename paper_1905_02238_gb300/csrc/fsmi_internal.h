@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/fsmi.h"
+
 namespace fsmi {
 
 // Host-validated parameters plus the derived constants every kernel needs.
@@ -16,6 +18,7 @@ struct DevParams {
     int H;              // uniform half-width
     float inv_2h1;      // 1 / (2H + 1)
     long long rfix;     // round(max_range * 2^16), 2D range limit in Q16
+    float rmax;         // max_range as given (2D: bound of a candidate set's range)
     float rend;         // rfix / 2^16 as float: the end distance of a beam cut by the range
     int nmax;           // per-beam capacity: cells (2D) or virtual cells (3D)
     int e0;             // e0_mode
@@ -24,16 +27,37 @@ struct DevParams {
     int approx_reading; // Approx-FSMI-RLE reading
     int K;              // RLE kernel support radius (cells)
     int flags;          // FSMI_FLAG_* bits
+    int cell_runlen;    // RLE: rays whose mean run length is below this take the cell-level form
 };
 
-constexpr int kWarps2D = 4;   // warps per block, 2D kernels
-constexpr int kWarpsRLE = 4;  // warps per block, RLE kernels
+constexpr int kMaxWarps = 8;  // most warps per block any evaluation kernel is launched with
+constexpr int kWarpsRLE = 4;  // warps per block of the RLE encoder kernels
+
+// Launch schedule of the evaluation kernels (fsmi_set_schedule; defaults filled in).
+struct Schedule {
+    int warps_per_block;  // 1 .. kMaxWarps
+    int blocks_per_sm;    // 0 = as many as fit
+    int queue_chunk;      // 0 = static assignment
+    int cell_runlen;      // >= 1
+};
+const Schedule &current_schedule();
+
+// The schedule's warps per block, lowered until `fixed` + warps * `per_warp` bytes of shared
+// memory fit in one block of the current device (at least 1).
+int fit_warps(int warps, size_t per_warp, size_t fixed);
+
+// Bytes at the front of an evaluation workspace reserved for the work-queue counter.
+constexpr size_t kQueueBytes = 256;
 
 // 2D (fsmi_2d.cu)
-cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs,
-                           int B, const DevParams &p, float *out, float4 *gains, int *status, cudaStream_t s);
+cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                           const DevParams &p, float *out, float4 *gains, unsigned long long *queue, int *status,
+                           cudaStream_t s);
+cudaError_t launch_eval_2d_sets(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs,
+                                int B, const fsmi_set_2d *sets, int nsets, long long nbeams, const DevParams &p, float *out,
+                                float4 *gains, unsigned long long *queue, int *status, cudaStream_t s);
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
-                              const DevParams &p, float *out, int *status, cudaStream_t s);
+                              const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s);
 cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,
                             float rend, int cap, int32_t *cells, float *l, int32_t *n, cudaStream_t s);
 cudaError_t launch_gauss_tail(const float *s, float *out, long long n, cudaStream_t st);
@@ -51,9 +75,9 @@ cudaError_t launch_rle_encode_3d(const Vox3D &v, const DevParams &p, int32_t *ru
                                  uint8_t *run_len, int run_capacity, int32_t *ws_tiles, int ntiles, int *status,
                                  cudaStream_t s);
 cudaError_t launch_eval_rle(const int32_t *run_off, const float *run_o, const uint8_t *run_len, int nrays,
-                            const DevParams &p, float *out, int *status, cudaStream_t s);
-cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32_t *nruns, int *status,
-                           cudaStream_t s);
+                            const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s);
+cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32_t *nruns,
+                           unsigned long long *queue, int *status, cudaStream_t s);
 
 // scan tile size of the RLE offsets (elements per tile)
 constexpr int kScanTile = 4096;
@@ -66,5 +90,9 @@ cudaError_t launch_rle_encode_3d_static(const Vox3D &v, const DevParams &p, int3
                                         cudaStream_t s);
 
 int sm_count();
+
+// kernel loads and per-device lookups done ahead of stream capture (fsmi_prepare)
+cudaError_t prepare_2d();
+cudaError_t prepare_rle();
 
 }  // namespace fsmi

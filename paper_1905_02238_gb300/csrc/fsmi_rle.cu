@@ -232,10 +232,6 @@ __device__ float pairs_thm5(const RunSmem &r, int nr, const float2 *tab, int K, 
     return tot;
 }
 
-#ifndef FSMI_CELL_RUNLEN
-#define FSMI_CELL_RUNLEN 16
-#endif
-constexpr int kCellRunLen = FSMI_CELL_RUNLEN;  // mean run length below which a ray is evaluated per cell
 constexpr int kArraysRLE = 7;                  // per-warp shared arrays (each `stride` floats)
 
 // run containing virtual cell i: the last u with S[u] <= i
@@ -302,7 +298,7 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
     const int n = r.S[nr];
     const bool thm5 = p.variant == FSMI_APPROX && p.approx_reading == 0;
     float v;
-    if (!thm5 && n < kCellRunLen * nr) {
+    if (!thm5 && n < p.cell_runlen * nr) {
         v = ray_mi_cells(base, stride, nr, n, p, gtab, K);
     } else {
         run_prefixes(r, nr, p.docc, p.demp);
@@ -405,72 +401,95 @@ __host__ __device__ inline size_t rle_table_bytes(int K)
              (size_t)(2 * K + 1) * sizeof(float)) + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(kWarpsRLE * 32)
-    k_eval_3d(Vox3D vx, DevParams p, long long nrays, int stride, float *__restrict__ out, int32_t *__restrict__ nruns,
-              int *status)
+// Shared-memory layout of the RLE evaluation kernels: the block's kernel table, then each warp's
+// kArraysRLE arrays of `stride` floats.
+struct RleBlock {
+    TabSpec ts;
+    float2 *tab;
+    float *gtab;
+    float *base;
+};
+
+__device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const DevParams &p, int stride)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TabSpec ts = table_spec(p);
-    float2 *tab = (float2 *)smem_raw;
-    double *gs = (double *)(smem_raw + (size_t)(2 * ts.K + 2) * sizeof(float2));
-    float *gtab = (float *)(gs + ts.K + 1);
-    build_table(tab, gs, gtab, ts.K, ts.kind, ts.sigma, ts.H, ts.band);
-    const int warp = threadIdx.x >> 5;
-    float *base = (float *)(smem_raw + rle_table_bytes(ts.K)) + (size_t)warp * kArraysRLE * stride;
-    const RunSmem r = run_smem(base, stride);
-    for (long long ray = (long long)blockIdx.x * kWarpsRLE + warp; ray < nrays; ray += (long long)gridDim.x * kWarpsRLE) {
-        const int nr = sample_encode(vx, ray, p.nmax, p.run_cap, r.O, r.S);
-        const float I = ray_mi(base, stride, nr, p, tab, gtab, ts.K, true);
-        if (lane_id() == 0) {
-            out[ray] = I;
-            if (nruns) nruns[ray] = nr;
-        }
-        __syncwarp();
-    }
+    RleBlock rb;
+    rb.ts = table_spec(p);
+    rb.tab = (float2 *)smem_raw;
+    double *gs = (double *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
+    rb.gtab = (float *)(gs + rb.ts.K + 1);
+    build_table(rb.tab, gs, rb.gtab, rb.ts.K, rb.ts.kind, rb.ts.sigma, rb.ts.H, rb.ts.band);
+    rb.base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * kArraysRLE * stride;
+    return rb;
 }
 
-__global__ void __launch_bounds__(kWarpsRLE * 32)
-    k_eval_rle(const int32_t *__restrict__ off, const float *__restrict__ ro, const uint8_t *__restrict__ rl,
-               DevParams p, long long nrays, int stride, float *__restrict__ out, int *status)
+// sampling, encoding and evaluation of one 3D ray (= pose * R + r)
+__device__ __forceinline__ void eval_ray_3d(const Vox3D &vx, const DevParams &p, const RleBlock &rb, int stride,
+                                            long long ray, float *__restrict__ out, int32_t *__restrict__ nruns)
+{
+    const RunSmem r = run_smem(rb.base, stride);
+    const int nr = sample_encode(vx, ray, p.nmax, p.run_cap, r.O, r.S);
+    const float I = ray_mi(rb.base, stride, nr, p, rb.tab, rb.gtab, rb.ts.K, true);
+    if (lane_id() == 0) {
+        out[ray] = I;
+        if (nruns) nruns[ray] = nr;
+    }
+    __syncwarp();
+}
+
+// evaluation of one run-length-encoded ray given in CSR form
+__device__ __forceinline__ void eval_ray_rle(const int32_t *__restrict__ off, const float *__restrict__ ro,
+                                             const uint8_t *__restrict__ rl, const DevParams &p, const RleBlock &rb,
+                                             int stride, long long ray, float *__restrict__ out, int *status)
+{
+    const int lane = lane_id();
+    const RunSmem r = run_smem(rb.base, stride);
+    const int b = off[ray];
+    const int nr = off[ray + 1] - b;
+    bool bad = nr < 0 || nr > p.nmax;
+    int cells = 0;
+    if (!bad) {
+        for (int u = lane; u < nr; u += 32) {
+            const int L = rl[b + u];
+            r.O[u] = __ldg(ro + b + u);
+            r.L[u] = L;
+            cells += L;
+            bad |= (L == 0);
+        }
+        cells = __reduce_add_sync(kFull, cells);
+        bad = __any_sync(kFull, bad) || cells > p.nmax;
+    }
+    __syncwarp();
+    if (bad) {
+        if (lane == 0) {
+            out[ray] = __int_as_float(0x7fc00000);
+            set_status(status, FSMI_STATUS_BAD_BEAM);
+        }
+        __syncwarp();
+        return;
+    }
+    const float I = ray_mi(rb.base, stride, nr, p, rb.tab, rb.gtab, rb.ts.K, false);
+    if (lane == 0) out[ray] = I;
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    k_eval_3d(Vox3D vx, DevParams p, long long nrays, int stride, float *__restrict__ out, int32_t *__restrict__ nruns,
+              unsigned long long *queue, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TabSpec ts = table_spec(p);
-    float2 *tab = (float2 *)smem_raw;
-    double *gs = (double *)(smem_raw + (size_t)(2 * ts.K + 2) * sizeof(float2));
-    float *gtab = (float *)(gs + ts.K + 1);
-    build_table(tab, gs, gtab, ts.K, ts.kind, ts.sigma, ts.H, ts.band);
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    float *base = (float *)(smem_raw + rle_table_bytes(ts.K)) + (size_t)warp * kArraysRLE * stride;
-    const RunSmem r = run_smem(base, stride);
-    for (long long ray = (long long)blockIdx.x * kWarpsRLE + warp; ray < nrays; ray += (long long)gridDim.x * kWarpsRLE) {
-        const int b = off[ray];
-        const int nr = off[ray + 1] - b;
-        bool bad = nr < 0 || nr > p.nmax;
-        int cells = 0;
-        if (!bad) {
-            for (int u = lane; u < nr; u += 32) {
-                const int L = rl[b + u];
-                r.O[u] = __ldg(ro + b + u);
-                r.L[u] = L;
-                cells += L;
-                bad |= (L == 0);
-            }
-            cells = __reduce_add_sync(kFull, cells);
-            bad = __any_sync(kFull, bad) || cells > p.nmax;
-        }
-        __syncwarp();
-        if (bad) {
-            if (lane == 0) {
-                out[ray] = __int_as_float(0x7fc00000);
-                set_status(status, FSMI_STATUS_BAD_BEAM);
-            }
-            __syncwarp();
-            continue;
-        }
-        const float I = ray_mi(base, stride, nr, p, tab, gtab, ts.K, false);
-        if (lane == 0) out[ray] = I;
-        __syncwarp();
-    }
+    const RleBlock rb = rle_block(smem_raw, p, stride);
+    for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d(vx, p, rb, stride, ray, out, nruns); });
+}
+
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    k_eval_rle(const int32_t *__restrict__ off, const float *__restrict__ ro, const uint8_t *__restrict__ rl,
+               DevParams p, long long nrays, int stride, float *__restrict__ out, int *status,
+               unsigned long long *queue, int chunk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const RleBlock rb = rle_block(smem_raw, p, stride);
+    for_each_item(nrays, queue, chunk,
+                  [&](long long ray) { eval_ray_rle(off, ro, rl, p, rb, stride, ray, out, status); });
 }
 
 __global__ void __launch_bounds__(kWarpsRLE * 32)
@@ -582,45 +601,62 @@ __global__ void k_scan_add(int32_t *a, long long n, const int32_t *tot)
 static int rle_stride(int nmax, int K) { return ((nmax + 2 * K + 4) + 3) & ~3; }  // cells + 2K padding
 
 template <typename Kern>
-static cudaError_t grid_for(Kern k, size_t smem, long long nitems, long long &grid)
+static cudaError_t grid_for(Kern k, size_t smem, long long nitems, int wpb, int bps, long long &grid)
 {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kWarpsRLE * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, wpb * 32, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    const long long want = (nitems + kWarpsRLE - 1) / kWarpsRLE;
+    if (bps > 0 && bps < occ) occ = bps;
+    const long long want = (nitems + wpb - 1) / wpb;
     grid = (long long)sm_count() * occ;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
     return cudaSuccess;
 }
 
-cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32_t *nruns, int *status,
-                           cudaStream_t s)
+static cudaError_t reset_queue(unsigned long long *queue, cudaStream_t s)
 {
+    return queue ? cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s) : cudaSuccess;
+}
+
+cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32_t *nruns,
+                           unsigned long long *queue, int *status, cudaStream_t s)
+{
+    (void)status;
     const long long nrays = (long long)v.P * v.R;
     if (nrays <= 0) return cudaSuccess;
+    const Schedule &sc = current_schedule();
     const int stride = rle_stride(p.nmax, p.K);
-    const size_t smem = rle_table_bytes(p.K) + (size_t)kWarpsRLE * kArraysRLE * stride * sizeof(float);
+    const size_t per_warp = (size_t)kArraysRLE * stride * sizeof(float);
+    const int wpb = fit_warps(sc.warps_per_block, per_warp, rle_table_bytes(p.K));
+    const size_t smem = rle_table_bytes(p.K) + (size_t)wpb * per_warp;
     long long grid;
-    cudaError_t e = grid_for(k_eval_3d, smem, nrays, grid);
+    cudaError_t e = grid_for(k_eval_3d, smem, nrays, wpb, sc.blocks_per_sm, grid);
+    if (e == cudaSuccess) e = reset_queue(queue, s);
     if (e != cudaSuccess) return e;
-    k_eval_3d<<<(unsigned)grid, kWarpsRLE * 32, smem, s>>>(v, p, nrays, stride, out, nruns, status);
+    k_eval_3d<<<(unsigned)grid, wpb * 32, smem, s>>>(v, p, nrays, stride, out, nruns, queue,
+                                                     sc.queue_chunk > 0 ? sc.queue_chunk : 1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_eval_rle(const int32_t *run_off, const float *run_o, const uint8_t *run_len, int nrays,
-                            const DevParams &p, float *out, int *status, cudaStream_t s)
+                            const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s)
 {
     if (nrays <= 0) return cudaSuccess;
+    const Schedule &sc = current_schedule();
     const int stride = rle_stride(p.nmax, p.K);
-    const size_t smem = rle_table_bytes(p.K) + (size_t)kWarpsRLE * kArraysRLE * stride * sizeof(float);
+    const size_t per_warp = (size_t)kArraysRLE * stride * sizeof(float);
+    const int wpb = fit_warps(sc.warps_per_block, per_warp, rle_table_bytes(p.K));
+    const size_t smem = rle_table_bytes(p.K) + (size_t)wpb * per_warp;
     long long grid;
-    cudaError_t e = grid_for(k_eval_rle, smem, nrays, grid);
+    cudaError_t e = grid_for(k_eval_rle, smem, nrays, wpb, sc.blocks_per_sm, grid);
+    if (e == cudaSuccess) e = reset_queue(queue, s);
     if (e != cudaSuccess) return e;
-    k_eval_rle<<<(unsigned)grid, kWarpsRLE * 32, smem, s>>>(run_off, run_o, run_len, p, nrays, stride, out, status);
+    k_eval_rle<<<(unsigned)grid, wpb * 32, smem, s>>>(run_off, run_o, run_len, p, nrays, stride, out, status, queue,
+                                                      sc.queue_chunk > 0 ? sc.queue_chunk : 1);
     return cudaGetLastError();
 }
 
@@ -635,7 +671,7 @@ cudaError_t launch_rle_encode_3d(const Vox3D &v, const DevParams &p, int32_t *ru
     const int stride = rle_stride(p.nmax, 0);
     const size_t smem = (size_t)kWarpsRLE * 2 * stride * sizeof(float);
     long long grid;
-    cudaError_t e = grid_for(k_rle_count, smem, nrays, grid);
+    cudaError_t e = grid_for(k_rle_count, smem, nrays, kWarpsRLE, 0, grid);
     if (e != cudaSuccess) return e;
     k_rle_count<<<(unsigned)grid, kWarpsRLE * 32, smem, s>>>(v, p, nrays, stride, run_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -647,7 +683,7 @@ cudaError_t launch_rle_encode_3d(const Vox3D &v, const DevParams &p, int32_t *ru
     if (ag > (long long)sm_count() * 8) ag = (long long)sm_count() * 8;
     k_scan_add<<<(unsigned)ag, 256, 0, s>>>(run_off + 1, nrays, ws_tiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = grid_for(k_rle_write, smem, nrays, grid);
+    e = grid_for(k_rle_write, smem, nrays, kWarpsRLE, 0, grid);
     if (e != cudaSuccess) return e;
     k_rle_write<<<(unsigned)grid, kWarpsRLE * 32, smem, s>>>(v, p, nrays, stride, run_off, run_o, run_len,
                                                               run_capacity, status);
@@ -667,6 +703,24 @@ namespace {
 std::mutex g_scratch_mu;
 int32_t *g_scratch_ptr[64];
 }  // namespace
+
+cudaError_t encode_scratch_ptr(int32_t **ptr);
+
+// Loads every RLE kernel on the current device (a kernel's first use loads it lazily).
+cudaError_t prepare_rle()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_3d);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_rle);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_rle_count);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_rle_write);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_scan_tiles);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_scan_totals);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_scan_add);
+    int32_t *scratch = nullptr;
+    if (e == cudaSuccess) e = encode_scratch_ptr(&scratch);
+    return e;
+}
 
 // Device address of g_encode_scan_scratch for the current device. The symbol's name is only a
 // host-side stand-in, so the address is looked up once per device, with that device current.

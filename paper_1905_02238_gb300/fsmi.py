@@ -7,6 +7,9 @@ is no CPU fallback: without a CUDA device or without the built library every cal
 Inputs may be CUDA tensors (the device path) or CPU tensors, in which case they are copied to
 the current device on the current stream (from pinned memory when the caller pinned them) and the
 result is copied back; that is the end-to-end form of the same call.
+
+Inside a CUDA graph capture (torch's or the library's own, `Graph`) nothing may be allocated:
+pass device inputs and a preallocated `out`; a call without `ws` then runs without a workspace.
 """
 from __future__ import annotations
 
@@ -23,11 +26,14 @@ EXACT, APPROX, UNIFORM = 0, 1, 2
 G_PDF, G_ERF = 0, 1
 FLAG_FULL_SWEEP = 0x1
 FN_EVAL_2D, FN_EVAL_BEAMS, FN_RLE_ENCODE_3D, FN_EVAL_RLE, FN_EVAL_3D = 0, 1, 2, 3, 4
+QUEUE_BYTES = 256
+KIND_2D, KIND_RLE = 0, 1
 STATUS_BEAM_OVERFLOW, STATUS_RUN_OVERFLOW, STATUS_BAD_BEAM = 0x1, 0x2, 0x4
 MAX_RANGE_2D, MAX_CELLS, MAX_SAMPLES_3D = 1024.0, 2048, 1024
 
 _lock = threading.Lock()
 _lib = None
+_TUNE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class FsmiError(RuntimeError):
@@ -49,6 +55,38 @@ class _CParams(ctypes.Structure):
         ("approx_reading", ctypes.c_int),
         ("flags", ctypes.c_int),
     ]
+
+
+class _CSchedule(ctypes.Structure):
+    _fields_ = [
+        ("warps_per_block", ctypes.c_int),
+        ("blocks_per_sm", ctypes.c_int),
+        ("queue_chunk", ctypes.c_int),
+        ("cell_runlen", ctypes.c_int),
+    ]
+
+
+@dataclass(frozen=True)
+class Schedule:
+    """fsmi_schedule: warps per block, resident-block cap, work-queue chunk (0 = static), RLE
+    cell-form threshold. Zeros select the library defaults."""
+
+    warps_per_block: int = 0
+    blocks_per_sm: int = 0
+    queue_chunk: int = 0
+    cell_runlen: int = 0
+
+    def c(self) -> _CSchedule:
+        return _CSchedule(self.warps_per_block, self.blocks_per_sm, self.queue_chunk, self.cell_runlen)
+
+    @staticmethod
+    def of(c: _CSchedule) -> "Schedule":
+        return Schedule(c.warps_per_block, c.blocks_per_sm, c.queue_chunk, c.cell_runlen)
+
+
+# fsmi_set_2d as 8 int32 words: pose_offset, npose, dir_offset, nbeam, max_range (float bits),
+# reserved, beam_offset (int64, little-endian low word first)
+SET_2D_WORDS = 8
 
 
 @dataclass
@@ -92,13 +130,25 @@ def load():
         lib = ctypes.CDLL(path)
         i, p, ll = ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong
         P = ctypes.POINTER(_CParams)
+        sz = ctypes.c_size_t
+        S = ctypes.POINTER(_CSchedule)
         sig = {
-            "fsmi_eval_2d": [p, i, i, p, i, p, i, P, p, p, ctypes.c_size_t, p],
-            "fsmi_eval_beams": [p, p, p, p, i, P, p, p],
+            "fsmi_eval_2d": [p, i, i, p, i, p, i, P, p, p, sz, p],
+            "fsmi_eval_2d_sets": [p, i, i, p, i, p, i, p, i, ll, P, p, p, sz, p],
+            "fsmi_eval_beams": [p, p, p, p, i, P, p, p, sz, p],
             "fsmi_trace_2d": [i, i, p, i, p, i, ctypes.c_float, i, p, p, p, p],
             "fsmi_rle_encode_3d": [p, i, i, i, p, i, p, i, P, p, p, p, i, p, ctypes.c_size_t, p],
-            "fsmi_eval_rle": [p, p, p, i, P, p, p],
-            "fsmi_eval_3d": [p, i, i, i, p, i, p, i, P, p, p, p],
+            "fsmi_eval_rle": [p, p, p, i, P, p, p, sz, p],
+            "fsmi_eval_3d": [p, i, i, i, p, i, p, i, P, p, p, p, sz, p],
+            "fsmi_set_schedule": [S],
+            "fsmi_get_schedule": [S],
+            "fsmi_schedule_candidates": [i, S, i, ctypes.POINTER(ctypes.c_int)],
+            "fsmi_autotune": [_TUNE_FN, p, S, i, i, p, S, ctypes.POINTER(ctypes.c_float)],
+            "fsmi_prepare": [],
+            "fsmi_capture_begin": [p],
+            "fsmi_capture_end": [p, ctypes.POINTER(p)],
+            "fsmi_graph_launch": [p, p],
+            "fsmi_graph_destroy": [p],
             "fsmi_workspace_size": [i, ll, P, ctypes.POINTER(ctypes.c_size_t)],
             "fsmi_device_status": [p, ctypes.POINTER(ctypes.c_int)],
             "fsmi_gauss_tail": [p, p, ll, p],
@@ -133,6 +183,34 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _capturing() -> bool:
+    return torch.cuda.is_current_stream_capturing()
+
+
+def _ws_args(ws):
+    """(pointer, bytes) of an optional workspace tensor (None or empty = none)."""
+    if ws is None or ws.numel() == 0:
+        return None, 0
+    if not ws.is_cuda:
+        raise ValueError("ws must be a CUDA tensor")
+    return _ptr(ws), ws.numel() * ws.element_size()
+
+
+def _default_ws(nbytes: int, dev):
+    """A fresh workspace from torch's allocator, or none inside a graph capture."""
+    if _capturing():
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+
+def _out(out, shape, m):
+    if out is None or m.host:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass a preallocated device `out`")
+        out = torch.empty(shape, dtype=torch.float32, device=m.dev)
+    return out
+
+
 class _Marshal:
     """Moves CPU inputs to the device (non-blocking) and remembers to bring results back."""
 
@@ -162,27 +240,62 @@ class _Marshal:
 def eval_2d(grid: torch.Tensor, poses: torch.Tensor, dirs: torch.Tensor, prm: Params,
             out: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
     """fsmi_eval_2d: grid float32 [H, W]; poses int32 [P, 4]; dirs int32 [B, 2] -> float32 [P, B].
-    ws: optional device workspace (uint8, >= workspace_size(FN_EVAL_2D, H*W) bytes) for per-cell
-    gains; by default one is taken from torch's allocator. Pass an empty tensor to use none."""
+    ws: optional device workspace (uint8, 16-byte aligned; workspace_size(FN_EVAL_2D, H*W) bytes
+    hold the work-queue counter and the per-cell gains); by default one is taken from torch's
+    allocator. Pass an empty tensor to use none."""
     lib = load()
     m = _Marshal(grid, poses, dirs)
     g = m.arg(grid, torch.float32, "grid", 2)
     ps = m.arg(poses, torch.int32, "poses", 2, 4)
     ds = m.arg(dirs, torch.int32, "dirs", 2, 2)
     P, B = ps.shape[0], ds.shape[0]
-    if out is None or m.host:
-        out = torch.empty((P, B), dtype=torch.float32, device=m.dev)
+    out = _out(out, (P, B), m)
     if ws is None:
-        ws = torch.empty(16 * g.numel(), dtype=torch.uint8, device=m.dev)
+        ws = _default_ws(workspace_size(FN_EVAL_2D, g.numel()), m.dev)
+    wp, wb = _ws_args(ws)
     cp = prm.c()
     _raise(lib.fsmi_eval_2d(_ptr(g), g.shape[1], g.shape[0], _ptr(ps), P, _ptr(ds), B, ctypes.byref(cp),
-                            _ptr(out), _ptr(ws) if ws.numel() else None, ws.numel() * ws.element_size(),
-                            _stream()), "fsmi_eval_2d")
+                            _ptr(out), wp, wb, _stream()), "fsmi_eval_2d")
     return m.out(out)
 
 
-def eval_beams(off, o, l, lend, prm: Params, out=None) -> torch.Tensor:
-    """fsmi_eval_beams on CSR beams -> float32 [nbeams]."""
+def make_sets_2d(sets, device=None):
+    """Packs candidate-set descriptors [(pose_offset, npose, dir_offset, nbeam, max_range), ...]
+    into the fsmi_set_2d layout (int32 [nsets, 8] on `device`, consecutive output blocks in list
+    order). Returns (tensor, total beams)."""
+    import struct
+    words, off = [], 0
+    for po, npose, do, nbeam, rng in sets:
+        fbits = struct.unpack("<i", struct.pack("<f", float(rng)))[0]
+        lo, hi = struct.unpack("<ii", struct.pack("<q", off))
+        words.append([int(po), int(npose), int(do), int(nbeam), fbits, 0, lo, hi])
+        off += int(npose) * int(nbeam)
+    t = torch.tensor(words, dtype=torch.int32).reshape(len(words), SET_2D_WORDS)
+    return (t.to(device) if device is not None else t), off
+
+
+def eval_2d_sets(grid, poses, dirs, sets, nbeams: int, prm: Params, out=None, ws=None) -> torch.Tensor:
+    """fsmi_eval_2d_sets: several candidate sets (own poses, beams and range each) in one launch.
+    sets: int32 [nsets, 8] from make_sets_2d; nbeams its total -> float32 [nbeams]."""
+    lib = load()
+    m = _Marshal(grid, poses, dirs, sets)
+    g = m.arg(grid, torch.float32, "grid", 2)
+    ps = m.arg(poses, torch.int32, "poses", 2, 4)
+    ds = m.arg(dirs, torch.int32, "dirs", 2, 2)
+    st = m.arg(sets, torch.int32, "sets", 2, SET_2D_WORDS)
+    out = _out(out, (nbeams,), m)
+    if ws is None:
+        ws = _default_ws(workspace_size(FN_EVAL_2D, g.numel()), m.dev)
+    wp, wb = _ws_args(ws)
+    cp = prm.c()
+    _raise(lib.fsmi_eval_2d_sets(_ptr(g), g.shape[1], g.shape[0], _ptr(ps), ps.shape[0], _ptr(ds), ds.shape[0],
+                                 _ptr(st), st.shape[0], nbeams, ctypes.byref(cp), _ptr(out), wp, wb, _stream()),
+           "fsmi_eval_2d_sets")
+    return m.out(out)
+
+
+def eval_beams(off, o, l, lend, prm: Params, out=None, ws=None) -> torch.Tensor:
+    """fsmi_eval_beams on CSR beams -> float32 [nbeams]. ws: optional work-queue workspace."""
     lib = load()
     m = _Marshal(off, o, l, lend)
     off = m.arg(off, torch.int32, "off", 1)
@@ -190,11 +303,13 @@ def eval_beams(off, o, l, lend, prm: Params, out=None) -> torch.Tensor:
     l = m.arg(l, torch.float32, "l", 1)
     lend = m.arg(lend, torch.float32, "lend", 1)
     nb = off.shape[0] - 1
-    if out is None or m.host:
-        out = torch.empty(nb, dtype=torch.float32, device=m.dev)
+    out = _out(out, (nb,), m)
+    if ws is None:
+        ws = _default_ws(QUEUE_BYTES, m.dev)
+    wp, wb = _ws_args(ws)
     cp = prm.c()
-    _raise(lib.fsmi_eval_beams(_ptr(off), _ptr(o), _ptr(l), _ptr(lend), nb, ctypes.byref(cp), _ptr(out), _stream()),
-           "fsmi_eval_beams")
+    _raise(lib.fsmi_eval_beams(_ptr(off), _ptr(o), _ptr(l), _ptr(lend), nb, ctypes.byref(cp), _ptr(out), wp, wb,
+                               _stream()), "fsmi_eval_beams")
     return m.out(out)
 
 
@@ -266,23 +381,27 @@ def rle_encode_3d_noalloc(vox, poses, dirs, prm: Params, capacity: int):
     return m.out(off), m.out(ro[:capacity]), m.out(rl[:capacity])
 
 
-def eval_rle(off, run_o, run_len, prm: Params, out=None) -> torch.Tensor:
-    """fsmi_eval_rle on CSR runs -> float32 [nrays]."""
+def eval_rle(off, run_o, run_len, prm: Params, out=None, ws=None) -> torch.Tensor:
+    """fsmi_eval_rle on CSR runs -> float32 [nrays]. ws: optional work-queue workspace."""
     lib = load()
     m = _Marshal(off, run_o, run_len)
     off = m.arg(off, torch.int32, "run_off", 1)
     ro = m.arg(run_o, torch.float32, "run_o", 1)
     rl = m.arg(run_len, torch.uint8, "run_len", 1)
     nr = off.shape[0] - 1
-    if out is None or m.host:
-        out = torch.empty(nr, dtype=torch.float32, device=m.dev)
+    out = _out(out, (nr,), m)
+    if ws is None:
+        ws = _default_ws(QUEUE_BYTES, m.dev)
+    wp, wb = _ws_args(ws)
     cp = prm.c()
-    _raise(lib.fsmi_eval_rle(_ptr(off), _ptr(ro), _ptr(rl), nr, ctypes.byref(cp), _ptr(out), _stream()), "fsmi_eval_rle")
+    _raise(lib.fsmi_eval_rle(_ptr(off), _ptr(ro), _ptr(rl), nr, ctypes.byref(cp), _ptr(out), wp, wb, _stream()),
+           "fsmi_eval_rle")
     return m.out(out)
 
 
-def eval_3d(vox, poses, dirs, prm: Params, out=None, with_runs: bool = False):
-    """fsmi_eval_3d (fused sample + encode + RLE variant) -> float32 [P, R] (and run counts)."""
+def eval_3d(vox, poses, dirs, prm: Params, out=None, with_runs: bool = False, ws=None):
+    """fsmi_eval_3d (fused sample + encode + RLE variant) -> float32 [P, R] (and run counts).
+    ws: optional work-queue workspace."""
     lib = load()
     m = _Marshal(vox, poses, dirs)
     v = m.arg(vox, torch.float32, "vox", 3)
@@ -290,12 +409,14 @@ def eval_3d(vox, poses, dirs, prm: Params, out=None, with_runs: bool = False):
     ds = m.arg(dirs, torch.int32, "dirs", 2, 3)
     Z, Y, X = v.shape
     P, R = ps.shape[0], ds.shape[0]
-    if out is None or m.host:
-        out = torch.empty((P, R), dtype=torch.float32, device=m.dev)
+    out = _out(out, (P, R), m)
     nr = torch.empty((P, R), dtype=torch.int32, device=m.dev) if with_runs else None
+    if ws is None:
+        ws = _default_ws(QUEUE_BYTES, m.dev)
+    wp, wb = _ws_args(ws)
     cp = prm.c()
     _raise(lib.fsmi_eval_3d(_ptr(v), X, Y, Z, _ptr(ps), P, _ptr(ds), R, ctypes.byref(cp), _ptr(out), _ptr(nr),
-                            _stream()), "fsmi_eval_3d")
+                            wp, wb, _stream()), "fsmi_eval_3d")
     if with_runs:
         return m.out(out), m.out(nr)
     return m.out(out)
@@ -317,3 +438,89 @@ def device_status() -> int:
     v = ctypes.c_int(0)
     _raise(lib.fsmi_device_status(_stream(), ctypes.byref(v)), "fsmi_device_status")
     return int(v.value)
+
+
+def set_schedule(sched: Schedule | None) -> None:
+    """fsmi_set_schedule for the calling thread (None restores the defaults)."""
+    lib = load()
+    c = sched.c() if sched is not None else None
+    _raise(lib.fsmi_set_schedule(ctypes.byref(c) if c is not None else None), "fsmi_set_schedule")
+
+
+def get_schedule() -> Schedule:
+    lib = load()
+    c = _CSchedule()
+    _raise(lib.fsmi_get_schedule(ctypes.byref(c)), "fsmi_get_schedule")
+    return Schedule.of(c)
+
+
+def schedule_candidates(kind: int) -> list[Schedule]:
+    """The library's default candidate schedules (KIND_2D or KIND_RLE)."""
+    lib = load()
+    arr = (_CSchedule * 64)()
+    n = ctypes.c_int(0)
+    _raise(lib.fsmi_schedule_candidates(kind, arr, 64, ctypes.byref(n)), "fsmi_schedule_candidates")
+    return [Schedule.of(arr[i]) for i in range(n.value)]
+
+
+def autotune(fn, candidates: list[Schedule], reps: int = 3):
+    """fsmi_autotune: times fn() (fsmi calls on the current stream) under each candidate; leaves
+    the fastest schedule set for this thread. Returns (best, [ms per candidate or -1])."""
+    lib = load()
+    err = []
+
+    def cb(ctx, stream):
+        try:
+            fn()
+            return 0
+        except FsmiError as e:  # a schedule the launch cannot take: the candidate is skipped
+            err.append(e)
+            return 1
+
+    cfn = _TUNE_FN(cb)
+    arr = (_CSchedule * len(candidates))(*[c.c() for c in candidates])
+    ms = (ctypes.c_float * len(candidates))()
+    best = _CSchedule()
+    _raise(lib.fsmi_autotune(cfn, None, arr, len(candidates), reps, _stream(), ctypes.byref(best), ms), "fsmi_autotune")
+    return Schedule.of(best), [float(v) for v in ms]
+
+
+def prepare() -> None:
+    """fsmi_prepare: per-device lookups and kernel loads, ahead of a graph capture."""
+    _raise(load().fsmi_prepare(), "fsmi_prepare")
+
+
+class Graph:
+    """fsmi_* calls captured by the library's own stream-capture helpers and replayed as one CUDA
+    graph. fn must make only asynchronous fsmi calls on device tensors with preallocated outputs
+    and workspaces."""
+
+    def __init__(self, fn, stream: torch.cuda.Stream | None = None):
+        lib = load()
+        prepare()
+        self.stream = stream or torch.cuda.Stream()
+        self._g = ctypes.c_void_p()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            _raise(lib.fsmi_capture_begin(_stream()), "fsmi_capture_begin")
+            try:
+                fn()
+            finally:
+                code = lib.fsmi_capture_end(_stream(), ctypes.byref(self._g))
+            _raise(code, "fsmi_capture_end")
+        torch.cuda.current_stream().wait_stream(self.stream)
+
+    def replay(self) -> None:
+        """Launches the graph on the current stream."""
+        _raise(load().fsmi_graph_launch(self._g, _stream()), "fsmi_graph_launch")
+
+    def close(self) -> None:
+        if self._g:
+            load().fsmi_graph_destroy(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,6 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "fsmi.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"^\s*typedef\b.*$", "", src, flags=re.M)  # function-pointer types are not exports
     return sorted(set(re.findall(r"^\s*[A-Za-z_][\w \*]*?\b(fsmi_\w+)\s*\(", src, flags=re.M)))
 
 
@@ -24,8 +25,10 @@ def lib_path():
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for fn in ("fsmi_eval_2d", "fsmi_eval_beams", "fsmi_trace_2d", "fsmi_rle_encode_3d", "fsmi_eval_rle",
-               "fsmi_eval_3d", "fsmi_workspace_size", "fsmi_device_status", "fsmi_status_str", "fsmi_version"):
+    for fn in ("fsmi_eval_2d", "fsmi_eval_2d_sets", "fsmi_eval_beams", "fsmi_trace_2d", "fsmi_rle_encode_3d",
+               "fsmi_eval_rle", "fsmi_eval_3d", "fsmi_workspace_size", "fsmi_device_status", "fsmi_status_str",
+               "fsmi_version", "fsmi_set_schedule", "fsmi_get_schedule", "fsmi_autotune", "fsmi_schedule_candidates",
+               "fsmi_prepare", "fsmi_capture_begin", "fsmi_capture_end", "fsmi_graph_launch", "fsmi_graph_destroy"):
         assert fn in names
 
 
@@ -46,9 +49,61 @@ def test_host_only_entry_points(lib_path):
     lib.fsmi_workspace_size.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     assert lib.fsmi_workspace_size(2, 4096 * 3 + 1, None, ctypes.byref(b)) == 0
     assert b.value == 4 * 4
-    assert lib.fsmi_workspace_size(0, 100, None, ctypes.byref(b)) == 0 and b.value == 1600
-    assert lib.fsmi_workspace_size(3, 100, None, ctypes.byref(b)) == 0 and b.value == 0
+    # eval workspaces: the 256-byte work-queue counter, then (2D) 16 bytes of gains per map cell
+    assert lib.fsmi_workspace_size(0, 100, None, ctypes.byref(b)) == 0 and b.value == 256 + 1600
+    for fn in (1, 3, 4):
+        assert lib.fsmi_workspace_size(fn, 100, None, ctypes.byref(b)) == 0 and b.value == 256
     assert lib.fsmi_workspace_size(9, 100, None, ctypes.byref(b)) == 1
+
+
+class _Sched(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("warps_per_block", "blocks_per_sm", "queue_chunk", "cell_runlen")]
+
+
+def test_schedule_is_checked_and_thread_local(lib_path):
+    import threading
+
+    lib = ctypes.CDLL(lib_path)
+    S = ctypes.POINTER(_Sched)
+    lib.fsmi_set_schedule.argtypes = [S]
+    lib.fsmi_get_schedule.argtypes = [S]
+    got = _Sched()
+    assert lib.fsmi_set_schedule(None) == 0
+    assert lib.fsmi_get_schedule(ctypes.byref(got)) == 0
+    assert (got.warps_per_block, got.blocks_per_sm, got.queue_chunk, got.cell_runlen) == (4, 0, 0, 16)
+    assert lib.fsmi_set_schedule(ctypes.byref(_Sched(8, 2, 4, 0))) == 0
+    assert lib.fsmi_get_schedule(ctypes.byref(got)) == 0
+    assert (got.warps_per_block, got.blocks_per_sm, got.queue_chunk, got.cell_runlen) == (8, 2, 4, 16)
+    for bad in (_Sched(9, 0, 0, 0), _Sched(-1, 0, 0, 0), _Sched(4, -1, 0, 0), _Sched(4, 0, -2, 0),
+                _Sched(4, 0, 0, -3)):
+        assert lib.fsmi_set_schedule(ctypes.byref(bad)) == 1
+    other = {}
+
+    def peek():
+        s = _Sched()
+        lib.fsmi_get_schedule(ctypes.byref(s))
+        other["wpb"] = s.warps_per_block
+
+    t = threading.Thread(target=peek)
+    t.start()
+    t.join()
+    assert other["wpb"] == 4  # another thread still has the defaults
+    assert lib.fsmi_get_schedule(ctypes.byref(got)) == 0 and got.warps_per_block == 8
+    assert lib.fsmi_set_schedule(None) == 0
+
+
+def test_schedule_candidates(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    arr = (_Sched * 64)()
+    n = ctypes.c_int(0)
+    lib.fsmi_schedule_candidates.argtypes = [ctypes.c_int, ctypes.POINTER(_Sched), ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int)]
+    assert lib.fsmi_schedule_candidates(0, arr, 64, ctypes.byref(n)) == 0 and n.value == 9
+    assert {arr[i].warps_per_block for i in range(n.value)} == {2, 4, 8}
+    assert lib.fsmi_schedule_candidates(1, arr, 64, ctypes.byref(n)) == 0 and n.value == 27
+    assert {arr[i].cell_runlen for i in range(n.value)} == {8, 16, 32}
+    assert lib.fsmi_schedule_candidates(1, arr, 5, ctypes.byref(n)) == 0 and n.value == 5
+    assert lib.fsmi_schedule_candidates(2, arr, 64, ctypes.byref(n)) == 1
 
 
 def test_binding_fails_loudly_without_gpu():
