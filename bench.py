@@ -3,7 +3,9 @@
 Workload (one step): exact FSMI (Theorem 1) of every beam of a batch on the 2D office map:
 2048x2048 grid (background 0.1, 400 obstacles at 0.9, 40% unknown at 0.5), 1024 candidate poses
 x 360 beams, range 256 cells, sigma = 2 cells, delta_occ = 1.5, delta_emp = 0.67, through
-fsmi_eval_2d (traversal, first-hit probabilities, C_k and the full pair sum, all in one kernel).
+fsmi_eval_2d (traversal, first-hit probabilities, C_k and the full pair sum, all in one kernel),
+with the schedule picked by fsmi_autotune and the call captured once in a CUDA graph that each
+step replays.
 Synthetic, seeded inputs (paper_1905_02238_gb300.synth); no dataset is involved.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {fsmi,reference}]
@@ -199,32 +201,54 @@ def _time_ms(fn, reps=5):
     return s.elapsed_time(e) / reps
 
 
+def _sched(s):
+    return {"warps_per_block": s.warps_per_block, "blocks_per_sm": s.blocks_per_sm, "queue_chunk": s.queue_chunk,
+            "cell_runlen": s.cell_runlen}
+
+
 def other_variants(g, p, d, out):  # noqa: C901
-    """Throughput of the other variants on the same devices (context; not the headline)."""
+    """Throughput of the other variants on the same devices (context; not the headline). The 3D
+    variants run as the 512x512x128 depth-camera batch in one persistent launch with an autotuned
+    schedule, captured in a CUDA graph and timed by graph replays."""
     import torch
 
     from paper_1905_02238_gb300 import fsmi, synth
 
     res = {}
     nb = p.shape[0] * d.shape[0]
+    gains_ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=g.device)
     for name, kw in (("exact_fsmi_full_sweep", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP)),
                      ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
                      ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4))):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)
-        gains_ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=g.device)
         ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out, ws=gains_ws))
         res[name] = {"beams_per_s": nb / (ms * 1e-3), "ms": ms}
     vox, vp, vd = synth.config3()
     v, vp, vd = (torch.from_numpy(x).to(g.device) for x in (vox, vp, vd))
     nr = vp.shape[0] * vd.shape[0]
     out3 = torch.empty((vp.shape[0], vd.shape[0]), dtype=torch.float32, device=g.device)
+    ws3 = torch.empty(fsmi.QUEUE_BYTES, dtype=torch.uint8, device=g.device)
+    saved = fsmi.get_schedule(fsmi.KIND_RLE)
     for name, kw in (("fsmi_rle_3d", dict(variant=fsmi.EXACT)), ("approx_fsmi_rle_3d_delta6", dict(variant=fsmi.APPROX)),
+                     ("approx_fsmi_rle_3d_delta6_band", dict(variant=fsmi.APPROX, approx_reading=1)),
                      ("uniform_fsmi_rle_3d_h4", dict(variant=fsmi.UNIFORM))):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=384.0, run_cap=64, trunc_delta=6,
                           uniform_h=4, **kw)
-        ms = _time_ms(lambda: fsmi.eval_3d(v, vp, vd, prm, out=out3))
-        res[name] = {"rays_per_s": nr / (ms * 1e-3), "ms": ms,
-                     "workload": "512x512x128 voxels, 64 poses x 128x128 rays, 384 virtual cells, fused sample+RLE+MI"}
+        fsmi.set_schedule(fsmi.KIND_RLE, saved)
+
+        def call():
+            fsmi.eval_3d(v, vp, vd, prm, out=out3, ws=ws3)
+
+        ms_default = _time_ms(call)
+        best, _, _ = fsmi.autotune(fsmi.KIND_RLE, call, reps=2)
+        graph = fsmi.Graph(call)
+        ms = _time_ms(graph.replay)
+        graph.close()
+        res[name] = {"rays_per_s": nr / (ms * 1e-3), "ms": ms, "ms_default_schedule_no_graph": ms_default,
+                     "schedule": _sched(best),
+                     "workload": "512x512x128 voxels, 64 poses x 128x128 rays, 384 virtual cells, fused sample+RLE+MI, "
+                                 "autotuned schedule, CUDA-graph replay"}
+    fsmi.set_schedule(fsmi.KIND_RLE, saved)
     return res
 
 
@@ -297,8 +321,14 @@ def run_fsmi(args):
 
     gains_ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, grid.size), dtype=torch.uint8, device=dev)
 
-    def step():
+    def call():
         fsmi.eval_2d(g, p, d, prm, out=out, ws=gains_ws)
+
+    # the step: the autotuned schedule (work queue, warps per block) captured once in a CUDA graph
+    ms_default = _time_ms(call, reps=3)
+    sched, cands, tune_ms = fsmi.autotune(fsmi.KIND_2D, call, reps=2)
+    graph = fsmi.Graph(call)
+    step = graph.replay
 
     for _ in range(args.warmup):
         step()
@@ -355,6 +385,10 @@ def run_fsmi(args):
             "config": {"workload": WORKLOAD, "poses_per_gpu": P, "beams_per_pose": B, "cells": cells,
                        "theorem1_terms": pairs, "evaluated_terms": terms,
                        "l2": "flushed between timed steps (512 MB write)",
+                       "launch": "one CUDA-graph replay per step (queue reset, per-cell gains, beams)",
+                       "schedule": _sched(sched), "ms_default_schedule_no_graph": ms_default,
+                       "autotune_ms": {f"{c.warps_per_block}w/q{c.queue_chunk}": round(t, 4)
+                                       for c, t in zip(cands, tune_ms)},
                        "parallelism": f"dp{ws} (poses sharded, map replicated)"},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32-op/s", "frac": achieved_ops / peak_ops, "traffic": traffic,

@@ -89,31 +89,36 @@ typedef struct {
 #define FSMI_FLAG_FULL_SWEEP 0x1
 
 /*
- * Launch schedule of the evaluation kernels (fsmi_eval_2d, fsmi_eval_2d_sets, fsmi_eval_beams,
- * fsmi_eval_rle, fsmi_eval_3d). The paper fixes no schedule; this one only changes how beams are
- * dealt to warps and how many warps share a block, never which terms are summed (the RLE cell
- * form below sums the same terms as the run-pair form, in another order). One warp evaluates one
- * beam (or ray) at a time in every schedule; the kernels are persistent (at most as many blocks
- * as fit on the GPU at once), so a grid never depends on the batch beyond its size.
+ * Launch schedule of the evaluation kernels, one per kernel family:
+ *   FSMI_KIND_2D   fsmi_eval_2d, fsmi_eval_2d_sets, fsmi_eval_beams
+ *   FSMI_KIND_RLE  fsmi_eval_rle, fsmi_eval_3d
+ * The paper fixes no schedule; this one only changes how beams are dealt to warps and how many
+ * warps share a block, never which terms are summed (the RLE cell form below sums the same terms
+ * as the run-pair form, in another order). One warp evaluates one beam (or ray) at a time in
+ * every schedule; the kernels are persistent (at most as many blocks as fit on the GPU at once).
+ * A zero field selects the family's default, given in brackets [2D; RLE].
  */
+#define FSMI_KIND_2D 0
+#define FSMI_KIND_RLE 1
 typedef struct {
-    int warps_per_block; /* 1 .. 8 warps per block; 0 = default (4). Lowered for a call whose
-                            per-warp shared arrays would not fit in one block */
-    int blocks_per_sm;   /* cap on resident blocks per SM; 0 = as many as fit */
+    int warps_per_block; /* 1 .. 8 warps per block [4; 2]. Lowered for a call whose per-warp
+                            shared arrays would not fit in one block */
+    int blocks_per_sm;   /* cap on resident blocks per SM [as many as fit] */
     int queue_chunk;     /* > 0: warps take beams from an atomic work queue, this many consecutive
-                            beams per grab, which balances beams of very different lengths; needs a
-                            workspace (without one, beams are dealt statically). 0 = static
-                            grid-stride assignment (default) */
-    int cell_runlen;     /* RLE variants other than Theorem 5's sub-blocks: a ray whose mean run
-                            length is below this is evaluated per virtual cell (a banded
-                            convolution, O(n K)) instead of per run pair (O(n_r^2)); 0 = default (16) */
+                            beams per grab, which balances beams of very different lengths; needs
+                            a workspace (without one, beams are dealt statically) [1; 4].
+                            -1: static grid-stride assignment */
+    int cell_runlen;     /* RLE family, variants other than Theorem 5's sub-blocks: a ray whose
+                            mean run length is below this is evaluated per virtual cell (a banded
+                            convolution, O(n K)) instead of per run pair (O(n_r^2)) [-; 32] */
 } fsmi_schedule;
 
-/* Sets the calling thread's schedule (NULL restores the defaults). FSMI_ERR_ARG if a field is out
- * of range. The schedule is read when a call enqueues its kernels. */
-fsmi_status fsmi_set_schedule(const fsmi_schedule *sched);
-/* The calling thread's schedule, defaults filled in. */
-fsmi_status fsmi_get_schedule(fsmi_schedule *sched);
+/* Sets the calling thread's schedule of family `kind` (NULL restores the defaults). FSMI_ERR_ARG
+ * for an unknown kind or a field out of range. The schedule is read when a call enqueues its
+ * kernels. */
+fsmi_status fsmi_set_schedule(int kind, const fsmi_schedule *sched);
+/* The calling thread's schedule of family `kind`, defaults filled in. */
+fsmi_status fsmi_get_schedule(int kind, fsmi_schedule *sched);
 
 /* Documented maxima. */
 #define FSMI_MAX_GRID 32767        /* W, H (2D) and X, Y, Z (3D) */
@@ -295,20 +300,23 @@ fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm
 /*
  * Native schedule tuning and CUDA-graph helpers (library conveniences; the paper has none).
  *
- * fsmi_autotune - times `fn(ctx, stream)` (which makes one or more fsmi_* calls on `stream`) under
- * each of the ncands schedules: one untimed call, then `reps` calls between two CUDA events. On
- * return the calling thread's schedule is the fastest one, copied to *best; ms (optional, host
- * float [ncands]) receives each candidate's mean milliseconds per call, or -1 where fn failed.
- * FSMI_ERR_ARG if every candidate failed. fn must not capture or synchronise other streams.
+ * fsmi_autotune - times `fn(ctx, stream)` (which makes one or more fsmi_* calls of family `kind`
+ * on `stream`) under each of the ncands schedules of that family: one untimed call, then `reps`
+ * calls between two CUDA events. On return the calling thread's schedule of that family is the
+ * fastest one, copied to *best with defaults filled in; ms (optional, host float [ncands])
+ * receives each candidate's mean milliseconds per call, or -1 where fn failed. FSMI_ERR_ARG if
+ * every candidate failed (the schedule is then left as it was). fn must not capture or
+ * synchronise other streams.
  */
 typedef fsmi_status (*fsmi_tune_fn)(void *ctx, fsmi_stream_t stream);
-fsmi_status fsmi_autotune(fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands, int ncands,
-                          int reps, fsmi_stream_t stream, fsmi_schedule *best, float *ms);
+fsmi_status fsmi_autotune(int kind, fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands,
+                          int ncands, int reps, fsmi_stream_t stream, fsmi_schedule *best,
+                          float *ms);
 
-/* Default candidate schedules for fsmi_autotune (every field filled in, as fsmi_get_schedule
- * reports them): kind 0 = 2D evaluations (2, 4, 8 warps x static, chunk 1, chunk 4), 1 = RLE / 3D
- * evaluations (the same x cell_runlen 8, 16, 32). Writes at most `max` entries to out (host) and
- * their number to *n. */
+/* Default candidate schedules of family `kind` for fsmi_autotune, every field filled in as
+ * fsmi_get_schedule reports them: FSMI_KIND_2D 2, 4, 8 warps x chunk 1, 4, static (9);
+ * FSMI_KIND_RLE 1, 2, 4 warps x chunk 2, 4, 8, static x cell_runlen 16, 32 (24). Writes at most
+ * `max` entries to out (host) and their number to *n. */
 fsmi_status fsmi_schedule_candidates(int kind, fsmi_schedule *out, int max, int *n);
 
 /* Does every per-device lookup and kernel load of the library on the current device, so that

@@ -623,7 +623,7 @@ template <int VAR, int SRC>
 static cudaError_t launch_variant(const Src2D &src, const DevParams &p, long long nbeams, float *out, int *status,
                                   unsigned long long *queue, cudaStream_t s)
 {
-    const Schedule &sc = current_schedule();
+    const Schedule &sc = current_schedule(FSMI_KIND_2D);
     const int stride = ((p.nmax + 2) + 3) & ~3;
     const size_t per_warp = (size_t)kArrays2D * stride * sizeof(float);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, 0);

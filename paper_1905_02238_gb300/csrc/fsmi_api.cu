@@ -21,8 +21,13 @@ int g_sms[kMaxDevices];
 int g_smem_optin[kMaxDevices];
 thread_local int g_last_cuda = 0;
 
-constexpr Schedule kDefaultSchedule{4, 0, 0, 16};
-thread_local Schedule g_schedule = kDefaultSchedule;
+// defaults per family, from timing the schedule candidates on the 2D office-map batch and the
+// 3D depth-camera batch: the queue removes the tail of the static assignment (the slowest of
+// thousands of warps, each with its own mix of beam lengths)
+constexpr Schedule kDefaults[2] = {{4, 0, 1, 32}, {2, 0, 4, 32}};
+thread_local Schedule g_schedule[2] = {kDefaults[0], kDefaults[1]};
+
+bool kind_ok(int kind) { return kind == FSMI_KIND_2D || kind == FSMI_KIND_RLE; }
 
 int current_device()
 {
@@ -85,7 +90,7 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     d.g_kernel = prm->g_kernel;
     d.approx_reading = prm->approx_reading;
     d.flags = prm->flags;
-    d.cell_runlen = g_schedule.cell_runlen;
+    d.cell_runlen = g_schedule[FSMI_KIND_RLE].cell_runlen;
     d.rmax = prm->max_range;
     d.rfix = 0;
     d.rend = 0.0f;
@@ -122,9 +127,9 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 // Work-queue counter at the front of a workspace, when the schedule asks for a queue and the
 // workspace holds one.
-unsigned long long *queue_of(void *ws, size_t ws_bytes)
+unsigned long long *queue_of(int kind, void *ws, size_t ws_bytes)
 {
-    if (g_schedule.queue_chunk <= 0 || !ws || !aligned16(ws) || ws_bytes < kQueueBytes) return nullptr;
+    if (g_schedule[kind].queue_chunk <= 0 || !ws || !aligned16(ws) || ws_bytes < kQueueBytes) return nullptr;
     return (unsigned long long *)ws;
 }
 
@@ -140,16 +145,17 @@ float4 *gains_of(void *ws, size_t ws_bytes, long long cells, long long nbeams, i
 bool schedule_ok(const fsmi_schedule &s)
 {
     return s.warps_per_block >= 0 && s.warps_per_block <= kMaxWarps && s.blocks_per_sm >= 0 && s.blocks_per_sm <= 64 &&
-           s.queue_chunk >= 0 && s.queue_chunk <= 1 << 20 && s.cell_runlen >= 0 && s.cell_runlen <= 1 << 20;
+           s.queue_chunk >= -1 && s.queue_chunk <= 1 << 20 && s.cell_runlen >= 0 && s.cell_runlen <= 1 << 20;
 }
 
-Schedule to_internal(const fsmi_schedule &s)
+Schedule to_internal(int kind, const fsmi_schedule &s)
 {
+    const Schedule &d = kDefaults[kind];
     Schedule r;
-    r.warps_per_block = s.warps_per_block ? s.warps_per_block : kDefaultSchedule.warps_per_block;
+    r.warps_per_block = s.warps_per_block ? s.warps_per_block : d.warps_per_block;
     r.blocks_per_sm = s.blocks_per_sm;
-    r.queue_chunk = s.queue_chunk;
-    r.cell_runlen = s.cell_runlen ? s.cell_runlen : kDefaultSchedule.cell_runlen;
+    r.queue_chunk = s.queue_chunk ? s.queue_chunk : d.queue_chunk;
+    r.cell_runlen = s.cell_runlen ? s.cell_runlen : d.cell_runlen;
     return r;
 }
 
@@ -164,7 +170,7 @@ fsmi_schedule to_public(const Schedule &s)
 }
 }  // namespace
 
-const Schedule &current_schedule() { return g_schedule; }
+const Schedule &current_schedule(int kind) { return g_schedule[kind]; }
 
 int sm_count()
 {
@@ -215,7 +221,7 @@ fsmi_status fsmi_eval_2d(const float *map, int W, int H, const int32_t *poses, i
     if (!sp) return cuda_fail(cudaGetLastError());
     const long long nbeams = (long long)P * B;
     cudaError_t e = launch_eval_2d(map, W, H, poses, P, dirs, B, d, out,
-                                   gains_of(ws, ws_bytes, (long long)W * H, nbeams, d.nmax), queue_of(ws, ws_bytes), sp,
+                                   gains_of(ws, ws_bytes, (long long)W * H, nbeams, d.nmax), queue_of(FSMI_KIND_2D, ws, ws_bytes), sp,
                                    (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
@@ -234,7 +240,7 @@ fsmi_status fsmi_eval_2d_sets(const float *map, int W, int H, const int32_t *pos
     if (!sp) return cuda_fail(cudaGetLastError());
     cudaError_t e = launch_eval_2d_sets(map, W, H, poses, P, dirs, B, sets, nsets, nbeams, d, out,
                                         gains_of(ws, ws_bytes, (long long)W * H, nbeams, d.nmax),
-                                        queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
+                                        queue_of(FSMI_KIND_2D, ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -249,7 +255,7 @@ fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, 
     if (!off || !o || !l || !lend || !out) return FSMI_ERR_ARG;
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
-    cudaError_t e = launch_eval_beams(off, o, l, lend, nbeams, d, out, queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
+    cudaError_t e = launch_eval_beams(off, o, l, lend, nbeams, d, out, queue_of(FSMI_KIND_2D, ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -327,7 +333,7 @@ fsmi_status fsmi_eval_rle(const int32_t *run_off, const float *run_o, const uint
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
     cudaError_t e =
-        launch_eval_rle(run_off, run_o, run_len, nrays, d, out, queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
+        launch_eval_rle(run_off, run_o, run_len, nrays, d, out, queue_of(FSMI_KIND_RLE, ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -344,7 +350,7 @@ fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *p
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
     Vox3D v{vox, X, Y, Z, poses, P, dirs, R};
-    cudaError_t e = launch_eval_3d(v, d, out, nruns, queue_of(ws, ws_bytes), sp, (cudaStream_t)stream);
+    cudaError_t e = launch_eval_3d(v, d, out, nruns, queue_of(FSMI_KIND_RLE, ws, ws_bytes), sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -396,46 +402,51 @@ const char *fsmi_status_str(fsmi_status s)
     }
 }
 
-fsmi_status fsmi_set_schedule(const fsmi_schedule *sched)
+fsmi_status fsmi_set_schedule(int kind, const fsmi_schedule *sched)
 {
+    if (!kind_ok(kind)) return FSMI_ERR_ARG;
     if (!sched) {
-        g_schedule = kDefaultSchedule;
+        g_schedule[kind] = kDefaults[kind];
         return FSMI_OK;
     }
     if (!schedule_ok(*sched)) return FSMI_ERR_ARG;
-    g_schedule = to_internal(*sched);
+    g_schedule[kind] = to_internal(kind, *sched);
     return FSMI_OK;
 }
 
-fsmi_status fsmi_get_schedule(fsmi_schedule *sched)
+fsmi_status fsmi_get_schedule(int kind, fsmi_schedule *sched)
 {
-    if (!sched) return FSMI_ERR_ARG;
-    *sched = to_public(g_schedule);
+    if (!kind_ok(kind) || !sched) return FSMI_ERR_ARG;
+    *sched = to_public(g_schedule[kind]);
     return FSMI_OK;
 }
 
 fsmi_status fsmi_schedule_candidates(int kind, fsmi_schedule *out, int max, int *n)
 {
-    if ((kind != 0 && kind != 1) || max < 0 || !n || (max > 0 && !out)) return FSMI_ERR_ARG;
-    static const int kWpb[] = {2, 4, 8};
-    static const int kChunk[] = {0, 1, 4};
-    static const int kRunlen[] = {8, 16, 32};
-    const int nrun = kind == 1 ? 3 : 1;
+    if (!kind_ok(kind) || max < 0 || !n || (max > 0 && !out)) return FSMI_ERR_ARG;
+    static const int kWpb2D[] = {2, 4, 8}, kChunk2D[] = {1, 4, -1};
+    static const int kWpbRLE[] = {1, 2, 4}, kChunkRLE[] = {2, 4, 8, -1}, kRunlen[] = {16, 32};
     int k = 0;
-    for (int w : kWpb)
-        for (int c : kChunk)
-            for (int r = 0; r < nrun; ++r) {
-                if (k < max) out[k] = fsmi_schedule{w, 0, c, kind == 1 ? kRunlen[r] : kDefaultSchedule.cell_runlen};
-                ++k;
-            }
+    auto put = [&](int w, int c, int r) {
+        if (k < max) out[k] = to_public(to_internal(kind, fsmi_schedule{w, 0, c, r}));
+        ++k;
+    };
+    if (kind == FSMI_KIND_2D) {
+        for (int w : kWpb2D)
+            for (int c : kChunk2D) put(w, c, 0);
+    } else {
+        for (int w : kWpbRLE)
+            for (int c : kChunkRLE)
+                for (int r : kRunlen) put(w, c, r);
+    }
     *n = k < max ? k : max;
     return FSMI_OK;
 }
 
-fsmi_status fsmi_autotune(fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands, int ncands, int reps,
+fsmi_status fsmi_autotune(int kind, fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands, int ncands, int reps,
                           fsmi_stream_t stream, fsmi_schedule *best, float *ms)
 {
-    if (!fn || !cands || ncands < 1 || reps < 1 || !best) return FSMI_ERR_ARG;
+    if (!kind_ok(kind) || !fn || !cands || ncands < 1 || reps < 1 || !best) return FSMI_ERR_ARG;
     for (int i = 0; i < ncands; ++i)
         if (!schedule_ok(cands[i])) return FSMI_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -447,11 +458,11 @@ fsmi_status fsmi_autotune(fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands
         cudaEventDestroy(e0);
         return cuda_fail(e);
     }
-    const Schedule saved = g_schedule;
+    const Schedule saved = g_schedule[kind];
     int ibest = -1;
     float tbest = 0.0f;
     for (int i = 0; i < ncands; ++i) {
-        g_schedule = to_internal(cands[i]);
+        g_schedule[kind] = to_internal(kind, cands[i]);
         float t = -1.0f;
         bool ok = fn(ctx, stream) == FSMI_OK;
         ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
@@ -468,11 +479,11 @@ fsmi_status fsmi_autotune(fsmi_tune_fn fn, void *ctx, const fsmi_schedule *cands
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ibest < 0) {
-        g_schedule = saved;
+        g_schedule[kind] = saved;
         return FSMI_ERR_ARG;
     }
-    g_schedule = to_internal(cands[ibest]);
-    *best = to_public(g_schedule);
+    g_schedule[kind] = to_internal(kind, cands[ibest]);
+    *best = to_public(g_schedule[kind]);
     return FSMI_OK;
 }
 

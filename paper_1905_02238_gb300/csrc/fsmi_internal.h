@@ -33,14 +33,14 @@ struct DevParams {
 constexpr int kMaxWarps = 8;  // most warps per block any evaluation kernel is launched with
 constexpr int kWarpsRLE = 4;  // warps per block of the RLE encoder kernels
 
-// Launch schedule of the evaluation kernels (fsmi_set_schedule; defaults filled in).
+// Launch schedule of one kernel family (fsmi_set_schedule; defaults filled in).
 struct Schedule {
     int warps_per_block;  // 1 .. kMaxWarps
     int blocks_per_sm;    // 0 = as many as fit
-    int queue_chunk;      // 0 = static assignment
-    int cell_runlen;      // >= 1
+    int queue_chunk;      // beams per queue grab; -1 = static assignment
+    int cell_runlen;      // >= 1 (RLE family)
 };
-const Schedule &current_schedule();
+const Schedule &current_schedule(int kind);  // FSMI_KIND_2D / FSMI_KIND_RLE
 
 // The schedule's warps per block, lowered until `fixed` + warps * `per_warp` bytes of shared
 // memory fit in one block of the current device (at least 1).

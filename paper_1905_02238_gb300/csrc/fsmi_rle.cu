@@ -628,7 +628,7 @@ cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32
     (void)status;
     const long long nrays = (long long)v.P * v.R;
     if (nrays <= 0) return cudaSuccess;
-    const Schedule &sc = current_schedule();
+    const Schedule &sc = current_schedule(FSMI_KIND_RLE);
     const int stride = rle_stride(p.nmax, p.K);
     const size_t per_warp = (size_t)kArraysRLE * stride * sizeof(float);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, rle_table_bytes(p.K));
@@ -646,7 +646,7 @@ cudaError_t launch_eval_rle(const int32_t *run_off, const float *run_o, const ui
                             const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s)
 {
     if (nrays <= 0) return cudaSuccess;
-    const Schedule &sc = current_schedule();
+    const Schedule &sc = current_schedule(FSMI_KIND_RLE);
     const int stride = rle_stride(p.nmax, p.K);
     const size_t per_warp = (size_t)kArraysRLE * stride * sizeof(float);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, rle_table_bytes(p.K));

@@ -68,8 +68,8 @@ class _CSchedule(ctypes.Structure):
 
 @dataclass(frozen=True)
 class Schedule:
-    """fsmi_schedule: warps per block, resident-block cap, work-queue chunk (0 = static), RLE
-    cell-form threshold. Zeros select the library defaults."""
+    """fsmi_schedule: warps per block, resident-block cap, work-queue chunk (-1 = static), RLE
+    cell-form threshold. Zeros select the family's defaults."""
 
     warps_per_block: int = 0
     blocks_per_sm: int = 0
@@ -140,10 +140,10 @@ def load():
             "fsmi_rle_encode_3d": [p, i, i, i, p, i, p, i, P, p, p, p, i, p, ctypes.c_size_t, p],
             "fsmi_eval_rle": [p, p, p, i, P, p, p, sz, p],
             "fsmi_eval_3d": [p, i, i, i, p, i, p, i, P, p, p, p, sz, p],
-            "fsmi_set_schedule": [S],
-            "fsmi_get_schedule": [S],
+            "fsmi_set_schedule": [i, S],
+            "fsmi_get_schedule": [i, S],
             "fsmi_schedule_candidates": [i, S, i, ctypes.POINTER(ctypes.c_int)],
-            "fsmi_autotune": [_TUNE_FN, p, S, i, i, p, S, ctypes.POINTER(ctypes.c_float)],
+            "fsmi_autotune": [i, _TUNE_FN, p, S, i, i, p, S, ctypes.POINTER(ctypes.c_float)],
             "fsmi_prepare": [],
             "fsmi_capture_begin": [p],
             "fsmi_capture_end": [p, ctypes.POINTER(p)],
@@ -440,22 +440,23 @@ def device_status() -> int:
     return int(v.value)
 
 
-def set_schedule(sched: Schedule | None) -> None:
-    """fsmi_set_schedule for the calling thread (None restores the defaults)."""
+def set_schedule(kind: int, sched: Schedule | None) -> None:
+    """fsmi_set_schedule of family `kind` (KIND_2D / KIND_RLE) for the calling thread (None
+    restores the defaults)."""
     lib = load()
     c = sched.c() if sched is not None else None
-    _raise(lib.fsmi_set_schedule(ctypes.byref(c) if c is not None else None), "fsmi_set_schedule")
+    _raise(lib.fsmi_set_schedule(kind, ctypes.byref(c) if c is not None else None), "fsmi_set_schedule")
 
 
-def get_schedule() -> Schedule:
+def get_schedule(kind: int) -> Schedule:
     lib = load()
     c = _CSchedule()
-    _raise(lib.fsmi_get_schedule(ctypes.byref(c)), "fsmi_get_schedule")
+    _raise(lib.fsmi_get_schedule(kind, ctypes.byref(c)), "fsmi_get_schedule")
     return Schedule.of(c)
 
 
 def schedule_candidates(kind: int) -> list[Schedule]:
-    """The library's default candidate schedules (KIND_2D or KIND_RLE)."""
+    """The library's default candidate schedules of family `kind`."""
     lib = load()
     arr = (_CSchedule * 64)()
     n = ctypes.c_int(0)
@@ -463,26 +464,28 @@ def schedule_candidates(kind: int) -> list[Schedule]:
     return [Schedule.of(arr[i]) for i in range(n.value)]
 
 
-def autotune(fn, candidates: list[Schedule], reps: int = 3):
-    """fsmi_autotune: times fn() (fsmi calls on the current stream) under each candidate; leaves
-    the fastest schedule set for this thread. Returns (best, [ms per candidate or -1])."""
+def autotune(kind: int, fn, candidates: list[Schedule] | None = None, reps: int = 3):
+    """fsmi_autotune: times fn() (fsmi calls of family `kind` on the current stream) under each
+    candidate (default: the library's list); leaves the fastest schedule set for this thread.
+    Returns (best, candidates, [ms per candidate or -1])."""
     lib = load()
-    err = []
+    if candidates is None:
+        candidates = schedule_candidates(kind)
 
     def cb(ctx, stream):
         try:
             fn()
             return 0
-        except FsmiError as e:  # a schedule the launch cannot take: the candidate is skipped
-            err.append(e)
+        except FsmiError:  # a schedule the launch cannot take: the candidate is skipped
             return 1
 
     cfn = _TUNE_FN(cb)
     arr = (_CSchedule * len(candidates))(*[c.c() for c in candidates])
     ms = (ctypes.c_float * len(candidates))()
     best = _CSchedule()
-    _raise(lib.fsmi_autotune(cfn, None, arr, len(candidates), reps, _stream(), ctypes.byref(best), ms), "fsmi_autotune")
-    return Schedule.of(best), [float(v) for v in ms]
+    _raise(lib.fsmi_autotune(kind, cfn, None, arr, len(candidates), reps, _stream(), ctypes.byref(best), ms),
+           "fsmi_autotune")
+    return Schedule.of(best), list(candidates), [float(v) for v in ms]
 
 
 def prepare() -> None:

@@ -60,36 +60,43 @@ class _Sched(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("warps_per_block", "blocks_per_sm", "queue_chunk", "cell_runlen")]
 
 
-def test_schedule_is_checked_and_thread_local(lib_path):
+def test_schedule_is_checked_per_family_and_thread_local(lib_path):
     import threading
 
     lib = ctypes.CDLL(lib_path)
     S = ctypes.POINTER(_Sched)
-    lib.fsmi_set_schedule.argtypes = [S]
-    lib.fsmi_get_schedule.argtypes = [S]
-    got = _Sched()
-    assert lib.fsmi_set_schedule(None) == 0
-    assert lib.fsmi_get_schedule(ctypes.byref(got)) == 0
-    assert (got.warps_per_block, got.blocks_per_sm, got.queue_chunk, got.cell_runlen) == (4, 0, 0, 16)
-    assert lib.fsmi_set_schedule(ctypes.byref(_Sched(8, 2, 4, 0))) == 0
-    assert lib.fsmi_get_schedule(ctypes.byref(got)) == 0
-    assert (got.warps_per_block, got.blocks_per_sm, got.queue_chunk, got.cell_runlen) == (8, 2, 4, 16)
+    lib.fsmi_set_schedule.argtypes = [ctypes.c_int, S]
+    lib.fsmi_get_schedule.argtypes = [ctypes.c_int, S]
+
+    def get(kind):
+        s = _Sched()
+        assert lib.fsmi_get_schedule(kind, ctypes.byref(s)) == 0
+        return (s.warps_per_block, s.blocks_per_sm, s.queue_chunk, s.cell_runlen)
+
+    for k in (0, 1):
+        assert lib.fsmi_set_schedule(k, None) == 0
+    assert get(0) == (4, 0, 1, 32) and get(1) == (2, 0, 4, 32)  # family defaults
+    assert lib.fsmi_set_schedule(0, ctypes.byref(_Sched(8, 2, -1, 0))) == 0
+    assert get(0) == (8, 2, -1, 32) and get(1) == (2, 0, 4, 32)  # the other family is untouched
+    assert lib.fsmi_set_schedule(1, ctypes.byref(_Sched(0, 0, 0, 7))) == 0
+    assert get(1) == (2, 0, 4, 7)
     for bad in (_Sched(9, 0, 0, 0), _Sched(-1, 0, 0, 0), _Sched(4, -1, 0, 0), _Sched(4, 0, -2, 0),
                 _Sched(4, 0, 0, -3)):
-        assert lib.fsmi_set_schedule(ctypes.byref(bad)) == 1
+        assert lib.fsmi_set_schedule(0, ctypes.byref(bad)) == 1
+    assert lib.fsmi_set_schedule(2, None) == 1
+    assert lib.fsmi_get_schedule(-1, ctypes.byref(_Sched())) == 1
     other = {}
 
     def peek():
-        s = _Sched()
-        lib.fsmi_get_schedule(ctypes.byref(s))
-        other["wpb"] = s.warps_per_block
+        other["2d"] = get(0)
 
     t = threading.Thread(target=peek)
     t.start()
     t.join()
-    assert other["wpb"] == 4  # another thread still has the defaults
-    assert lib.fsmi_get_schedule(ctypes.byref(got)) == 0 and got.warps_per_block == 8
-    assert lib.fsmi_set_schedule(None) == 0
+    assert other["2d"] == (4, 0, 1, 32)  # another thread still has the defaults
+    assert get(0) == (8, 2, -1, 32)
+    for k in (0, 1):
+        assert lib.fsmi_set_schedule(k, None) == 0
 
 
 def test_schedule_candidates(lib_path):
@@ -100,18 +107,8 @@ def test_schedule_candidates(lib_path):
                                              ctypes.POINTER(ctypes.c_int)]
     assert lib.fsmi_schedule_candidates(0, arr, 64, ctypes.byref(n)) == 0 and n.value == 9
     assert {arr[i].warps_per_block for i in range(n.value)} == {2, 4, 8}
-    assert lib.fsmi_schedule_candidates(1, arr, 64, ctypes.byref(n)) == 0 and n.value == 27
-    assert {arr[i].cell_runlen for i in range(n.value)} == {8, 16, 32}
+    assert {arr[i].queue_chunk for i in range(n.value)} == {1, 4, -1}
+    assert lib.fsmi_schedule_candidates(1, arr, 64, ctypes.byref(n)) == 0 and n.value == 24
+    assert {arr[i].cell_runlen for i in range(n.value)} == {16, 32}
     assert lib.fsmi_schedule_candidates(1, arr, 5, ctypes.byref(n)) == 0 and n.value == 5
     assert lib.fsmi_schedule_candidates(2, arr, 64, ctypes.byref(n)) == 1
-
-
-def test_binding_fails_loudly_without_gpu():
-    import torch
-
-    from paper_1905_02238_gb300 import fsmi
-
-    if torch.cuda.is_available():
-        pytest.skip("a GPU is present")
-    with pytest.raises(fsmi.FsmiError):
-        fsmi.load()

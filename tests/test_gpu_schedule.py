@@ -26,9 +26,14 @@ def lib():
 
 @pytest.fixture(autouse=True)
 def default_schedule():
-    fsmi.set_schedule(None)
+    for k in (fsmi.KIND_2D, fsmi.KIND_RLE):
+        fsmi.set_schedule(k, None)
     yield
-    fsmi.set_schedule(None)
+    for k in (fsmi.KIND_2D, fsmi.KIND_RLE):
+        fsmi.set_schedule(k, None)
+
+
+K2, KR = fsmi.KIND_2D, fsmi.KIND_RLE
 
 
 def _cuda(a):
@@ -58,15 +63,15 @@ def test_every_2d_schedule_gives_identical_bits():
     grid, poses = _office()
     dirs = synth.beam_dirs_2d(90)
     g, p, d = _cuda(grid), _cuda(poses), _cuda(dirs)
-    scheds = fsmi.schedule_candidates(fsmi.KIND_2D) + [fsmi.Schedule(1, 1, 0, 0), fsmi.Schedule(8, 1, 7, 0),
-                                                       fsmi.Schedule(3, 0, 1000, 0)]
+    scheds = fsmi.schedule_candidates(K2) + [fsmi.Schedule(1, 1, -1, 0), fsmi.Schedule(8, 1, 7, 0),
+                                             fsmi.Schedule(3, 0, 1000, 0)]
     for var in VARIANTS_2D:
         gp, _ = _prm2d(var, 96.0)
-        fsmi.set_schedule(None)
+        fsmi.set_schedule(K2, None)
         ref = fsmi.eval_2d(g, p, d, gp)
         for s in scheds:
-            fsmi.set_schedule(s)
-            assert fsmi.get_schedule().warps_per_block == s.warps_per_block
+            fsmi.set_schedule(K2, s)
+            assert fsmi.get_schedule(K2).warps_per_block == s.warps_per_block
             got = fsmi.eval_2d(g, p, d, gp)
             np.testing.assert_array_equal(_bits(got), _bits(ref), err_msg=f"{var} {s}")
             got = fsmi.eval_2d(g, p, d, gp, ws=torch.empty(0, dtype=torch.uint8, device="cuda"))
@@ -81,8 +86,9 @@ def test_queued_explicit_beams_match_oracle():
     for var in VARIANTS_2D:
         gp, op = _prm2d(var, 1.0)
         ref_by_var[var] = oracle.eval_beams(off, o, l, lend, op)
-    for s in (fsmi.Schedule(), fsmi.Schedule(4, 0, 1, 0), fsmi.Schedule(8, 0, 3, 0), fsmi.Schedule(2, 1, 16, 0)):
-        fsmi.set_schedule(s)
+    for s in (fsmi.Schedule(4, 0, -1, 0), fsmi.Schedule(4, 0, 1, 0), fsmi.Schedule(8, 0, 3, 0),
+              fsmi.Schedule(2, 1, 16, 0)):
+        fsmi.set_schedule(K2, s)
         for var in VARIANTS_2D:
             gp, _ = _prm2d(var, 1.0)
             got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
@@ -106,11 +112,11 @@ def test_rle_schedules_and_cell_form_threshold():
         ref = oracle.eval_rle(off, ro, rl, op)
         # threshold 1: every ray on the run-pair path; 100000: every ray (but Theorem 5's) per cell
         for runlen in (1, 100000):
-            fsmi.set_schedule(fsmi.Schedule(cell_runlen=runlen))
+            fsmi.set_schedule(KR, fsmi.Schedule(cell_runlen=runlen))
             first = fsmi.eval_rle(*args, gp)
             assert_mi_close(first.cpu().numpy(), ref, f"rle {kw} runlen={runlen}")
-            for s in (fsmi.Schedule(2, 0, 0, runlen), fsmi.Schedule(8, 0, 1, runlen), fsmi.Schedule(4, 2, 5, runlen)):
-                fsmi.set_schedule(s)
+            for s in (fsmi.Schedule(2, 0, -1, runlen), fsmi.Schedule(8, 0, 1, runlen), fsmi.Schedule(4, 2, 5, runlen)):
+                fsmi.set_schedule(KR, s)
                 np.testing.assert_array_equal(_bits(fsmi.eval_rle(*args, gp)), _bits(first), err_msg=f"{kw} {s}")
 
 
@@ -124,10 +130,10 @@ def test_eval_3d_schedules_identical_and_match_oracle():
     v, p, d = _cuda(vox), _cuda(poses), _cuda(dirs)
     first = fsmi.eval_3d(v, p, d, gp)
     assert_mi_close(first.cpu().numpy(), ref, "3d default")
-    for s in fsmi.schedule_candidates(fsmi.KIND_RLE):
-        fsmi.set_schedule(s)
+    for s in fsmi.schedule_candidates(KR):
+        fsmi.set_schedule(KR, s)
         got = fsmi.eval_3d(v, p, d, gp)
-        if s.cell_runlen == 16:
+        if s.cell_runlen == 32:  # the default threshold: same path for every ray as `first`
             np.testing.assert_array_equal(_bits(got), _bits(first), err_msg=str(s))
         else:
             assert_mi_close(got.cpu().numpy(), ref, f"3d {s}")
@@ -151,8 +157,8 @@ def test_sets_equal_separate_calls_and_oracle(variant):
     g, p, d = _cuda(grid), _cuda(poses), _cuda(dirs)
     st, nb = fsmi.make_sets_2d(sets, "cuda")
     gp, _ = _prm2d(variant, 200.0)
-    for s in (fsmi.Schedule(), fsmi.Schedule(8, 0, 2, 0)):
-        fsmi.set_schedule(s)
+    for s in (fsmi.Schedule(4, 0, -1, 0), fsmi.Schedule(8, 0, 2, 0)):
+        fsmi.set_schedule(K2, s)
         got = fsmi.eval_2d_sets(g, p, d, st, nb, gp).cpu().numpy()
         at = 0
         for po, npose, do, nbeam, rng in sets:
@@ -160,7 +166,7 @@ def test_sets_equal_separate_calls_and_oracle(variant):
             sep = fsmi.eval_2d(g, p[po:po + npose], d[do:do + nbeam], gps).cpu().numpy().reshape(-1)
             np.testing.assert_array_equal(got[at:at + sep.size].view(np.uint32), sep.view(np.uint32),
                                           err_msg=f"set {po, npose, do, nbeam, rng} {s}")
-            if npose and s.queue_chunk == 0:
+            if npose and s.queue_chunk < 0:
                 ref = oracle.eval_2d(grid, poses[po:po + min(npose, 2)], dirs[do:do + nbeam], ops).reshape(-1)
                 assert_mi_close(got[at:at + ref.size], ref, f"set oracle {variant} {rng}")
             at += sep.size
@@ -203,7 +209,8 @@ def test_graph_replay_of_sets_and_3d():
     vdirs = synth.pinhole_dirs(8, 8, 90.0)
     v, vp, vd = _cuda(vox), _cuda(vposes), _cuda(vdirs)
     gp3 = fsmi.Params(variant=fsmi.APPROX, sigma=2.0, trunc_delta=6, max_range=80.0, run_cap=16)
-    fsmi.set_schedule(fsmi.Schedule(4, 0, 2, 0))  # queued: the captured memset must reset the counters
+    fsmi.set_schedule(K2, fsmi.Schedule(4, 0, 2, 0))  # queued: the captured memsets must reset the counters
+    fsmi.set_schedule(KR, fsmi.Schedule(2, 0, 3, 0))
     out2 = torch.empty(nb, dtype=torch.float32, device="cuda")
     out3 = torch.empty((vp.shape[0], vd.shape[0]), dtype=torch.float32, device="cuda")
     ws2 = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device="cuda")
@@ -236,14 +243,14 @@ def test_autotune_picks_a_candidate_and_sets_it():
     gp, _ = _prm2d(fsmi.EXACT, 128.0)
     out = torch.empty((p.shape[0], d.shape[0]), dtype=torch.float32, device="cuda")
     ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device="cuda")
-    cands = fsmi.schedule_candidates(fsmi.KIND_2D)
-    best, ms = fsmi.autotune(lambda: fsmi.eval_2d(g, p, d, gp, out=out, ws=ws), cands, reps=2)
+    best, cands, ms = fsmi.autotune(K2, lambda: fsmi.eval_2d(g, p, d, gp, out=out, ws=ws), reps=2)
     assert best in cands
     assert all(t > 0 for t in ms)
     assert ms[cands.index(best)] == min(ms)
-    assert fsmi.get_schedule() == best
+    assert fsmi.get_schedule(K2) == best
+    assert fsmi.get_schedule(KR) == fsmi.Schedule(2, 0, 4, 32)  # the other family is untouched
     ref = fsmi.eval_2d(g, p, d, gp)
-    fsmi.set_schedule(None)
+    fsmi.set_schedule(K2, None)
     np.testing.assert_array_equal(_bits(ref), _bits(fsmi.eval_2d(g, p, d, gp)))
 
 
@@ -254,14 +261,16 @@ def test_autotune_skips_failing_candidates():
     calls = []
 
     def fn():
-        s = fsmi.get_schedule()
+        s = fsmi.get_schedule(K2)
         calls.append(s)
         if s.warps_per_block == 2:
             raise fsmi.FsmiError("rejected")
         fsmi.eval_2d(g, p, d, gp)
 
-    cands = [fsmi.Schedule(2, 0, 0, 0), fsmi.Schedule(4, 0, 0, 0)]
-    best, ms = fsmi.autotune(fn, cands, reps=1)
-    assert best == fsmi.Schedule(4, 0, 0, 16) and ms[0] == -1.0 and ms[1] > 0
+    cands = [fsmi.Schedule(2, 0, -1, 0), fsmi.Schedule(4, 0, -1, 0)]
+    best, _, ms = fsmi.autotune(K2, fn, cands, reps=1)
+    assert best == fsmi.Schedule(4, 0, -1, 32) and ms[0] == -1.0 and ms[1] > 0
+    fsmi.set_schedule(K2, fsmi.Schedule(8, 0, 0, 0))
     with pytest.raises(fsmi.FsmiError):
-        fsmi.autotune(fn, cands[:1], reps=1)
+        fsmi.autotune(K2, fn, cands[:1], reps=1)
+    assert fsmi.get_schedule(K2) == fsmi.Schedule(8, 0, 1, 32)  # left as it was
