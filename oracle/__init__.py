@@ -95,6 +95,10 @@ def _load():
             lib.oracle_c_k.argtypes = [p, i, d, d, p]
             lib.oracle_fsmi_beam.restype = d
             lib.oracle_fsmi_beam.argtypes = [p, p, i, P]
+            lib.oracle_fsmi_beam_skip.restype = d
+            lib.oracle_fsmi_beam_skip.argtypes = [p, p, p, i, P]
+            lib.oracle_eval_trajectories_2d.argtypes = [p, i, i, p, p, i, p, i, P, p, p, p]
+            lib.oracle_update_map_2d.argtypes = [p, i, i, p, i, p, i, p, P]
             lib.oracle_uniform_pairsum.restype = d
             lib.oracle_uniform_pairsum.argtypes = [p, p, i, P]
             lib.oracle_beam_dir_2d.argtypes = [p, p, p]
@@ -170,6 +174,17 @@ def fsmi_beam(o, l, prm: Params) -> float:
     return _load().oracle_fsmi_beam(_ptr(o), _ptr(l), len(o), ctypes.byref(cp))
 
 
+def fsmi_beam_skip(o, l, skip, prm: Params) -> float:
+    """fsmi_beam summing only the cells with skip[i] == 0 (Section 2.4: already-counted cells keep
+    their occupancy but add no gain)."""
+    o = _c(o, np.float64)
+    l = _c(l, np.float64)
+    sk = _c(np.asarray(skip, bool), np.uint8)
+    assert len(l) == len(o) + 1 and len(sk) == len(o)
+    cp = prm.c()
+    return _load().oracle_fsmi_beam_skip(_ptr(o), _ptr(l), _ptr(sk), len(o), ctypes.byref(cp))
+
+
 def uniform_pairsum(o, l, prm: Params) -> float:
     """Uniform-FSMI as the generic pair sum of eq. (uniform) (overlap of the uniform density)."""
     o = _c(o, np.float64)
@@ -216,6 +231,51 @@ def eval_2d(grid, poses, dirs, prm: Params, nthreads: int | None = None) -> np.n
     _load().oracle_eval_2d(_ptr(grid), W, Hh, _ptr(poses), P, _ptr(dirs), B, ctypes.byref(cp), _ptr(out),
                            nthreads or default_threads())
     return out
+
+
+def eval_trajectories_2d(grid, poses, traj_off, dirs, prm: Params):
+    """Section 2.4: MI along trajectories with already-counted cells dropped at later states.
+    Returns (beam [P, B], state [P], traj [T]) in float64."""
+    grid = _c(grid, np.float32)
+    poses = _c(poses, np.int32)
+    traj_off = _c(traj_off, np.int32)
+    dirs = _c(dirs, np.int32)
+    Hh, W = grid.shape
+    P, B, T = poses.shape[0], dirs.shape[0], len(traj_off) - 1
+    beam = np.zeros((P, B), np.float64)
+    state = np.zeros(P, np.float64)
+    traj = np.zeros(T, np.float64)
+    cp = prm.c()
+    cp.max_range = float(np.float32(prm.max_range))
+    _load().oracle_eval_trajectories_2d(_ptr(grid), W, Hh, _ptr(poses), _ptr(traj_off), T, _ptr(dirs), B,
+                                        ctypes.byref(cp), _ptr(beam), _ptr(state), _ptr(traj))
+    return beam, state, traj
+
+
+def path_lengths(poses, traj_off) -> np.ndarray:
+    """Travel distance of each trajectory: the straight distances between consecutive states
+    (cells), at least 1."""
+    xy = np.asarray(poses, np.float64)[:, :2] / 65536.0
+    out = []
+    for a, b in zip(traj_off[:-1], traj_off[1:]):
+        seg = np.diff(xy[a:b], axis=0)
+        out.append(max(1.0, float(np.sqrt((seg ** 2).sum(axis=1)).sum())))
+    return np.array(out)
+
+
+def update_map_2d(grid, poses, dirs, ranges, prm: Params) -> np.ndarray:
+    """Eq. (bayesian_filter) applied beam by beam; returns the updated map in float64."""
+    m = np.array(grid, np.float64, copy=True, order="C")
+    poses = _c(poses, np.int32)
+    dirs = _c(dirs, np.int32)
+    ranges = _c(ranges, np.float32)
+    Hh, W = m.shape
+    P, B = poses.shape[0], dirs.shape[0]
+    assert ranges.size == P * B
+    cp = prm.c()
+    cp.max_range = float(np.float32(prm.max_range))
+    _load().oracle_update_map_2d(_ptr(m), W, Hh, _ptr(poses), P, _ptr(dirs), B, _ptr(ranges), ctypes.byref(cp))
+    return m
 
 
 def eval_beams(off, o, l, lend, prm: Params, nthreads: int | None = None) -> np.ndarray:

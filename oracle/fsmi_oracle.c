@@ -100,15 +100,30 @@ static double G_gauss(const double *l, int k, int j, double sigma)
     return Phi((l[k] - mu) / sigma) - Phi((l[k - 1] - mu) / sigma);
 }
 
+/* C_k of a beam some of whose cells are excluded from the sum of eq. (mi_sum) (Section 2.4: cells
+ * that already contributed along a trajectory add nothing): an excluded cell keeps its occupancy
+ * (it still stops the beam) but its terms f(delta_occ, r_k), f(delta_emp, r_k) are dropped.
+ * skip = NULL excludes nothing (then this is Algorithm 3). */
+static void c_k_skip(const double *o, const unsigned char *skip, int n, double docc, double demp, double *C)
+{
+    double q = 0.0;
+    for (int k = 1; k <= n; ++k) {
+        int use = !(skip && skip[k - 1]);
+        C[k - 1] = q + (use ? oracle_f_prob(docc, o[k - 1]) : 0.0);
+        q = q + (use ? oracle_f_prob(demp, o[k - 1]) : 0.0);
+    }
+}
+
 /* FSMI (Theorem 1 / Algorithm 1), Approx-FSMI (eq. fsmi_approx) and Uniform-FSMI (Theorem 4 /
- * Algorithm 4) for one beam. */
-ORACLE_EXPORT double oracle_fsmi_beam(const double *o, const double *l, int n, const struct oracle_params *p)
+ * Algorithm 4) for one beam, summing the cells not excluded by skip (NULL: all cells). */
+ORACLE_EXPORT double oracle_fsmi_beam_skip(const double *o, const double *l, const unsigned char *skip, int n,
+                                           const struct oracle_params *p)
 {
     if (n <= 0) return 0.0;
     double *pe = (double *)malloc(sizeof(double) * (size_t)(n + 1));
     double *C = (double *)malloc(sizeof(double) * (size_t)(n + 1));
     oracle_first_hit(o, n, pe);
-    oracle_c_k(o, n, p->delta_occ, p->delta_emp, C);
+    c_k_skip(o, skip, n, p->delta_occ, p->delta_emp, C);
     int j0 = p->e0_mode ? 0 : 1;
     double I = 0.0;
     if (p->variant == OV_EXACT || p->variant == OV_APPROX) {
@@ -137,6 +152,11 @@ ORACLE_EXPORT double oracle_fsmi_beam(const double *o, const double *l, int n, c
     free(pe);
     free(C);
     return I;
+}
+
+ORACLE_EXPORT double oracle_fsmi_beam(const double *o, const double *l, int n, const struct oracle_params *p)
+{
+    return oracle_fsmi_beam_skip(o, l, NULL, n, p);
 }
 
 /* Uniform-FSMI as the generic pair sum of eq. (uniform): sum_j P(e_j) sum_k C_k G^U_{k,j}, with
@@ -190,9 +210,22 @@ ORACLE_EXPORT void oracle_beam_dir_2d(const int32_t *pose, const int32_t *u, int
  * cells[i] = cy*W + cx; l[i] = entry distance of cell i (l[0] = 0); l[n] = min(R, grid exit).
  * Returns n, or -1 if more than cap cells. Distance is the parameter lambda of
  * o + lambda * d / 2^30 (cell units). rfix = round(R * 2^16). */
+static int trace_2d_end(int W, int H, int32_t ox, int32_t oy, int32_t dx, int32_t dy, int64_t rfix, int cap,
+                        int32_t *cells, double *l, int *by_range);
+
 ORACLE_EXPORT int oracle_trace_2d(int W, int H, int32_t ox, int32_t oy, int32_t dx, int32_t dy,
                                   int64_t rfix, int cap, int32_t *cells, double *l)
 {
+    int by_range;
+    return trace_2d_end(W, H, ox, oy, dx, dy, rfix, cap, cells, l, &by_range);
+}
+
+/* The traversal itself; *by_range = 1 when the beam ended at the range limit R (inside the grid),
+ * 0 when it left the grid first or crossed no cell. */
+static int trace_2d_end(int W, int H, int32_t ox, int32_t oy, int32_t dx, int32_t dy, int64_t rfix, int cap,
+                        int32_t *cells, double *l, int *by_range)
+{
+    *by_range = 0;
     if (dx == 0 && dy == 0) return 0;
     int64_t cx = floor_shift(ox, 16), cy = floor_shift(oy, 16);
     if (dx < 0 && (ox & 0xFFFF) == 0) cx -= 1; /* the cell entered by o + eps*d */
@@ -220,6 +253,7 @@ ORACLE_EXPORT int oracle_trace_2d(int W, int H, int32_t ox, int32_t oy, int32_t 
         int64_t num = stepx ? nx : ny, den = stepx ? adx : ady;
         if (!((num << 30) < rfix * den)) { /* next entry parameter >= R */
             l[n] = (double)rfix / 65536.0;
+            *by_range = 1;
             break;
         }
         double lam = (double)num * 16384.0 / (double)den;
@@ -267,6 +301,112 @@ ORACLE_EXPORT void oracle_eval_2d(const float *map, int W, int H, const int32_t 
         free(l);
         free(o);
     }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Section 2.4: mutual information along discretised trajectories. The MI of a trajectory is the */
+/* sum over its states of the scan MI (the sum over the state's beams, eq. mi_sum per beam);     */
+/* a cell that contributed at an earlier state is marked and not used again. Within one state    */
+/* the beams are summed as a scan, as in eq. (mi_sum) per beam.                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+/* States of trajectory t are poses traj_off[t] .. traj_off[t+1]-1, in travel order.
+ * beam_out[p*B + b], state_out[p] and traj_out[t] in nats. */
+ORACLE_EXPORT void oracle_eval_trajectories_2d(const float *map, int W, int H, const int32_t *poses,
+                                               const int32_t *traj_off, int T, const int32_t *dirs, int B,
+                                               const struct oracle_params *p, double *beam_out,
+                                               double *state_out, double *traj_out)
+{
+    int64_t rfix = range_fix(p->max_range);
+    int cap = (int)(p->max_range * 1.5) + 4;
+    unsigned char *counted = (unsigned char *)malloc((size_t)W * H);
+    int32_t *cells = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    double *l = (double *)malloc(sizeof(double) * (size_t)(cap + 1));
+    double *o = (double *)malloc(sizeof(double) * (size_t)cap);
+    unsigned char *skip = (unsigned char *)malloc((size_t)cap);
+    for (int t = 0; t < T; ++t) {
+        memset(counted, 0, (size_t)W * H);
+        double traj = 0.0;
+        for (int pi = traj_off[t]; pi < traj_off[t + 1]; ++pi) {
+            double scan = 0.0;
+            /* the state's beams see only the marks of earlier states */
+            for (int bi = 0; bi < B; ++bi) {
+                int32_t d[2];
+                oracle_beam_dir_2d(poses + 4 * pi, dirs + 2 * bi, d);
+                int n = oracle_trace_2d(W, H, poses[4 * pi], poses[4 * pi + 1], d[0], d[1], rfix, cap, cells, l);
+                double I = NAN;
+                if (n >= 0) {
+                    for (int c = 0; c < n; ++c) {
+                        o[c] = (double)map[cells[c]];
+                        skip[c] = counted[cells[c]] != 0;
+                    }
+                    I = oracle_fsmi_beam_skip(o, l, skip, n, p);
+                }
+                beam_out[(size_t)pi * B + bi] = I;
+                scan += I;
+            }
+            /* then every cell the state's beams crossed is marked */
+            for (int bi = 0; bi < B; ++bi) {
+                int32_t d[2];
+                oracle_beam_dir_2d(poses + 4 * pi, dirs + 2 * bi, d);
+                int n = oracle_trace_2d(W, H, poses[4 * pi], poses[4 * pi + 1], d[0], d[1], rfix, cap, cells, l);
+                for (int c = 0; c < n; ++c) counted[cells[c]] = 1;
+            }
+            state_out[pi] = scan;
+            traj += scan;
+        }
+        traj_out[t] = traj;
+    }
+    free(counted);
+    free(cells);
+    free(l);
+    free(o);
+    free(skip);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Eq. (bayesian_filter) with the inverse sensor model of eq. (inverse_sensing): for a beam that */
+/* measured range z, the cell where z falls is updated by delta_occ and every cell the beam     */
+/* crossed before it by delta_emp (odds multiplied); a beam with z >= max_range returned        */
+/* nothing and updates every cell up to max_range by delta_emp. Beams are applied one after the */
+/* other in (pose, beam) order, each as r <- r * delta, i.e. o <- o delta / (1 + o (delta-1)).  */
+/* ------------------------------------------------------------------------------------------ */
+
+static double odds_update(double o, double delta) { return o * delta / (1.0 + o * (delta - 1.0)); }
+
+ORACLE_EXPORT void oracle_update_map_2d(double *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs,
+                                        int B, const float *ranges, const struct oracle_params *p)
+{
+    int64_t rmax = range_fix(p->max_range);
+    int cap = (int)(p->max_range * 1.5) + 4;
+    int32_t *cells = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    double *l = (double *)malloc(sizeof(double) * (size_t)(cap + 1));
+    for (int pi = 0; pi < P; ++pi) {
+        for (int bi = 0; bi < B; ++bi) {
+            double z = (double)ranges[(size_t)pi * B + bi];
+            if (!(z > 0.0)) continue; /* no measurement */
+            int64_t rfix = rmax;
+            int ret = 0; /* the beam returned at z < max_range */
+            if (z < (double)rmax / 65536.0) {
+                int64_t rz = range_fix(z);
+                if (rz < rmax) {
+                    rfix = rz;
+                    ret = 1;
+                }
+            }
+            int32_t d[2];
+            oracle_beam_dir_2d(poses + 4 * pi, dirs + 2 * bi, d);
+            int by_range;
+            int n = trace_2d_end(W, H, poses[4 * pi], poses[4 * pi + 1], d[0], d[1], rfix, cap, cells, l, &by_range);
+            for (int c = 0; c < n; ++c) {
+                int occ = ret && by_range && c == n - 1;
+                double *m = &map[cells[c]];
+                if (*m > 0.0 && *m < 1.0) *m = odds_update(*m, occ ? p->delta_occ : p->delta_emp);
+            }
+        }
+    }
+    free(cells);
+    free(l);
 }
 
 /* Batched explicit beams in CSR form: beam b has cells off[b]..off[b+1]-1 with occupancies o[]

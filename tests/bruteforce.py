@@ -33,14 +33,16 @@ def _gain(delta: float, o: float) -> float:
     return kl_gain(delta, o)
 
 
-def smi_integral(o, l, sigma, delta_occ, delta_emp, e0_mode=0, noise="gauss", H=0, panels=8, order=24):
+def smi_integral(o, l, sigma, delta_occ, delta_emp, e0_mode=0, noise="gauss", H=0, panels=8, order=24, skip=None):
     """Numerical integration of eq. (mi_sum) on one beam (o[n], l[n+1]).
 
     noise="gauss": P(z|e_j) = N(mu_j, sigma), mu_j the centre of cell j.
     noise="uniform": P(z|e_j) = U[l_j - H, l_{j+1} + H] (Theorem 4's model, unit cells).
     e0_mode=1 adds the no-return event with centre l_1 - 1/2 (or support [l_1 - 1 - H, l_1 + H]).
     A measurement outside [l_1, l_{n+1}) carries no information.
+    skip: cells left out of the sum over i of eq. (mi_sum) (they still shape P(Z=z)).
     """
+    skip = set() if skip is None else {i for i, v in enumerate(skip) if v}
     o = [float(v) for v in o]
     l = [float(v) for v in l]
     n = len(o)
@@ -77,6 +79,8 @@ def smi_integral(o, l, sigma, delta_occ, delta_emp, e0_mode=0, noise="gauss", H=
         # cells after k are not informed (delta = 1, zero gain).
         s = 0.0
         for i in range(n):
+            if i in skip:
+                continue
             if i < k:
                 s += _gain(delta_emp, o[i])
             elif i == k:
