@@ -282,19 +282,84 @@ fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *p
  */
 fsmi_status fsmi_gauss_tail(const float *s, float *out, long long n, fsmi_stream_t stream);
 
+/*
+ * The exploration loop around the beam MI (Section 2.4; eq. (1) of Section 2.1).
+ *
+ * fsmi_eval_trajectories_2d - mutual information along discretised candidate trajectories: the
+ * MI of a trajectory is the sum over its states of the scan MI (the sum of the state's beam MI),
+ * where a cell that already contributed at an earlier state of the same trajectory adds nothing
+ * (it keeps its occupancy, so it still stops the beam with probability o, but its terms
+ * f(delta, r) leave C_k). The beams of one state are summed as a scan, without marks between
+ * them. Trajectories are independent of one another.
+ *   poses     int32 [P][4] as fsmi_eval_2d: every state of every trajectory.
+ *   traj_off  int32 [T+1] device CSR offsets: trajectory t has states traj_off[t] ..
+ *             traj_off[t+1]-1 in travel order (traj_off[0] = 0, traj_off[T] = P, non-decreasing);
+ *             a pose outside every trajectory gets NaN beams and FSMI_STATUS_BAD_BEAM.
+ *   dirs, B, prm, map: as fsmi_eval_2d.
+ *   beam_mi   float32 [P][B] (device, output), state_mi float32 [P], traj_mi float32 [T].
+ *   ws        required, 16-byte aligned, fsmi_trajectory_workspace_size(W, H, T) bytes: the
+ *             queue counter, per-map-cell gains and one int32 visit stamp per map cell and
+ *             trajectory (the first state whose beams cross the cell).
+ * Sums are taken in a fixed order, so results do not change from run to run.
+ */
+fsmi_status fsmi_trajectory_workspace_size(int W, int H, int T, size_t *bytes);
+fsmi_status fsmi_eval_trajectories_2d(const float *map, int W, int H, const int32_t *poses, int P,
+                                      const int32_t *traj_off, int T, const int32_t *dirs, int B,
+                                      const fsmi_params *prm, float *beam_mi, float *state_mi,
+                                      float *traj_mi, void *ws, size_t ws_bytes,
+                                      fsmi_stream_t stream);
+
+/* fsmi_best_trajectory - the trajectory with the most mutual information per travel distance
+ * (Sections 2.4 and 5.2): ratio[t] = traj_mi[t] / max(1, L_t), L_t the sum of the straight
+ * distances (cells) between consecutive states (poses int32 [P][4], traj_off as above; offsets are
+ * clamped to [0, P]); *best (device int32) = argmax of ratio, the lowest index among equal ratios,
+ * -1 if none is a number. T >= 1. */
+fsmi_status fsmi_best_trajectory(const float *traj_mi, const int32_t *poses, int P,
+                                 const int32_t *traj_off, int T, float *ratio, int32_t *best,
+                                 fsmi_stream_t stream);
+
+/* fsmi_scan_sums - pose_mi[p] = sum over b of beam_mi[p*B + b] (the scan MI of each candidate
+ * pose), in a fixed order. */
+fsmi_status fsmi_scan_sums(const float *beam_mi, long long P, int B, float *pose_mi,
+                           fsmi_stream_t stream);
+
+/*
+ * fsmi_update_map_2d - the Bayesian occupancy update of eq. (1) with the inverse sensor model of
+ * Section 2.2, for a batch of measured beams: the odds of the cell where a measured range ends are
+ * multiplied by delta_occ, those of every cell the beam crossed before it by delta_emp, the rest
+ * are unchanged. The traversal is fsmi_eval_2d's cut at the measured range, so the cell holding
+ * the range end is decided exactly (its entry distance is below the range, the next one is not).
+ *   map     float32 [H][W], updated in place; cells at exactly 0 or 1 stay put.
+ *   poses, dirs: as fsmi_eval_2d; ranges float32 [P][B] measured range per beam, cells. A range
+ *           >= prm->max_range (or +inf) is a beam without return: every cell up to max_range is
+ *           crossed (delta_emp). A range that is NaN or <= 0 is no measurement. A range that ends
+ *           outside the grid updates only the cells crossed inside it.
+ *   prm     delta_occ, delta_emp, max_range (other fields must be valid but are not used).
+ *   ws      16-byte aligned, fsmi_workspace_size(FSMI_FN_UPDATE_MAP_2D, W*H) bytes (per-cell
+ *           update counts).
+ * Updates commute, so the batch is applied at once per cell as
+ * o' = 1 / (1 + exp(-(logit(o) + a ln delta_occ + b ln delta_emp))) with a, b the cell's counts.
+ */
+fsmi_status fsmi_update_map_2d(float *map, int W, int H, const int32_t *poses, int P,
+                               const int32_t *dirs, int B, const float *ranges,
+                               const fsmi_params *prm, void *ws, size_t ws_bytes,
+                               fsmi_stream_t stream);
+
 /* Function ids for fsmi_workspace_size. */
 #define FSMI_FN_EVAL_2D 0
 #define FSMI_FN_EVAL_BEAMS 1
 #define FSMI_FN_RLE_ENCODE_3D 2
 #define FSMI_FN_EVAL_RLE 3
 #define FSMI_FN_EVAL_3D 4
+#define FSMI_FN_UPDATE_MAP_2D 5
 
 /* Bytes at the front of an evaluation workspace that hold the work-queue counter. */
 #define FSMI_QUEUE_BYTES 256
 
 /* Bytes of device workspace entry point `fn` can use for `nitems` items: map cells for
  * FSMI_FN_EVAL_2D (queue counter + optional gains; also fsmi_eval_2d_sets), rays for
- * FSMI_FN_RLE_ENCODE_3D (required offset scan), FSMI_QUEUE_BYTES for the other evaluations. */
+ * FSMI_FN_RLE_ENCODE_3D (required offset scan), map cells for FSMI_FN_UPDATE_MAP_2D (required
+ * update counts), FSMI_QUEUE_BYTES for the other evaluations. */
 fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm, size_t *bytes);
 
 /*

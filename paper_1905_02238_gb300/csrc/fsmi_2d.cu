@@ -17,184 +17,11 @@
 // difference, which is 0 for a cell shorter than the FP32 resolution of its distance.
 #include "../../include/fsmi.h"
 #include "fsmi_device.cuh"
+#include "dda2d.cuh"
 #include "fsmi_internal.h"
 #include "gauss_tail.cuh"
 
 namespace fsmi {
-
-// Beam direction: the sensor-frame unit vector u rotated by the pose's (cos, sin), rounded half
-// up: d = floor((Rot u + 2^29) / 2^30). Arithmetic right shift is a floor division by 2^30.
-__device__ __forceinline__ void beam_dir(const int32_t *pose, int32_t ux, int32_t uy, int &dx, int &dy)
-{
-    const long long c = pose[2], s = pose[3];
-    dx = (int)((c * ux - s * uy + (1LL << 29)) >> 30);
-    dy = (int)((s * ux + c * uy + (1LL << 29)) >> 30);
-}
-
-// ---- traversal ----------------------------------------------------------------------------------
-//
-// The beam is o + lambda * d / 2^30 (o in Q16 cell units, d in Q30); lambda is its distance. Cells
-// change at x crossings lambda_x(a) = (nx0 + a 2^16) 2^14 / |dx| and y crossings likewise, with
-// nx0, ny0 the Q16 distances from o to the far side of the first cell (the cell entered by
-// o + eps d). Crossings are ordered by exact int64 comparison; coinciding crossings are one
-// diagonal step. A cell is entered while its entry lambda < R and it lies inside the grid.
-//
-// Parallel form: along the major axis M (|d_M| >= |d_m|) consecutive M-crossings split the beam
-// into intervals [lambda_M(k), lambda_M(k+1)), k = -1, 0, 1, ... (lambda_M(-1) = 0). Minor
-// crossings are at least as far apart as major ones, so each interval holds the cell entered at
-// its start plus at most one cell entered at a minor crossing strictly inside it. Lane L walks a
-// contiguous block of intervals; its starting minor coordinate is the number of minor crossings
-// at or before lambda_M(k0) (one integer division). A warp scan of per-lane cell counts places the
-// cells; the first lane that meets the range limit or the grid boundary ends the beam.
-
-struct Geo {
-    int sM, sm, cM0, cm0, dimM, dimm, xmaj, W;
-    unsigned nM0, nm0;  // Q16 distances to the first major / minor boundary (< 2^31 + 2^16 with k)
-    unsigned aM, am;    // |d| along the major / minor axis (Q30, <= 2^31)
-    unsigned LM, Lm;    // crossing numerators below these have entry distance < R
-    float rM, rm, R;
-};
-
-__device__ __forceinline__ unsigned long long mulw(unsigned a, unsigned b) { return (unsigned long long)a * b; }
-
-// Number of minor crossings at or before the major crossing k: #{i >= 0 : nm(i) aM <= nM(k) am}
-// = floor((nM(k) am - nm0 aM) / (2^16 aM)) + 1 when that numerator is >= 0. The quotient (< 2^11
-// for ranges up to 1024 cells) is estimated in FP32 and corrected exactly in integers.
-__device__ __forceinline__ int minor_before(const Geo &g, int k)
-{
-    if (g.am == 0 || k < 0) return 0;
-    const long long num = (long long)mulw(g.nM0 + (unsigned)k * 65536u, g.am) - (long long)mulw(g.nm0, g.aM);
-    if (num < 0) return 0;
-    const long long hi = num >> 16;  // floor(num / 2^16); floor(hi / aM) = floor(num / (2^16 aM))
-    long long q = (long long)((float)hi * (1.0f / (float)g.aM));
-    q -= (q * (long long)g.aM > hi);
-    q -= (q * (long long)g.aM > hi);
-    q += ((q + 1) * (long long)g.aM <= hi);
-    q += ((q + 1) * (long long)g.aM <= hi);
-    return (int)q + 1;
-}
-
-template <bool WRITE>
-__device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int base, int cap, int *ids, float *l, int &cnt,
-                                     bool &ended, float &endl)
-{
-    int cM = g.cM0 + g.sM * (k0 + 1);
-    int i = minor_before(g, k0);
-    int cm = g.cm0 + g.sm * i;
-    cnt = 0;
-    ended = false;
-    endl = 0.0f;
-#define FSMI_EMIT(lam_)                                                              \
-    do {                                                                             \
-        if (WRITE) {                                                                 \
-            const int pos_ = base + cnt;                                             \
-            if (pos_ < cap) {                                                        \
-                ids[pos_] = g.xmaj ? (cm * g.W + cM) : (cM * g.W + cm);              \
-                l[pos_] = (lam_);                                                    \
-            }                                                                        \
-        }                                                                            \
-        ++cnt;                                                                       \
-    } while (0)
-    for (int k = k0; k <= k1; ++k) {
-        FSMI_EMIT(k < 0 ? 0.0f : (float)(g.nM0 + (unsigned)k * 65536u) * g.rM);
-        const unsigned nMn = g.nM0 + (unsigned)(k + 1) * 65536u;  // next major crossing
-        unsigned nmi = g.nm0 + (unsigned)i * 65536u;              // next minor crossing
-        if (g.am && mulw(nmi, g.aM) < mulw(nMn, g.am)) {         // minor crossing inside
-            if (nmi >= g.Lm) {
-                ended = true;
-                endl = g.R;
-                break;
-            }
-            cm += g.sm;
-            if ((unsigned)cm >= (unsigned)g.dimm) {
-                ended = true;
-                endl = (float)nmi * g.rm;
-                break;
-            }
-            FSMI_EMIT((float)nmi * g.rm);
-            ++i;
-            nmi += 65536u;
-        }
-        if (nMn >= g.LM) {
-            ended = true;
-            endl = g.R;
-            break;
-        }
-        const bool tie = g.am && (mulw(nmi, g.aM) == mulw(nMn, g.am));
-        cM += g.sM;
-        if (tie) {
-            cm += g.sm;
-            ++i;
-        }
-        if ((unsigned)cM >= (unsigned)g.dimM || (unsigned)cm >= (unsigned)g.dimm) {
-            ended = true;
-            endl = (float)nMn * g.rM;
-            break;
-        }
-    }
-#undef FSMI_EMIT
-}
-
-// All 32 lanes call this. Writes ids[0..n-1] (cell y*W + x) and l[0..n] (entry distances, then
-// the end distance) and returns n; returns -1 (writing nothing) if the beam has more than cap
-// cells. rend = R as float.
-__device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, long long rfix, float rend, int cap, int *ids,
-                        float *l)
-{
-    const int lane = lane_id();
-    if ((dx | dy) == 0) return 0;
-    int cx = ox >> 16, cy = oy >> 16;
-    if (dx < 0 && (ox & 0xFFFF) == 0) --cx;
-    if (dy < 0 && (oy & 0xFFFF) == 0) --cy;
-    if ((unsigned)cx >= (unsigned)W || (unsigned)cy >= (unsigned)H) return 0;
-    const unsigned adx = dx < 0 ? 0u - (unsigned)dx : (unsigned)dx, ady = dy < 0 ? 0u - (unsigned)dy : (unsigned)dy;
-    Geo g;
-    g.xmaj = adx >= ady;
-    g.W = W;
-    g.aM = g.xmaj ? adx : ady;
-    g.am = g.xmaj ? ady : adx;
-    const int dM = g.xmaj ? dx : dy, dm = g.xmaj ? dy : dx;
-    g.sM = dM > 0 ? 1 : -1;
-    g.sm = dm > 0 ? 1 : -1;
-    g.cM0 = g.xmaj ? cx : cy;
-    g.cm0 = g.xmaj ? cy : cx;
-    g.dimM = g.xmaj ? W : H;
-    g.dimm = g.xmaj ? H : W;
-    const long long oM = g.xmaj ? ox : oy, om = g.xmaj ? oy : ox;
-    g.nM0 = (unsigned)(g.sM > 0 ? ((long long)(g.cM0 + 1) << 16) - oM : oM - ((long long)g.cM0 << 16));
-    g.nm0 = g.am == 0 ? 0u
-                      : (unsigned)(g.sm > 0 ? ((long long)(g.cm0 + 1) << 16) - om : om - ((long long)g.cm0 << 16));
-    // crossing numerators below these limits have entry lambda < R:
-    //   num * 2^30 < rfix * a  <=>  num < floor((rfix * a - 1) / 2^30) + 1
-    g.LM = (unsigned)((((unsigned long long)rfix * g.aM - 1) >> 30) + 1);
-    g.Lm = g.am ? (unsigned)((((unsigned long long)rfix * g.am - 1) >> 30) + 1) : 0u;
-    g.rM = 16384.0f / (float)g.aM;
-    g.rm = g.am ? 16384.0f / (float)g.am : 0.0f;
-    g.R = rend;
-    // major crossings that stay in range and inside the grid along M
-    const long long KR = g.LM > g.nM0 ? ((long long)g.LM - g.nM0 + 65535) >> 16 : 0;
-    const long long KG = g.sM > 0 ? (g.dimM - 1 - g.cM0) : g.cM0;
-    const int K = (int)(KR < KG ? KR : KG);
-    const int NI = K + 1;  // intervals k = -1 .. K-1
-    const int q = (NI + 31) >> 5;
-    const int k0 = -1 + lane * q;
-    const int k1 = min(K - 1, k0 + q - 1);
-    int cnt = 0;
-    bool ended = false;
-    float endl = 0.0f;
-    if (k0 <= k1) walk<false>(g, k0, k1, 0, cap, ids, l, cnt, ended, endl);
-    const unsigned eb = __ballot_sync(kFull, ended);
-    const int first = eb ? __ffs(eb) - 1 : 31;
-    const int c = lane <= first ? cnt : 0;
-    const int inc = warp_incl_add_int(c);
-    const int n = __shfl_sync(kFull, inc, 31);
-    const float lend = __shfl_sync(kFull, endl, first);
-    if (n > cap) return -1;
-    if (lane <= first && k0 <= k1) walk<true>(g, k0, k1, inc - c, cap, ids, l, cnt, ended, endl);
-    if (lane == 0) l[n] = lend;
-    __syncwarp();
-    return n;
-}
 
 // ---- pair sums ------------------------------------------------------------------------------------
 
@@ -203,7 +30,7 @@ constexpr int kArrays2D = 4;
 // internal variant id of the full n(n+1) exact sweep (FSMI_FLAG_FULL_SWEEP)
 constexpr int kExactFullSweep = 3;
 
-enum { kSrcMap = 0, kSrcBeams = 1, kSrcSets = 2 };
+enum { kSrcMap = 0, kSrcBeams = 1, kSrcSets = 2, kSrcTraj = 3 };
 
 struct Src2D {
     // map source (kSrcMap, kSrcSets)
@@ -222,6 +49,11 @@ struct Src2D {
     // candidate sets (kSrcSets): device array of nsets descriptors
     const fsmi_set_2d *sets;
     int nsets;
+    // trajectories (kSrcTraj, poses and beams as kSrcMap): states traj_off[t] .. traj_off[t+1]-1,
+    // stamp[t][cell] = first state of trajectory t whose beams visit the cell
+    const int32_t *traj_off;
+    int T;
+    const int32_t *stamp;
 };
 
 // One register-blocked pass of the exact pair sum over scaled distances: each lane owns J
@@ -441,6 +273,23 @@ __device__ __forceinline__ int set_of(const fsmi_set_2d *sets, int nsets, long l
     return lo - 1;
 }
 
+// the trajectory holding pose p: t with traj_off[t] <= p < traj_off[t+1], or -1
+__device__ __forceinline__ int traj_of(const int32_t *traj_off, int T, int p)
+{
+    int lo = 0, len = T + 1;  // last index with traj_off[idx] <= p
+    while (len > 0) {
+        const int half = len >> 1;
+        if (__ldg(traj_off + lo + half) <= p) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    const int t = lo - 1;
+    return (t >= 0 && t < T && p < __ldg(traj_off + t + 1)) ? t : -1;
+}
+
 // One beam: traversal (or explicit cells), gains, prefixes, the variant's pair sum, store.
 template <int VAR, int SRC>
 __device__ __forceinline__ void eval_beam(const Src2D &src, const DevParams &p, long long beam, float *sl, float *sc,
@@ -453,14 +302,28 @@ __device__ __forceinline__ void eval_beam(const Src2D &src, const DevParams &p, 
     if (SRC != kSrcBeams) {
         const int32_t *pose;
         int ux, uy;
+        int state = 0;                   // kSrcTraj: state index within the trajectory
+        const int32_t *stamps = nullptr;  // kSrcTraj: the trajectory's visit stamps
         long long rfix = p.rfix;
         float rend = p.rend;
         int cap = p.nmax;
-        if (SRC == kSrcMap) {
+        if (SRC == kSrcMap || SRC == kSrcTraj) {
             const int pi = (int)(beam / src.B), bi = (int)(beam % src.B);
             pose = src.poses + 4 * (size_t)pi;
             ux = src.dirs[2 * bi];
             uy = src.dirs[2 * bi + 1];
+            if (SRC == kSrcTraj) {
+                const int t = traj_of(src.traj_off, src.T, pi);
+                if (t < 0) {  // pose not covered by the trajectory offsets
+                    if (lane == 0) {
+                        out[beam] = __int_as_float(0x7fc00000);
+                        set_status(status, FSMI_STATUS_BAD_BEAM);
+                    }
+                    return;
+                }
+                state = pi - __ldg(src.traj_off + t);
+                stamps = src.stamp + (size_t)t * src.W * src.H;
+            }
         } else {
             const int si = set_of(src.sets, src.nsets, beam);
             bool ok = si >= 0;
@@ -508,7 +371,8 @@ __device__ __forceinline__ void eval_beam(const Src2D &src, const DevParams &p, 
             for (int i = lane; i < n; i += 32) {
                 const unsigned id = (unsigned)((const int *)sx)[i];
                 bad |= id >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
-                const float4 v = id < ncell ? __ldg(src.gains + id) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 v = id < ncell ? __ldg(src.gains + id) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (SRC == kSrcTraj && id < ncell && __ldg(stamps + id) < state) v.y = v.z = 0.0f;
                 sp[i] = v.x;
                 sc[i] = v.y;
                 sx[i] = v.z;
@@ -518,9 +382,12 @@ __device__ __forceinline__ void eval_beam(const Src2D &src, const DevParams &p, 
                 const unsigned id = (unsigned)((const int *)sx)[i];
                 bad |= id >= ncell;
                 const float o = id < ncell ? __ldg(src.map + id) : 0.0f;
+                // a cell already counted by an earlier state of the trajectory (Section 2.4) still
+                // stops the beam with probability o but adds no information
+                const bool counted = SRC == kSrcTraj && id < ncell && __ldg(stamps + id) < state;
                 sp[i] = o;
-                sc[i] = cell_gain(p.docc, o);
-                sx[i] = cell_gain(p.demp, o);
+                sc[i] = counted ? 0.0f : cell_gain(p.docc, o);
+                sx[i] = counted ? 0.0f : cell_gain(p.demp, o);
             }
         }
         if (__any_sync(kFull, bad) && lane == 0) set_status(status, FSMI_STATUS_INTERNAL);
@@ -681,7 +548,7 @@ cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses,
         cudaError_t e = map_gains(map, W, H, p, gains, s);
         if (e != cudaSuccess) return e;
     }
-    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, 0, nullptr};
     return dispatch<kSrcMap>(src, p, (long long)P * B, out, status, queue, s);
 }
 
@@ -693,14 +560,26 @@ cudaError_t launch_eval_2d_sets(const float *map, int W, int H, const int32_t *p
         cudaError_t e = map_gains(map, W, H, p, gains, s);
         if (e != cudaSuccess) return e;
     }
-    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr, sets, nsets};
+    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr, sets, nsets, nullptr, 0, nullptr};
     return dispatch<kSrcSets>(src, p, nbeams, out, status, queue, s);
+}
+
+cudaError_t launch_eval_2d_traj(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *traj_off,
+                                int T, const int32_t *stamp, const int32_t *dirs, int B, const DevParams &p, float *out,
+                                float4 *gains, unsigned long long *queue, int *status, cudaStream_t s)
+{
+    if (gains) {
+        cudaError_t e = map_gains(map, W, H, p, gains, s);
+        if (e != cudaSuccess) return e;
+    }
+    Src2D src{map, W, H, poses, P, dirs, B, gains, nullptr, nullptr, nullptr, nullptr, nullptr, 0, traj_off, T, stamp};
+    return dispatch<kSrcTraj>(src, p, (long long)P * B, out, status, queue, s);
 }
 
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                               const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s)
 {
-    Src2D src{nullptr, 0, 0, nullptr, 0, nullptr, 0, nullptr, off, o, l, lend, nullptr, 0};
+    Src2D src{nullptr, 0, 0, nullptr, 0, nullptr, 0, nullptr, off, o, l, lend, nullptr, 0, nullptr, 0, nullptr};
     return dispatch<kSrcBeams>(src, p, nbeams, out, status, queue, s);
 }
 
@@ -721,6 +600,7 @@ cudaError_t prepare_2d()
     cudaError_t e = prepare_src<kSrcMap>();
     if (e == cudaSuccess) e = prepare_src<kSrcBeams>();
     if (e == cudaSuccess) e = prepare_src<kSrcSets>();
+    if (e == cudaSuccess) e = prepare_src<kSrcTraj>();
     cudaFuncAttributes a;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_map_gains);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_trace_2d);

@@ -244,6 +244,85 @@ fsmi_status fsmi_eval_2d_sets(const float *map, int W, int H, const int32_t *pos
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
+fsmi_status fsmi_trajectory_workspace_size(int W, int H, int T, size_t *bytes)
+{
+    if (!bytes || !grid_ok(W) || !grid_ok(H) || T < 0) return FSMI_ERR_ARG;
+    const size_t cells = (size_t)W * H;
+    *bytes = kQueueBytes + cells * sizeof(float4) + (size_t)T * cells * sizeof(int32_t);
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_eval_trajectories_2d(const float *map, int W, int H, const int32_t *poses, int P,
+                                      const int32_t *traj_off, int T, const int32_t *dirs, int B, const fsmi_params *prm,
+                                      float *beam_mi, float *state_mi, float *traj_mi, void *ws, size_t ws_bytes,
+                                      fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUse2D, d);
+    if (st != FSMI_OK) return st;
+    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || T < 0) return FSMI_ERR_ARG;
+    if (T == 0) return FSMI_OK;
+    if (!map || !poses || !traj_off || !traj_mi || (P > 0 && (!state_mi || (B > 0 && (!dirs || !beam_mi)))))
+        return FSMI_ERR_ARG;
+    size_t need = 0;
+    fsmi_trajectory_workspace_size(W, H, T, &need);
+    if (!ws || !aligned16(ws) || ws_bytes < need) return FSMI_ERR_WORKSPACE;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long cells = (long long)W * H;
+    int32_t *stamp = (int32_t *)((char *)ws + kQueueBytes + (size_t)cells * sizeof(float4));
+    cudaError_t e = launch_traj_stamps(W, H, poses, P, traj_off, T, dirs, B, d.rfix, d.rend, d.nmax, stamp, sp, s);
+    if (e == cudaSuccess && (long long)P * B > 0)
+        e = launch_eval_2d_traj(map, W, H, poses, P, traj_off, T, stamp, dirs, B, d, beam_mi,
+                                gains_of(ws, ws_bytes, cells, (long long)P * B, d.nmax),
+                                queue_of(FSMI_KIND_2D, ws, ws_bytes), sp, s);
+    if (e == cudaSuccess && P > 0) {
+        if (B > 0) e = launch_row_sums(beam_mi, P, B, state_mi, s);
+        else e = cudaMemsetAsync(state_mi, 0, (size_t)P * sizeof(float), s);
+    }
+    if (e == cudaSuccess) e = launch_csr_sums(state_mi, P, traj_off, T, traj_mi, s);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_best_trajectory(const float *traj_mi, const int32_t *poses, int P, const int32_t *traj_off, int T,
+                                 float *ratio, int32_t *best, fsmi_stream_t stream)
+{
+    if (T < 1 || P < 0 || !traj_mi || (P > 0 && !poses) || !traj_off || !ratio || !best) return FSMI_ERR_ARG;
+    cudaError_t e = launch_best_trajectory(traj_mi, poses, P, traj_off, T, ratio, best, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_scan_sums(const float *beam_mi, long long P, int B, float *pose_mi, fsmi_stream_t stream)
+{
+    if (P < 0 || B < 0) return FSMI_ERR_ARG;
+    if (P == 0) return FSMI_OK;
+    if (!pose_mi || (B > 0 && !beam_mi)) return FSMI_ERR_ARG;
+    cudaError_t e = B > 0 ? launch_row_sums(beam_mi, P, B, pose_mi, (cudaStream_t)stream)
+                          : cudaMemsetAsync(pose_mi, 0, (size_t)P * sizeof(float), (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_update_map_2d(float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                               const float *ranges, const fsmi_params *prm, void *ws, size_t ws_bytes,
+                               fsmi_stream_t stream)
+{
+    DevParams d;
+    fsmi_status st = make_params(prm, kUse2D, d);
+    if (st != FSMI_OK) return st;
+    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0) return FSMI_ERR_ARG;
+    if ((long long)P * B == 0) return FSMI_OK;
+    if (!map || !poses || !dirs || !ranges) return FSMI_ERR_ARG;
+    const size_t need = (size_t)W * H * 2 * sizeof(uint32_t);
+    if (!ws || !aligned16(ws) || ws_bytes < need) return FSMI_ERR_WORKSPACE;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_update_map_2d(map, W, H, poses, P, dirs, B, ranges, d.rfix, d.nmax,
+                                         (float)log((double)prm->delta_occ), (float)log((double)prm->delta_emp),
+                                         (uint32_t *)ws, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
 fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                             const fsmi_params *prm, float *out, void *ws, size_t ws_bytes, fsmi_stream_t stream)
 {
@@ -368,9 +447,10 @@ fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm
     (void)prm;
     if (!bytes || nitems < 0) return FSMI_ERR_ARG;
     *bytes = 0;
-    if (fn < FSMI_FN_EVAL_2D || fn > FSMI_FN_EVAL_3D) return FSMI_ERR_ARG;
+    if (fn < FSMI_FN_EVAL_2D || fn > FSMI_FN_UPDATE_MAP_2D) return FSMI_ERR_ARG;
     if (fn == FSMI_FN_RLE_ENCODE_3D) *bytes = (size_t)scan_tiles(nitems) * sizeof(int32_t);
     else if (fn == FSMI_FN_EVAL_2D) *bytes = kQueueBytes + (size_t)nitems * sizeof(float4);
+    else if (fn == FSMI_FN_UPDATE_MAP_2D) *bytes = (size_t)nitems * 2 * sizeof(uint32_t);
     else *bytes = kQueueBytes;
     return FSMI_OK;
 }
@@ -494,6 +574,7 @@ fsmi_status fsmi_prepare(void)
     (void)fit_warps(1, 0, 0);
     cudaError_t e = prepare_2d();
     if (e == cudaSuccess) e = prepare_rle();
+    if (e == cudaSuccess) e = prepare_explore();
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 

@@ -56,6 +56,9 @@ cudaError_t launch_eval_2d(const float *map, int W, int H, const int32_t *poses,
 cudaError_t launch_eval_2d_sets(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs,
                                 int B, const fsmi_set_2d *sets, int nsets, long long nbeams, const DevParams &p, float *out,
                                 float4 *gains, unsigned long long *queue, int *status, cudaStream_t s);
+cudaError_t launch_eval_2d_traj(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *traj_off,
+                                int T, const int32_t *stamp, const int32_t *dirs, int B, const DevParams &p, float *out,
+                                float4 *gains, unsigned long long *queue, int *status, cudaStream_t s);
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                               const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s);
 cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,
@@ -90,6 +93,19 @@ cudaError_t launch_rle_encode_3d_static(const Vox3D &v, const DevParams &p, int3
                                         cudaStream_t s);
 
 int sm_count();
+
+// exploration loop (fsmi_explore.cu): trajectory visit stamps and sums, the Bayesian map update
+cudaError_t launch_traj_stamps(int W, int H, const int32_t *poses, int P, const int32_t *traj_off, int T,
+                               const int32_t *dirs, int B, long long rfix, float rend, int cap, int32_t *stamp,
+                               int *status, cudaStream_t s);
+cudaError_t launch_row_sums(const float *v, long long rows, int cols, float *out, cudaStream_t s);
+cudaError_t launch_csr_sums(const float *v, int nv, const int32_t *off, int nseg, float *out, cudaStream_t s);
+cudaError_t launch_best_trajectory(const float *traj_mi, const int32_t *poses, int P, const int32_t *traj_off, int T,
+                                   float *ratio, int32_t *best, cudaStream_t s);
+cudaError_t launch_update_map_2d(float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                                 const float *ranges, long long rfix, int cap, float log_docc, float log_demp,
+                                 uint32_t *counts, int *status, cudaStream_t s);
+cudaError_t prepare_explore();
 
 // kernel loads and per-device lookups done ahead of stream capture (fsmi_prepare)
 cudaError_t prepare_2d();

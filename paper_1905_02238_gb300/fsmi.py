@@ -25,7 +25,7 @@ from . import build as _build
 EXACT, APPROX, UNIFORM = 0, 1, 2
 G_PDF, G_ERF = 0, 1
 FLAG_FULL_SWEEP = 0x1
-FN_EVAL_2D, FN_EVAL_BEAMS, FN_RLE_ENCODE_3D, FN_EVAL_RLE, FN_EVAL_3D = 0, 1, 2, 3, 4
+FN_EVAL_2D, FN_EVAL_BEAMS, FN_RLE_ENCODE_3D, FN_EVAL_RLE, FN_EVAL_3D, FN_UPDATE_MAP_2D = 0, 1, 2, 3, 4, 5
 QUEUE_BYTES = 256
 KIND_2D, KIND_RLE = 0, 1
 STATUS_BEAM_OVERFLOW, STATUS_RUN_OVERFLOW, STATUS_BAD_BEAM = 0x1, 0x2, 0x4
@@ -150,6 +150,11 @@ def load():
             "fsmi_graph_launch": [p, p],
             "fsmi_graph_destroy": [p],
             "fsmi_workspace_size": [i, ll, P, ctypes.POINTER(ctypes.c_size_t)],
+            "fsmi_trajectory_workspace_size": [i, i, i, ctypes.POINTER(ctypes.c_size_t)],
+            "fsmi_eval_trajectories_2d": [p, i, i, p, i, p, i, p, i, P, p, p, p, p, sz, p],
+            "fsmi_best_trajectory": [p, p, i, p, i, p, p, p],
+            "fsmi_scan_sums": [p, ll, i, p, p],
+            "fsmi_update_map_2d": [p, i, i, p, i, p, i, p, P, p, sz, p],
             "fsmi_device_status": [p, ctypes.POINTER(ctypes.c_int)],
             "fsmi_gauss_tail": [p, p, ll, p],
             "fsmi_rle_encode_3d_noalloc": [p, i, i, i, p, i, p, i, P, p, p, p, i, p],
@@ -292,6 +297,91 @@ def eval_2d_sets(grid, poses, dirs, sets, nbeams: int, prm: Params, out=None, ws
                                  _ptr(st), st.shape[0], nbeams, ctypes.byref(cp), _ptr(out), wp, wb, _stream()),
            "fsmi_eval_2d_sets")
     return m.out(out)
+
+
+def trajectory_workspace_size(W: int, H: int, T: int) -> int:
+    lib = load()
+    b = ctypes.c_size_t(0)
+    _raise(lib.fsmi_trajectory_workspace_size(W, H, T, ctypes.byref(b)), "fsmi_trajectory_workspace_size")
+    return int(b.value)
+
+
+def eval_trajectories_2d(grid, poses, traj_off, dirs, prm: Params, ws=None, out=None):
+    """fsmi_eval_trajectories_2d: MI along T trajectories (states = poses in CSR order traj_off
+    int32 [T+1]); cells counted at an earlier state add nothing later (Section 2.4).
+    Returns (beam_mi [P, B], state_mi [P], traj_mi [T]); `out` may pass those three tensors."""
+    lib = load()
+    m = _Marshal(grid, poses, traj_off, dirs)
+    g = m.arg(grid, torch.float32, "grid", 2)
+    ps = m.arg(poses, torch.int32, "poses", 2, 4)
+    to = m.arg(traj_off, torch.int32, "traj_off", 1)
+    ds = m.arg(dirs, torch.int32, "dirs", 2, 2)
+    P, B, T = ps.shape[0], ds.shape[0], to.shape[0] - 1
+    if out is None or m.host:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass preallocated outputs")
+        out = (torch.empty((P, B), dtype=torch.float32, device=m.dev), torch.empty(P, dtype=torch.float32, device=m.dev),
+               torch.empty(T, dtype=torch.float32, device=m.dev))
+    beam, state, traj = out
+    if ws is None:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass a preallocated workspace")
+        ws = torch.empty(trajectory_workspace_size(g.shape[1], g.shape[0], T), dtype=torch.uint8, device=m.dev)
+    wp, wb = _ws_args(ws)
+    cp = prm.c()
+    _raise(lib.fsmi_eval_trajectories_2d(_ptr(g), g.shape[1], g.shape[0], _ptr(ps), P, _ptr(to), T, _ptr(ds), B,
+                                         ctypes.byref(cp), _ptr(beam), _ptr(state), _ptr(traj), wp, wb, _stream()),
+           "fsmi_eval_trajectories_2d")
+    return m.out(beam), m.out(state), m.out(traj)
+
+
+def best_trajectory(traj_mi, poses, traj_off):
+    """fsmi_best_trajectory -> (ratio float32 [T] = MI per travel distance, best index int)."""
+    lib = load()
+    m = _Marshal(traj_mi, poses, traj_off)
+    tm = m.arg(traj_mi, torch.float32, "traj_mi", 1)
+    ps = m.arg(poses, torch.int32, "poses", 2, 4)
+    to = m.arg(traj_off, torch.int32, "traj_off", 1)
+    T = tm.shape[0]
+    ratio = torch.empty(T, dtype=torch.float32, device=m.dev)
+    best = torch.empty(1, dtype=torch.int32, device=m.dev)
+    _raise(lib.fsmi_best_trajectory(_ptr(tm), _ptr(ps), ps.shape[0], _ptr(to), T, _ptr(ratio), _ptr(best), _stream()),
+           "fsmi_best_trajectory")
+    return m.out(ratio), int(best.item())
+
+
+def scan_sums(beam_mi) -> torch.Tensor:
+    """fsmi_scan_sums: float32 [P, B] beam MI -> [P] scan MI per pose."""
+    lib = load()
+    m = _Marshal(beam_mi)
+    b = m.arg(beam_mi, torch.float32, "beam_mi", 2)
+    out = _out(None, (b.shape[0],), m)
+    _raise(lib.fsmi_scan_sums(_ptr(b), b.shape[0], b.shape[1], _ptr(out), _stream()), "fsmi_scan_sums")
+    return m.out(out)
+
+
+def update_map_2d(grid: torch.Tensor, poses, dirs, ranges, prm: Params, ws=None) -> torch.Tensor:
+    """fsmi_update_map_2d: Bayesian update (eq. 1) of `grid` (float32 CUDA tensor, in place) by
+    measured ranges float32 [P, B]. Returns grid."""
+    lib = load()
+    if not (isinstance(grid, torch.Tensor) and grid.is_cuda and grid.dtype == torch.float32 and grid.dim() == 2
+            and grid.is_contiguous()):
+        raise TypeError("grid must be a contiguous float32 CUDA tensor [H, W] (updated in place)")
+    m = _Marshal(poses, dirs, ranges)
+    ps = m.arg(poses, torch.int32, "poses", 2, 4)
+    ds = m.arg(dirs, torch.int32, "dirs", 2, 2)
+    rg = m.arg(ranges, torch.float32, "ranges", 2)
+    if tuple(rg.shape) != (ps.shape[0], ds.shape[0]):
+        raise ValueError(f"ranges must be [P, B] = [{ps.shape[0]}, {ds.shape[0]}], got {tuple(rg.shape)}")
+    if ws is None:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass a preallocated workspace")
+        ws = torch.empty(workspace_size(FN_UPDATE_MAP_2D, grid.numel()), dtype=torch.uint8, device=grid.device)
+    wp, wb = _ws_args(ws)
+    cp = prm.c()
+    _raise(lib.fsmi_update_map_2d(_ptr(grid), grid.shape[1], grid.shape[0], _ptr(ps), ps.shape[0], _ptr(ds),
+                                  ds.shape[0], _ptr(rg), ctypes.byref(cp), wp, wb, _stream()), "fsmi_update_map_2d")
+    return grid
 
 
 def eval_beams(off, o, l, lend, prm: Params, out=None, ws=None) -> torch.Tensor:
