@@ -345,6 +345,68 @@ fsmi_status fsmi_update_map_2d(float *map, int W, int H, const int32_t *poses, i
                                const fsmi_params *prm, void *ws, size_t ws_bytes,
                                fsmi_stream_t stream);
 
+/*
+ * Learned surrogate (not part of the paper; a library extension that prescreens candidate poses
+ * before exact FSMI reranks the best of them). One 2D beam's occupancy profile -> its predicted MI:
+ *   input  x[256][2]: sample i at distance i + 1/2 cells along the beam (the cell holding
+ *          o + (i + 1/2) d, d the beam's Q30 direction); (o, 1) inside the map, (0, 0) beyond it
+ *   conv1  2 -> 32 channels, kernel 3, stride 2, zero padding 1, ReLU (256 -> 128 positions);
+ *   conv2, conv3  32 -> 32, the same (-> 64 -> 32); fc1 1024 -> 256 (input t * 32 + c), ReLU;
+ *   fc2 256 -> 1.   conv: z[t][c] = b[c] + sum_{k<3} sum_ci W[c][k][ci] a[2t + k - 1][ci].
+ * Parameters: one flat float32 vector of FSMI_SURR_NPARAMS in the order W1 [32][3][2], b1 [32],
+ * W2 [32][3][32], b2, W3 [32][3][32], b3, W4 [256][1024], b4 [256], W5 [256], b5 [1]. Compute uses
+ * a BF16 copy of the same vector for the weights (uint16 bit patterns) and the float32 biases,
+ * with FP32 accumulation.
+ */
+#define FSMI_SURR_L 256
+#define FSMI_SURR_NPARAMS 269089
+
+/* fsmi_profiles_2d - BF16 profiles out [N][256][2] of beams `beam_ids` (flat p * B + b; NULL = all
+ * N = P * B beams in order). An id outside [0, P * B) gives an all-zero profile and sets
+ * FSMI_STATUS_BAD_BEAM. */
+fsmi_status fsmi_profiles_2d(const float *map, int W, int H, const int32_t *poses, int P,
+                             const int32_t *dirs, int B, const int32_t *beam_ids, long long N,
+                             uint16_t *out, fsmi_stream_t stream);
+
+/* Workspace of fsmi_surrogate_loss_grad for a batch of N (mode 0) or of fsmi_surrogate_predict
+ * for N beams (mode 1). */
+fsmi_status fsmi_surrogate_workspace_size(int mode, long long N, size_t *bytes);
+
+/* fsmi_surrogate_loss_grad - one training step's forward and backward on a batch of N profiles
+ * x [N][256][2] (BF16) with targets y [N]: loss = mean (pred - y)^2 (device float) and its gradient
+ * grad [FSMI_SURR_NPARAMS] with respect to the parameters (through the BF16 weights). Activations
+ * are kept in FP32. pred (optional) receives the N predictions. 1 <= N <= 65536. Deterministic. */
+fsmi_status fsmi_surrogate_loss_grad(const float *params, const uint16_t *wbf16, const uint16_t *x,
+                                     const float *y, int N, float *grad, float *loss, float *pred,
+                                     void *ws, size_t ws_bytes, fsmi_stream_t stream);
+
+/* fsmi_surrogate_adam - one Adam step (Kingma and Ba) with bias correction at step t >= 1 on params,
+ * moments m, v (all float32 [FSMI_SURR_NPARAMS]); refreshes the BF16 copy wbf16.
+ * fsmi_surrogate_cast - wbf16 = BF16(params) (round to nearest even). */
+fsmi_status fsmi_surrogate_adam(float *params, float *m, float *v, const float *grad, float lr,
+                                float beta1, float beta2, float eps, int t, uint16_t *wbf16,
+                                fsmi_stream_t stream);
+fsmi_status fsmi_surrogate_cast(const float *params, uint16_t *wbf16, fsmi_stream_t stream);
+
+/* fsmi_surrogate_predict - predictions pred [P*B] for every beam of every pose on the map (the
+ * profiles are sampled inside the kernel), or, with map == NULL, for N given profiles x. The conv
+ * layers and fc1 run on the tensor cores with BF16 activations between layers and FP32
+ * accumulation. ws: fsmi_surrogate_workspace_size(1, N) bytes, 16-byte aligned. */
+fsmi_status fsmi_surrogate_predict(const float *params, const uint16_t *wbf16, const float *map,
+                                   int W, int H, const int32_t *poses, int P, const int32_t *dirs,
+                                   int B, const uint16_t *x, long long N, float *pred, void *ws,
+                                   size_t ws_bytes, fsmi_stream_t stream);
+
+/* fsmi_topk - idx [k] = indices of the k largest of v [n] in descending order, lower index first
+ * among equal values, NaN last. 1 <= k <= n <= 16384. */
+fsmi_status fsmi_topk(const float *v, int n, int k, int32_t *idx, fsmi_stream_t stream);
+
+/* fsmi_gather_rows - dst[r][.] = src[idx[r]][.] for k rows of `width` int32 out of src's nrows
+ * (e.g. the poses a prescreen selected); an index outside [0, nrows) gives a row of zeros and sets
+ * FSMI_STATUS_BAD_BEAM. */
+fsmi_status fsmi_gather_rows(const int32_t *src, long long nrows, int width, const int32_t *idx, int k,
+                             int32_t *dst, fsmi_stream_t stream);
+
 /* Function ids for fsmi_workspace_size. */
 #define FSMI_FN_EVAL_2D 0
 #define FSMI_FN_EVAL_BEAMS 1

@@ -18,8 +18,9 @@ reranks the best of them. Architecture (fixed):
     conv: out[t][c] = b[c] + sum_{k < 3} sum_ci W[c][k][ci] in[2t + k - 1][ci]
 
 Parameters form one flat float vector in the order of LAYOUT. Weights are used rounded to BF16
-(round to nearest even) with accumulation in FP64 here; ``act_bf16`` also rounds the input of
-every layer to BF16 (the tensor-core inference path feeds BF16 activations).
+(round to nearest even) with accumulation in FP64 here; ``act_bf16`` also rounds the inputs of
+the conv layers and of fc1 to BF16 (the tensor-core inference path feeds them to the tensor cores
+in BF16; fc2 takes the fc1 activations in FP32).
 """
 from __future__ import annotations
 
@@ -150,7 +151,7 @@ def forward(theta, x, act_bf16: bool = False, bf16_weights: bool = True):
     a3 = rnd(np.maximum(z3, 0.0))
     h0 = a3.reshape(a3.shape[0], -1)  # index t * 32 + c
     z4 = h0 @ p["W4"].T + p["b4"]
-    a4 = rnd(np.maximum(z4, 0.0))
+    a4 = np.maximum(z4, 0.0)  # fc2 reads the fc1 activations in FP32 in both modes
     pred = a4 @ p["W5"] + p["b5"][0]
     return pred, dict(p=p, a0=a0, z1=z1, a1=a1, z2=z2, a2=a2, z3=z3, a3=a3, h0=h0, z4=z4, a4=a4)
 

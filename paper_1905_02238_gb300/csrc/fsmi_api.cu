@@ -323,6 +323,96 @@ fsmi_status fsmi_update_map_2d(float *map, int W, int H, const int32_t *poses, i
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
+fsmi_status fsmi_profiles_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                             const int32_t *beam_ids, long long N, uint16_t *out, fsmi_stream_t stream)
+{
+    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || N < 0) return FSMI_ERR_ARG;
+    if (!beam_ids && N != (long long)P * B) return FSMI_ERR_ARG;
+    if (N == 0) return FSMI_OK;
+    if (!map || !poses || !dirs || !out || B == 0) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_profiles(map, W, H, poses, P, dirs, B, beam_ids, N, out, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_surrogate_workspace_size(int mode, long long N, size_t *bytes)
+{
+    if (!bytes || N < 0 || (mode != 0 && mode != 1)) return FSMI_ERR_ARG;
+    if (mode == 0) {
+        if (N > 65536) return FSMI_ERR_CAPACITY;
+        *bytes = surrogate_train_floats((int)N) * sizeof(float);
+    } else {
+        *bytes = surrogate_infer_bytes(N);
+    }
+    return FSMI_OK;
+}
+
+fsmi_status fsmi_surrogate_loss_grad(const float *params, const uint16_t *wbf16, const uint16_t *x, const float *y,
+                                     int N, float *grad, float *loss, float *pred, void *ws, size_t ws_bytes,
+                                     fsmi_stream_t stream)
+{
+    if (N < 1 || N > 65536 || !params || !wbf16 || !x) return FSMI_ERR_ARG;
+    if (y && (!grad || !loss)) return FSMI_ERR_ARG;
+    if (!y && !pred) return FSMI_ERR_ARG;
+    if (!ws || !aligned16(ws) || ws_bytes < surrogate_train_floats(N) * sizeof(float)) return FSMI_ERR_WORKSPACE;
+    cudaError_t e = launch_surrogate_loss_grad(params, wbf16, x, y, N, grad, loss, pred, (float *)ws,
+                                               (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_surrogate_adam(float *params, float *m, float *v, const float *grad, float lr, float beta1,
+                                float beta2, float eps, int t, uint16_t *wbf16, fsmi_stream_t stream)
+{
+    if (!params || !m || !v || !grad || !wbf16 || t < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f))
+        return FSMI_ERR_ARG;
+    cudaError_t e = launch_surrogate_adam(params, m, v, grad, lr, beta1, beta2, eps, t, wbf16, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_surrogate_cast(const float *params, uint16_t *wbf16, fsmi_stream_t stream)
+{
+    if (!params || !wbf16) return FSMI_ERR_ARG;
+    cudaError_t e = launch_surrogate_cast(params, wbf16, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_surrogate_predict(const float *params, const uint16_t *wbf16, const float *map, int W, int H,
+                                   const int32_t *poses, int P, const int32_t *dirs, int B, const uint16_t *x,
+                                   long long N, float *pred, void *ws, size_t ws_bytes, fsmi_stream_t stream)
+{
+    if (!params || !wbf16 || !pred) return FSMI_ERR_ARG;
+    if (map) {
+        if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || (P > 0 && B > 0 && (!poses || !dirs))) return FSMI_ERR_ARG;
+        N = (long long)P * B;
+    } else if (N < 0 || (N > 0 && !x)) {
+        return FSMI_ERR_ARG;
+    }
+    if (N == 0) return FSMI_OK;
+    if (!ws || !aligned16(ws) || ws_bytes < surrogate_infer_bytes(N)) return FSMI_ERR_WORKSPACE;
+    cudaError_t e = launch_surrogate_infer(map, W, H, poses, dirs, B, x, N, wbf16, params, pred, ws,
+                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_topk(const float *v, int n, int k, int32_t *idx, fsmi_stream_t stream)
+{
+    if (!v || !idx || n < 1 || n > 16384 || k < 1 || k > n) return FSMI_ERR_ARG;
+    cudaError_t e = launch_topk(v, n, k, idx, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_gather_rows(const int32_t *src, long long nrows, int width, const int32_t *idx, int k, int32_t *dst,
+                             fsmi_stream_t stream)
+{
+    if (width < 1 || k < 0 || nrows < 0 || (k > 0 && (!src || !idx || !dst))) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_gather_rows(src, nrows, width, idx, k, dst, sp, (cudaStream_t)stream);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
 fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                             const fsmi_params *prm, float *out, void *ws, size_t ws_bytes, fsmi_stream_t stream)
 {
@@ -575,6 +665,7 @@ fsmi_status fsmi_prepare(void)
     cudaError_t e = prepare_2d();
     if (e == cudaSuccess) e = prepare_rle();
     if (e == cudaSuccess) e = prepare_explore();
+    if (e == cudaSuccess) e = prepare_surrogate();
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 

@@ -27,6 +27,7 @@ G_PDF, G_ERF = 0, 1
 FLAG_FULL_SWEEP = 0x1
 FN_EVAL_2D, FN_EVAL_BEAMS, FN_RLE_ENCODE_3D, FN_EVAL_RLE, FN_EVAL_3D, FN_UPDATE_MAP_2D = 0, 1, 2, 3, 4, 5
 QUEUE_BYTES = 256
+SURR_L, SURR_NPARAMS = 256, 269089
 KIND_2D, KIND_RLE = 0, 1
 STATUS_BEAM_OVERFLOW, STATUS_RUN_OVERFLOW, STATUS_BAD_BEAM = 0x1, 0x2, 0x4
 MAX_RANGE_2D, MAX_CELLS, MAX_SAMPLES_3D = 1024.0, 2048, 1024
@@ -155,6 +156,15 @@ def load():
             "fsmi_best_trajectory": [p, p, i, p, i, p, p, p],
             "fsmi_scan_sums": [p, ll, i, p, p],
             "fsmi_update_map_2d": [p, i, i, p, i, p, i, p, P, p, sz, p],
+            "fsmi_profiles_2d": [p, i, i, p, i, p, i, p, ll, p, p],
+            "fsmi_surrogate_workspace_size": [i, ll, ctypes.POINTER(ctypes.c_size_t)],
+            "fsmi_surrogate_loss_grad": [p, p, p, p, i, p, p, p, p, sz, p],
+            "fsmi_surrogate_adam": [p, p, p, p, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i, p,
+                                    p],
+            "fsmi_surrogate_cast": [p, p, p],
+            "fsmi_surrogate_predict": [p, p, p, i, i, p, i, p, i, p, ll, p, p, sz, p],
+            "fsmi_topk": [p, i, i, p, p],
+            "fsmi_gather_rows": [p, ll, i, p, i, p, p],
             "fsmi_device_status": [p, ctypes.POINTER(ctypes.c_int)],
             "fsmi_gauss_tail": [p, p, ll, p],
             "fsmi_rle_encode_3d_noalloc": [p, i, i, i, p, i, p, i, P, p, p, p, i, p],
@@ -350,12 +360,17 @@ def best_trajectory(traj_mi, poses, traj_off):
     return m.out(ratio), int(best.item())
 
 
-def scan_sums(beam_mi) -> torch.Tensor:
+def scan_sums_into(beam_mi, out) -> torch.Tensor:
+    """fsmi_scan_sums into a preallocated device tensor out [P]."""
+    return scan_sums(beam_mi, out=out)
+
+
+def scan_sums(beam_mi, out=None) -> torch.Tensor:
     """fsmi_scan_sums: float32 [P, B] beam MI -> [P] scan MI per pose."""
     lib = load()
     m = _Marshal(beam_mi)
     b = m.arg(beam_mi, torch.float32, "beam_mi", 2)
-    out = _out(None, (b.shape[0],), m)
+    out = _out(out, (b.shape[0],), m)
     _raise(lib.fsmi_scan_sums(_ptr(b), b.shape[0], b.shape[1], _ptr(out), _stream()), "fsmi_scan_sums")
     return m.out(out)
 
@@ -617,3 +632,127 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+# ---- learned surrogate ------------------------------------------------------------------------------
+
+def profiles_2d(grid, poses, dirs, beam_ids=None, out=None) -> torch.Tensor:
+    """fsmi_profiles_2d -> bfloat16 [N][256][2] beam profiles (all P*B beams, or beam_ids)."""
+    lib = load()
+    m = _Marshal(grid, poses, dirs, beam_ids)
+    g = m.arg(grid, torch.float32, "grid", 2)
+    ps = m.arg(poses, torch.int32, "poses", 2, 4)
+    ds = m.arg(dirs, torch.int32, "dirs", 2, 2)
+    ids = m.arg(beam_ids, torch.int32, "beam_ids", 1) if beam_ids is not None else None
+    N = ids.shape[0] if ids is not None else ps.shape[0] * ds.shape[0]
+    if out is None or m.host:
+        out = torch.empty((N, SURR_L, 2), dtype=torch.bfloat16, device=m.dev)
+    _raise(lib.fsmi_profiles_2d(_ptr(g), g.shape[1], g.shape[0], _ptr(ps), ps.shape[0], _ptr(ds), ds.shape[0],
+                                _ptr(ids), N, _ptr(out), _stream()), "fsmi_profiles_2d")
+    return m.out(out)
+
+
+def surrogate_workspace_size(mode: int, N: int) -> int:
+    lib = load()
+    b = ctypes.c_size_t(0)
+    _raise(lib.fsmi_surrogate_workspace_size(mode, N, ctypes.byref(b)), "fsmi_surrogate_workspace_size")
+    return int(b.value)
+
+
+def _dev_tensor(t, dtype, name, numel=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t
+
+
+def surrogate_loss_grad(params, wbf16, x, y, grad, loss, pred=None, ws=None):
+    """fsmi_surrogate_loss_grad: MSE loss (device float32 [1]) and its gradient into grad; with
+    y=None only the predictions (pred) are computed. All tensors on the device."""
+    lib = load()
+    _dev_tensor(params, torch.float32, "params", SURR_NPARAMS)
+    _dev_tensor(wbf16, torch.bfloat16, "wbf16", SURR_NPARAMS)
+    _dev_tensor(x, torch.bfloat16, "x")
+    N = x.shape[0]
+    if y is not None:
+        _dev_tensor(y, torch.float32, "y", N)
+        _dev_tensor(grad, torch.float32, "grad", SURR_NPARAMS)
+        _dev_tensor(loss, torch.float32, "loss", 1)
+    if pred is not None:
+        _dev_tensor(pred, torch.float32, "pred", N)
+    if ws is None:
+        ws = torch.empty(surrogate_workspace_size(0, N), dtype=torch.uint8, device=x.device)
+    wp, wb = _ws_args(ws)
+    _raise(lib.fsmi_surrogate_loss_grad(_ptr(params), _ptr(wbf16), _ptr(x), _ptr(y), N, _ptr(grad), _ptr(loss),
+                                        _ptr(pred), wp, wb, _stream()), "fsmi_surrogate_loss_grad")
+
+
+def surrogate_adam(params, m, v, grad, lr: float, t: int, wbf16, beta1=0.9, beta2=0.999, eps=1e-8):
+    lib = load()
+    for name, tt in (("params", params), ("m", m), ("v", v), ("grad", grad)):
+        _dev_tensor(tt, torch.float32, name, SURR_NPARAMS)
+    _dev_tensor(wbf16, torch.bfloat16, "wbf16", SURR_NPARAMS)
+    _raise(lib.fsmi_surrogate_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), float(lr), float(beta1), float(beta2),
+                                   float(eps), int(t), _ptr(wbf16), _stream()), "fsmi_surrogate_adam")
+
+
+def surrogate_cast(params, wbf16):
+    lib = load()
+    _dev_tensor(params, torch.float32, "params", SURR_NPARAMS)
+    _dev_tensor(wbf16, torch.bfloat16, "wbf16", SURR_NPARAMS)
+    _raise(lib.fsmi_surrogate_cast(_ptr(params), _ptr(wbf16), _stream()), "fsmi_surrogate_cast")
+
+
+def surrogate_predict(params, wbf16, grid=None, poses=None, dirs=None, x=None, out=None, ws=None) -> torch.Tensor:
+    """fsmi_surrogate_predict on the tensor cores: every beam of every pose on `grid` (profiles sampled
+    in the kernel) -> float32 [P*B], or given profiles x [N][256][2] -> [N]."""
+    lib = load()
+    _dev_tensor(params, torch.float32, "params", SURR_NPARAMS)
+    _dev_tensor(wbf16, torch.bfloat16, "wbf16", SURR_NPARAMS)
+    dev = params.device
+    if grid is not None:
+        g = _dev_tensor(grid, torch.float32, "grid")
+        ps = _dev_tensor(poses, torch.int32, "poses")
+        ds = _dev_tensor(dirs, torch.int32, "dirs")
+        N = ps.shape[0] * ds.shape[0]
+        args = (_ptr(g), g.shape[1], g.shape[0], _ptr(ps), ps.shape[0], _ptr(ds), ds.shape[0], None, 0)
+    else:
+        xx = _dev_tensor(x, torch.bfloat16, "x")
+        N = xx.shape[0]
+        args = (None, 0, 0, None, 0, None, 0, _ptr(xx), N)
+    if out is None:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass a preallocated `out`")
+        out = torch.empty(N, dtype=torch.float32, device=dev)
+    if ws is None:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass a preallocated workspace")
+        ws = torch.empty(surrogate_workspace_size(1, N), dtype=torch.uint8, device=dev)
+    wp, wb = _ws_args(ws)
+    _raise(lib.fsmi_surrogate_predict(_ptr(params), _ptr(wbf16), *args, _ptr(out), wp, wb, _stream()),
+           "fsmi_surrogate_predict")
+    return out
+
+
+def topk(v, k: int, out=None) -> torch.Tensor:
+    """fsmi_topk: int32 indices of the k largest values, descending, lower index first on ties."""
+    lib = load()
+    vv = _dev_tensor(v, torch.float32, "v")
+    if out is None:
+        out = torch.empty(k, dtype=torch.int32, device=vv.device)
+    _raise(lib.fsmi_topk(_ptr(vv), vv.numel(), k, _ptr(out), _stream()), "fsmi_topk")
+    return out
+
+
+def gather_rows(src, idx, out=None) -> torch.Tensor:
+    """fsmi_gather_rows: src int32 [R][w], idx int32 [k] -> [k][w]."""
+    lib = load()
+    s_ = _dev_tensor(src, torch.int32, "src")
+    ii = _dev_tensor(idx, torch.int32, "idx")
+    w = s_.shape[1]
+    if out is None:
+        out = torch.empty((ii.numel(), w), dtype=torch.int32, device=s_.device)
+    _raise(lib.fsmi_gather_rows(_ptr(s_), s_.shape[0], w, _ptr(ii), ii.numel(), _ptr(out), _stream()),
+           "fsmi_gather_rows")
+    return out

@@ -1,0 +1,225 @@
+"""GPU parity of the learned surrogate's kernels (profiles, training forward/backward, Adam,
+tensor-core inference, top-k, gather) against the FP64 oracle in oracle/surrogate.py, and the
+properties of training (determinism, checkpoint resume)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import surrogate as S
+from paper_1905_02238_gb300 import fsmi, synth
+from paper_1905_02238_gb300 import surrogate as sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_1905_02238_gb300 import build
+
+    build.build()
+    return fsmi.load()
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _case(seed=1, n_poses=6, nb=40):
+    grid = synth.office_grid(300, n_obst=40, seed=seed)
+    poses = synth.free_cell_poses_2d(grid, n_poses, seed=seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    dirs = np.concatenate([synth.beam_dirs_2d(nb - 8), synth.random_dirs_2d(8, rng)])
+    return grid, poses, dirs
+
+
+def _theta(seed=3):
+    rng = np.random.default_rng(seed)
+    th = sg.init_params(seed)
+    th += rng.normal(0, 0.02, th.shape).astype(np.float32)  # non-zero biases
+    return th
+
+
+def test_param_layout_matches_oracle():
+    assert fsmi.SURR_NPARAMS == S.n_params()
+    assert [n for n, _ in sg.LAYOUT] == [n for n, _ in S.LAYOUT]
+    assert all(tuple(a) == tuple(b) for (_, a), (_, b) in zip(sg.LAYOUT, S.LAYOUT))
+
+
+def test_profiles_bit_exact():
+    grid, poses, dirs = _case()
+    x = fsmi.profiles_2d(_cuda(grid), _cuda(poses), _cuda(dirs)).float().cpu().numpy().astype(np.float64)
+    ref = S.bf16_round(S.profiles_2d(grid, poses, dirs))
+    np.testing.assert_array_equal(x, ref)
+    ids = np.array([5, 0, 77, 239, 3], np.int32)
+    xs = fsmi.profiles_2d(_cuda(grid), _cuda(poses), _cuda(dirs), beam_ids=_cuda(ids)).float().cpu().numpy()
+    np.testing.assert_array_equal(xs, x[ids])
+
+
+def _profiles(grid, poses, dirs):
+    x = fsmi.profiles_2d(_cuda(grid), _cuda(poses), _cuda(dirs))
+    return x, x.float().cpu().numpy().astype(np.float64)
+
+
+def test_loss_and_gradient_match_oracle():
+    grid, poses, dirs = _case(n_poses=3, nb=40)
+    x, xh = _profiles(grid, poses, dirs)
+    N = x.shape[0]
+    rng = np.random.default_rng(4)
+    y = rng.uniform(0, 3, N).astype(np.float32)
+    th = _theta()
+    params = _cuda(th)
+    wb = torch.empty(fsmi.SURR_NPARAMS, dtype=torch.bfloat16, device="cuda")
+    fsmi.surrogate_cast(params, wb)
+    np.testing.assert_array_equal(wb.float().cpu().numpy().astype(np.float64), S.bf16_round(th))
+    grad = torch.zeros(fsmi.SURR_NPARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    pred = torch.zeros(N, device="cuda")
+    fsmi.surrogate_loss_grad(params, wb, x, _cuda(y), grad, loss, pred=pred)
+    rpred, cache = S.forward(th, xh)
+    rloss, dpred = S.mse(rpred, y)
+    rgrad = S.backward(cache, dpred)
+    np.testing.assert_allclose(pred.cpu().numpy(), rpred, rtol=2e-5, atol=2e-5 * np.abs(rpred).max())
+    assert abs(float(loss.item()) - rloss) <= 5e-5 * rloss
+    g = grad.cpu().numpy().astype(np.float64)
+    for name, (o, shape) in S.offsets().items():
+        n = int(np.prod(shape))
+        a, b = g[o:o + n], rgrad[o:o + n]
+        # FP32 accumulation over up to N * positions terms against FP64
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-9, name
+    # the same step twice gives the same floats
+    g2 = torch.zeros_like(grad)
+    fsmi.surrogate_loss_grad(params, wb, x, _cuda(y), g2, loss)
+    assert torch.equal(g2, grad)
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(5)
+    th = _theta(6)
+    g = rng.normal(0, 1e-2, th.shape).astype(np.float32)
+    m0 = rng.normal(0, 1e-3, th.shape).astype(np.float32)
+    v0 = rng.uniform(0, 1e-5, th.shape).astype(np.float32)
+    p, m, v = _cuda(th), _cuda(m0), _cuda(v0)
+    wb = torch.empty(fsmi.SURR_NPARAMS, dtype=torch.bfloat16, device="cuda")
+    fsmi.surrogate_adam(p, m, v, _cuda(g), 1e-3, 7, wb)
+    # the kernel's hyperparameters are the FP32 values of 0.9, 0.999, 1e-3, 1e-8 (1 - beta is then
+    # exact in FP32); the oracle takes the same values
+    b1, b2, lr, eps = (float(np.float32(x)) for x in (0.9, 0.999, 1e-3, 1e-8))
+    rp, rm, rv = S.adam(th.astype(np.float64), m0.astype(np.float64), v0.astype(np.float64), g.astype(np.float64), 7,
+                        lr, b1, b2, eps)
+    # FP32 moments: within a few units in the last place of the two terms they add (the sum can
+    # cancel, so the bound is on the terms, not on the result)
+    u = 2.0 ** -22
+    gm, gv, gp = (t.cpu().numpy().astype(np.float64) for t in (m, v, p))
+    assert np.all(np.abs(gm - rm) <= u * (b1 * np.abs(m0) + (1 - b1) * np.abs(g)))
+    assert np.all(np.abs(gv - rv) <= u * (b2 * v0 + (1 - b2) * g.astype(np.float64) ** 2))
+    # the parameter update from the GPU's own moments: a few ulp of theta and of the step
+    c1, c2 = float(np.float32(1 - b1 ** 7)), float(np.float32(1 - b2 ** 7))
+    step = lr * (gm / c1) / (np.sqrt(gv / c2) + eps)
+    ref_p = th.astype(np.float64) - step
+    assert np.all(np.abs(gp - ref_p) <= u * (np.abs(th) + 4 * np.abs(step)))
+    np.testing.assert_allclose(gp, rp, rtol=0, atol=2e-6)  # and close to the all-FP64 step
+    np.testing.assert_array_equal(wb.float().cpu().numpy().astype(np.float64), S.bf16_round(p.cpu().numpy()))
+
+
+def test_tensor_core_inference_matches_oracle():
+    grid, poses, dirs = _case(seed=8, n_poses=7, nb=48)  # 336 beams: 2 full fc row tiles + a tail
+    x, xh = _profiles(grid, poses, dirs)
+    th = _theta(9)
+    params = _cuda(th)
+    wb = torch.empty(fsmi.SURR_NPARAMS, dtype=torch.bfloat16, device="cuda")
+    fsmi.surrogate_cast(params, wb)
+    got = fsmi.surrogate_predict(params, wb, x=x).cpu().numpy().astype(np.float64)
+    ref, _ = S.forward(th, xh, act_bf16=True)
+    ref32, _ = S.forward(th, xh)
+    err = np.abs(got - ref)
+    scale = np.abs(ref).max()
+    # BF16 activations: the GPU rounds FP32 sums and the oracle FP64 sums to BF16; the two differ
+    # by one BF16 step (2^-8 relative) where the sums straddle a rounding boundary
+    assert err.max() <= 1e-3 * scale, (err.max(), scale)
+    assert np.median(err) <= 1e-5 * scale
+    # and the BF16-activation network stays close to the FP32-activation one
+    assert np.abs(got - ref32).max() <= 3e-2 * scale
+    # profiles sampled inside the kernel give the same floats
+    got_map = fsmi.surrogate_predict(params, wb, grid=_cuda(grid), poses=_cuda(poses), dirs=_cuda(dirs))
+    np.testing.assert_array_equal(got_map.cpu().numpy(), got.astype(np.float32))
+
+
+def test_topk_and_gather():
+    rng = np.random.default_rng(10)
+    for n, k in ((1, 1), (100, 10), (4096, 64), (5000, 5000), (16384, 7)):
+        v = rng.normal(size=n).astype(np.float32)
+        v[rng.choice(n, n // 10, replace=False)] = 0.5  # ties
+        if n > 10:
+            v[3] = np.nan
+        idx = fsmi.topk(_cuda(v), k).cpu().numpy()
+        key = np.where(np.isnan(v), -np.inf, v)
+        ref = np.lexsort((np.arange(n), -key))[:k]
+        np.testing.assert_array_equal(idx, ref)
+    src = rng.integers(-100, 100, (50, 4)).astype(np.int32)
+    ii = np.array([3, 3, 49, 0], np.int32)
+    np.testing.assert_array_equal(fsmi.gather_rows(_cuda(src), _cuda(ii)).cpu().numpy(), src[ii])
+
+
+def _tiny_training_set():
+    dirs = synth.beam_dirs_2d(90)
+    prm = fsmi.Params(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0)
+    return sg.label_maps(2, 64, dirs, prm, seed=300, size=512), dirs
+
+
+def test_training_is_deterministic_and_resumable(tmp_path):
+    maps, dirs = _tiny_training_set()
+    scale = float(torch.cat([m.labels for m in maps]).mean())
+    a = sg.Surrogate(seed=1, scale=scale)
+    losses = a.train(maps, dirs, steps=60, batch=512, lr=2e-3, log_every=10)
+    assert losses[-1] < losses[0]
+    b = sg.Surrogate(seed=1, scale=scale)
+    b.train(maps, dirs, steps=60, batch=512, lr=2e-3)
+    assert torch.equal(a.params, b.params)
+    # checkpoint after 30 steps, resume for the rest: same floats as the 60-step run when the
+    # learning-rate schedule of the two halves is the same
+    c = sg.Surrogate(seed=1, scale=scale)
+    c.train(maps, dirs, steps=30, batch=512, lr=1e-3, lr_min=1e-3)
+    path = str(tmp_path / "ckpt.npz")
+    c.save(path)
+    c.train(maps, dirs, steps=30, batch=512, lr=1e-3, lr_min=1e-3)
+    d = sg.Surrogate.load(path)
+    d.train(maps, dirs, steps=30, batch=512, lr=1e-3, lr_min=1e-3)
+    assert torch.equal(c.params, d.params) and torch.equal(c.m, d.m) and torch.equal(c.v, d.v)
+
+
+@pytest.mark.slow
+def test_trained_surrogate_prescreen_beats_exact_all():
+    """The gain of the learned part: on a held-out 2048x2048 office map with 4096 candidate poses,
+    the surrogate prescreen plus exact rerank of its top 64 finds the exact top-10 (up to exact
+    ties at 1e-4) in less time than exact FSMI of every beam; an untrained network does not."""
+    dirs = synth.beam_dirs_2d(360)
+    d = _cuda(dirs)
+    prm = fsmi.Params(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0)
+    maps = sg.label_maps(7, 4096, d, prm, seed=100)  # 10.3 M labelled beams
+    lab = torch.cat([m.labels for m in maps])
+    net = sg.Surrogate(seed=0, scale=float(lab.std()), shift=float(lab.mean()))
+    net.train(maps, d, steps=2500, batch=4096, lr=2e-3)
+    grid, poses, _ = synth.config2(n_poses=4096, seed=200, pose_seed=201)
+    g, p = _cuda(grid), _cuda(poses)
+    ex = sg.ExactAll(g, p, d, prm)
+    ex.run()
+    scores = ex.score.clone()
+    pre = sg.Prescreen(net, g, p, d, prm, k=64)
+    found = pre.run()
+    assert sg.recall_with_ties(found, scores) >= 0.95
+    assert sg.regret(found, scores) <= 1e-4
+
+    def ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps
+
+    assert ms(pre.run) < ms(ex.run)
+    untrained = sg.Prescreen(sg.Surrogate(seed=0, scale=net.scale, shift=net.shift), g, p, d, prm, k=64)
+    assert sg.recall_with_ties(untrained.run(), scores) < sg.recall_with_ties(found, scores)
