@@ -22,7 +22,9 @@
  *     a kernel can see (a beam longer than its capacity, an RLE output buffer too small) set bits
  *     of a per-device status word that fsmi_device_status() reads; the affected outputs are NaN
  *     (MI) or truncated (runs), never written out of bounds.
- *   - Kernels never spin on flags or other kernels; nothing here can hang the device.
+ *   - Kernels never wait on other kernels. The only waits inside a kernel are on the CTA's own
+ *     tensor-core operations (fsmi_surrogate_predict); each is bounded and, if it gives up, sets
+ *     FSMI_STATUS_TIMEOUT and leaves NaN outputs. Nothing here can hang the device.
  *   - Results for a beam whose origin lies outside the map are 0 (the beam crosses no cell).
  */
 #ifndef FSMI_H
@@ -64,6 +66,7 @@ typedef enum { FSMI_G_PDF = 0, FSMI_G_ERF = 1 } fsmi_kernel;
 #define FSMI_STATUS_RUN_OVERFLOW 0x2   /* RLE output exceeded run_capacity: runs were truncated */
 #define FSMI_STATUS_BAD_BEAM 0x4       /* an explicit beam or ray exceeded the per-beam maximum */
 #define FSMI_STATUS_INTERNAL 0x8       /* a traversal produced a cell outside the map (library bug) */
+#define FSMI_STATUS_TIMEOUT 0x10       /* a bounded wait inside a kernel gave up: its outputs are NaN */
 
 typedef struct {
     int variant;        /* fsmi_variant */
@@ -390,8 +393,9 @@ fsmi_status fsmi_surrogate_cast(const float *params, uint16_t *wbf16, fsmi_strea
 
 /* fsmi_surrogate_predict - predictions pred [P*B] for every beam of every pose on the map (the
  * profiles are sampled inside the kernel), or, with map == NULL, for N given profiles x. The conv
- * layers and fc1 run on the tensor cores with BF16 activations between layers and FP32
- * accumulation. ws: fsmi_surrogate_workspace_size(1, N) bytes, 16-byte aligned. */
+ * layers (mma.sync) and fc1 (tcgen05, accumulators in TMEM) run on the tensor cores with BF16
+ * activations between layers and FP32 accumulation; fc2 reads the fc1 activations in FP32.
+ * ws: fsmi_surrogate_workspace_size(1, N) bytes, 16-byte aligned. */
 fsmi_status fsmi_surrogate_predict(const float *params, const uint16_t *wbf16, const float *map,
                                    int W, int H, const int32_t *poses, int P, const int32_t *dirs,
                                    int B, const uint16_t *x, long long N, float *pred, void *ws,

@@ -391,7 +391,9 @@ fsmi_status fsmi_surrogate_predict(const float *params, const uint16_t *wbf16, c
     }
     if (N == 0) return FSMI_OK;
     if (!ws || !aligned16(ws) || ws_bytes < surrogate_infer_bytes(N)) return FSMI_ERR_WORKSPACE;
-    cudaError_t e = launch_surrogate_infer(map, W, H, poses, dirs, B, x, N, wbf16, params, pred, ws,
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaError_t e = launch_surrogate_infer(map, W, H, poses, dirs, B, x, N, wbf16, params, pred, ws, sp,
                                            (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }

@@ -119,7 +119,7 @@ cudaError_t launch_surrogate_adam(float *p, float *m, float *v, const float *g, 
 cudaError_t launch_surrogate_cast(const float *p, void *wbf16, cudaStream_t s);
 cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t *poses, const int32_t *dirs, int B,
                                    const void *x, long long N, const void *wbf16, const float *params, float *pred,
-                                   void *ws, cudaStream_t s);
+                                   void *ws, int *status, cudaStream_t s);
 cudaError_t launch_topk(const float *v, int n, int k, int32_t *idx, cudaStream_t s);
 cudaError_t launch_gather_rows(const int32_t *src, long long nrows, int width, const int32_t *idx, int k,
                                int32_t *dst, int *status, cudaStream_t s);

@@ -433,102 +433,129 @@ __device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<const unsigned *>(&v);
 }
 
-// Shared-memory row strides (bf16 elements) chosen so that the 8 rows one ldmatrix phase reads
-// fall into 8 different 4-bank groups: 24 (48 B) for the K = 16 operands, 104 (208 B) for K = 96.
-constexpr int kS1 = 24, kS2 = 104;
-constexpr int kConvWarps = 4;
-// per-warp buffers (bf16 elements): x [256][2]; R1 = im2col A1 [128][24] / A2 [64][104] / A3 [32][104];
-// R2 = act1 [128][32] / act2 [64][32]
-constexpr int kXs = kL * 2, kR1 = 64 * kS2, kR2 = 128 * kCh;
-constexpr int kConvWarpElems = kXs + kR1 + kR2;
-constexpr int kConvWElems = kCh * kS1 + 2 * kCh * kS2;  // W1, W2, W3
+__device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned &r0, unsigned &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
 
-// One m16 x n32 strip of a conv layer: rows [mt * 16, mt * 16 + 16) of the im2col operand A (row
-// stride sa) times W (32 rows, stride sw) over ksteps of 16; acc[nt][4] for the four n8 tiles.
-__device__ __forceinline__ void conv_strip(const bf16 *A, int sa, const bf16 *Wt, int sw, int mt, int ksteps,
-                                           float (&acc)[4][4])
+__device__ __forceinline__ void mma_bf16_k8(float (&c)[4], unsigned a0, unsigned a1, unsigned b0)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// Conv activations [rows][32 channels] (64 B per row) are kept in 128-byte lines of two rows;
+// the 16-byte chunk (row parity, channel quarter) of line L sits at chunk ((parity << 2) | q) ^
+// (L & 7). The eight rows 2t + k - 1 (t = t0 .. t0 + 7) that one ldmatrix phase reads for a conv
+// tap then land in eight different bank groups, and so do the eight rows one accumulator store
+// writes. Implicit GEMM: the im2col operand is addressed row by row, never materialised.
+__device__ __forceinline__ int act_chunk(int r, int q)
+{
+    const int line = r >> 1;
+    return line * 8 + ((((r & 1) << 2) | q) ^ (line & 7));  // in 16-byte units
+}
+
+constexpr int kConvWarps = 8;
+constexpr int kS2 = 104;  // W2 / W3 row stride (bf16): 208 B, eight rows in eight bank groups
+// per-warp buffers in 16-byte units: act1 (128 rows), then a 4 KB region that holds first the
+// profile x (64 units) and conv1's operand A1 (128 rows of 16 B), later act2 (64 rows)
+constexpr int kAct1Units = 128 * 4, kRegUnits = 256;
+constexpr int kConvWarpUnits = kAct1Units + kRegUnits;
+// block: W1 [32][8], W2 / W3 [32][104] bf16, biases, one zero chunk
+constexpr int kConvWBytes = kCh * 8 * 2 + 2 * kCh * kS2 * 2 + 3 * kCh * 4 + 16;
+
+// relu(acc + b) as bf16 pairs into a swizzled activation buffer (rows mt * 16 + g, + 8)
+__device__ __forceinline__ void store_act_swz(uint4 *act, const float *b, int mt, const float (&acc)[4][4])
+{
+    const int lane = lane_id(), g = lane >> 2, w = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int c = nt * 8 + 2 * w;
+        const int r0 = mt * 16 + g;
+        unsigned *p0 = reinterpret_cast<unsigned *>(act + act_chunk(r0, nt)) + w;
+        unsigned *p1 = reinterpret_cast<unsigned *>(act + act_chunk(r0 + 8, nt)) + w;
+        *p0 = pack_bf16x2(relu(acc[nt][0] + b[c]), relu(acc[nt][1] + b[c + 1]));
+        *p1 = pack_bf16x2(relu(acc[nt][2] + b[c]), relu(acc[nt][3] + b[c + 1]));
+    }
+}
+
+// Weight fragments of a K = 96 conv layer for all 6 k-steps and 4 n8 tiles.
+__device__ __forceinline__ void load_wfrag(const bf16 *Wt, unsigned (&bw)[6][4][2])
+{
+    const int lane = lane_id();
+#pragma unroll
+    for (int ks = 0; ks < 6; ++ks)
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+            const int row = np * 16 + (lane & 7) + 8 * (lane >> 4);
+            ldsm_x4(smem_u32(Wt + row * kS2 + ks * 16 + 8 * ((lane >> 3) & 1)), bw[ks][2 * np][0], bw[ks][2 * np][1],
+                    bw[ks][2 * np + 1][0], bw[ks][2 * np + 1][1]);
+        }
+}
+
+// One m16 x n32 strip of a stride-2, K = 96 conv from the swizzled activations `in` (Lin rows):
+// im2col row t, k-step ks (tap ks / 2, channel half ks % 2) is input row 2t + ks / 2 - 1.
+__device__ __forceinline__ void conv_strip_k96(const uint4 *in, const uint4 *zero, int mt, const unsigned (&bw)[6][4][2],
+                                               float (&acc)[4][4])
 {
     const int lane = lane_id();
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-    for (int ks = 0; ks < ksteps; ++ks) {
+    const int t = mt * 16 + (lane & 15);
+#pragma unroll
+    for (int ks = 0; ks < 6; ++ks) {
+        const int r = 2 * t + (ks >> 1) - 1;
+        const int q = ((ks & 1) << 1) | (lane >> 4);
+        const uint4 *src = r >= 0 ? in + act_chunk(r, q) : zero;
         unsigned a0, a1, a2, a3;
-        ldsm_x4(smem_u32(A + (mt * 16 + (lane & 15)) * sa + ks * 16 + 8 * (lane >> 4)), a0, a1, a2, a3);
+        ldsm_x4(smem_u32(src), a0, a1, a2, a3);
 #pragma unroll
-        for (int np = 0; np < 2; ++np) {  // two n8 tiles per ldmatrix.x4
-            unsigned b0, b1, b2, b3;
-            const int row = np * 16 + (lane & 7) + 8 * (lane >> 4);
-            ldsm_x4(smem_u32(Wt + row * sw + ks * 16 + 8 * ((lane >> 3) & 1)), b0, b1, b2, b3);
-            mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
-            mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
-        }
+        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[nt], a0, a1, a2, a3, bw[ks][nt][0], bw[ks][nt][1]);
     }
 }
 
-// acc -> relu(acc + b) as bf16 pairs into act [rows][32]
-__device__ __forceinline__ void store_act(bf16 *act, const float *b, int mt, const float (&acc)[4][4])
-{
-    const int lane = lane_id(), g = lane >> 2, c2 = 2 * (lane & 3);
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int c = nt * 8 + c2;
-        const int r0 = mt * 16 + g;
-        *reinterpret_cast<unsigned *>(act + r0 * kCh + c) =
-            pack_bf16x2(relu(acc[nt][0] + b[c]), relu(acc[nt][1] + b[c + 1]));
-        *reinterpret_cast<unsigned *>(act + (r0 + 8) * kCh + c) =
-            pack_bf16x2(relu(acc[nt][2] + b[c]), relu(acc[nt][3] + b[c + 1]));
-    }
-}
-
-// im2col of act [Lin][32] (stride 32) into A [Lin/2][sa]: A[t][k * 32 + ci] = act[2t + k - 1][ci]
-__device__ __forceinline__ void im2col(const bf16 *act, int Lin, bf16 *A)
-{
-    const int Lout = Lin >> 1;
-    for (int e = lane_id(); e < Lout * 3 * 4; e += 32) {  // 16-byte pieces: (t, k, quarter)
-        const int q = e & 3, k = (e >> 2) % 3, t = (e >> 2) / 3;
-        const int s = 2 * t + k - 1;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (s >= 0 && s < Lin) v = *reinterpret_cast<const uint4 *>(act + s * kCh + q * 8);
-        *reinterpret_cast<uint4 *>(A + t * kS2 + k * kCh + q * 8) = v;
-    }
-}
-
-// The conv stack of one beam: x [256][2] (bf16 pairs) in shared memory -> h0 row (1024 bf16) in
-// global memory, index t * 32 + c.
-__device__ void conv_stack(const __nv_bfloat162 *x, bf16 *R1, bf16 *R2, const bf16 *sW1, const bf16 *sW2,
+// The conv stack of one beam. x: profile as 256 words (bf16 pairs) in the warp's region; h0 row
+// (1024 bf16, index t * 32 + c) to global memory.
+__device__ void conv_stack(uint4 *act1, uint4 *reg, const uint4 *zero, const bf16 *sW1, const bf16 *sW2,
                            const bf16 *sW3, const float *sb, bf16 *__restrict__ h0)
 {
     const int lane = lane_id();
-    // conv1: A1[t] = {x[2t-1], x[2t], x[2t+1], 0 x 5} as 32-bit words (k * 2 + ci order)
-    for (int t = lane; t < 128; t += 32) {
-        const unsigned z = 0u;
-        const unsigned w0 = t > 0 ? *reinterpret_cast<const unsigned *>(x + 2 * t - 1) : z;
-        const unsigned w1 = *reinterpret_cast<const unsigned *>(x + 2 * t);
-        const unsigned w2 = *reinterpret_cast<const unsigned *>(x + 2 * t + 1);
-        uint4 *row = reinterpret_cast<uint4 *>(R1 + t * kS1);
-        row[0] = make_uint4(w0, w1, w2, z);
-        row[1] = make_uint4(z, z, z, z);
-    }
+    const unsigned *x = reinterpret_cast<const unsigned *>(reg);  // x[i] = (o, inside) of sample i
+    uint4 *A1 = reg + 64;                                          // 128 rows x 16 B
+    // conv1 operand: A1[t] = {x[2t-1], x[2t], x[2t+1], 0} (k * 2 + ci order, K padded to 8)
+    for (int t = lane; t < 128; t += 32)
+        A1[t] = make_uint4(t > 0 ? x[2 * t - 1] : 0u, x[2 * t], x[2 * t + 1], 0u);
     __syncwarp();
     float acc[4][4];
-    for (int mt = 0; mt < 8; ++mt) {
-        conv_strip(R1, kS1, sW1, kS1, mt, 1, acc);
-        store_act(R2, sb, mt, acc);
+    {
+        unsigned b[4];  // W1 fragments of the four n8 tiles (K = 8)
+        ldsm_x4(smem_u32(sW1 + lane * 8), b[0], b[1], b[2], b[3]);
+        for (int mt = 0; mt < 8; ++mt) {
+            unsigned a0, a1;
+            ldsm_x2(smem_u32(A1 + mt * 16 + (lane & 15)), a0, a1);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+                mma_bf16_k8(acc[nt], a0, a1, b[nt]);
+            }
+            store_act_swz(act1, sb, mt, acc);
+        }
     }
     __syncwarp();
-    im2col(R2, 128, R1);  // A2 [64][104]
-    __syncwarp();
+    unsigned bw[6][4][2];
+    load_wfrag(sW2, bw);
+    uint4 *act2 = reg;  // x and A1 are dead
     for (int mt = 0; mt < 4; ++mt) {
-        conv_strip(R1, kS2, sW2, kS2, mt, 6, acc);
-        store_act(R2, sb + kCh, mt, acc);  // act2 [64][32]
+        conv_strip_k96(act1, zero, mt, bw, acc);
+        store_act_swz(act2, sb + kCh, mt, acc);
     }
     __syncwarp();
-    im2col(R2, 64, R1);  // A3 [32][104]
-    __syncwarp();
+    load_wfrag(sW3, bw);
     const int g = lane >> 2, c2 = 2 * (lane & 3);
     const float *b3 = sb + 2 * kCh;
     for (int mt = 0; mt < 2; ++mt) {
-        conv_strip(R1, kS2, sW3, kS2, mt, 6, acc);
+        conv_strip_k96(act2, zero, mt, bw, acc);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
             const int c = nt * 8 + c2, t0 = mt * 16 + g;
@@ -550,16 +577,15 @@ __global__ void __launch_bounds__(kConvWarps * 32)
                  unsigned long long *queue)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16 *sW1 = (bf16 *)smem_raw;
-    bf16 *sW2 = sW1 + kCh * kS1;
-    bf16 *sW3 = sW2 + kCh * kS2;
+    bf16 *sW1 = (bf16 *)smem_raw;        // [32][8]
+    bf16 *sW2 = sW1 + kCh * 8;           // [32][104]
+    bf16 *sW3 = sW2 + kCh * kS2;         // [32][104]
     float *sb = (float *)(sW3 + kCh * kS2);  // b1, b2, b3
-    bf16 *wbase = (bf16 *)(sb + 3 * kCh) + (size_t)(threadIdx.x >> 5) * kConvWarpElems;
-    __nv_bfloat162 *xs = (__nv_bfloat162 *)wbase;
-    bf16 *R1 = wbase + kXs, *R2 = R1 + kR1;
-    // weights: rows of K values, zero-padded to the row stride
-    for (int e = threadIdx.x; e < kCh * kS1; e += blockDim.x) {
-        const int c = e / kS1, kk = e % kS1;
+    uint4 *zero = (uint4 *)(sb + 3 * kCh);
+    uint4 *wbase = zero + 1 + (size_t)(threadIdx.x >> 5) * kConvWarpUnits;
+    uint4 *act1 = wbase, *reg = wbase + kAct1Units;
+    for (int e = threadIdx.x; e < kCh * 8; e += blockDim.x) {
+        const int c = e / 8, kk = e % 8;
         sW1[e] = kk < kK * kCin ? w[oW1 + c * kK * kCin + kk] : __float2bfloat16_rn(0.0f);
     }
     for (int e = threadIdx.x; e < kCh * kS2; e += blockDim.x) {
@@ -572,8 +598,10 @@ __global__ void __launch_bounds__(kConvWarps * 32)
         sb[kCh + e] = params[oB2 + e];
         sb[2 * kCh + e] = params[oB3 + e];
     }
+    if (threadIdx.x == 0) *zero = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     const int lane = lane_id();
+    __nv_bfloat162 *xs = reinterpret_cast<__nv_bfloat162 *>(reg);
     for_each_item(N, queue, 4, [&](long long n) {
         if (map) {
             const int32_t *pose = poses + 4 * (n / B);
@@ -588,15 +616,13 @@ __global__ void __launch_bounds__(kConvWarps * 32)
             for (int i = lane; i < kL; i += 32) xs[i] = xg[n * kL + i];
         }
         __syncwarp();
-        conv_stack(xs, R1, R2, sW1, sW2, sW3, sb, h0 + n * kFlat);
+        conv_stack(act1, reg, zero, sW1, sW2, sW3, sb, h0 + n * kFlat);
     });
 }
 
-// fc1 + ReLU + fc2: pred[n] = b5 + sum_j W5[j] relu(b4[j] + sum_i W4[j][i] h0[n][i]).
-// Block tile 128 rows x 256 columns, 16 warps (4 x 4 of 32 x 64), K in chunks of 64 through a
-// double-buffered cp.async pipeline; rows of 128 B with the 16-byte chunks XOR-swizzled by row.
-constexpr int kFcRows = 128, kFcK = 64, kFcThreads = 512;
-constexpr int kFcStage = (kFcRows + kHid) * kFcK;  // bf16 elements per stage
+// Shared-memory layout of the fc operands: rows of 64 bf16 (128 B) with the 16-byte chunks
+// XOR-swizzled by row (the tensor cores' 128-byte swizzle when groups of 8 rows are 1024-B aligned).
+constexpr int kFcK = 64;
 
 __device__ __forceinline__ int swz(int row, int chunk) { return row * kFcK + ((chunk ^ (row & 7)) << 3); }
 
@@ -605,100 +631,193 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src, int by
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes));
 }
 
-__global__ void __launch_bounds__(kFcThreads)
-    k_fc_infer(const bf16 *__restrict__ h0, long long N, const bf16 *__restrict__ w, const float *__restrict__ params,
-               float *__restrict__ pred)
+// ---- fc1 + ReLU + fc2 on the 5th-generation tensor cores (tcgen05, accumulators in TMEM) ------------
+//
+// One CTA of 4 warps per 128-row tile: D[128][256] = h0_tile[128][1024] W4^T accumulates in
+// 256 TMEM columns (FP32, row i in TMEM lane i). K runs in chunks of 64 through a 4-stage
+// cp.async pipeline; each stage holds A (128 x 64) and B (256 x 64) in the K-major layout with
+// the 128-byte swizzle (16-byte chunk c of row r at c ^ (r & 7), 8-row groups 1024 B apart,
+// 1024-byte aligned). One thread issues 4 MMAs (M = 128, N = 256, K = 16) per chunk and commits
+// them to the stage's mbarrier, which frees the stage for the chunk S - 1 ahead. The epilogue
+// reads each row's 256 accumulators (one row per thread) and forms b5 + sum_j W5[j] relu(D + b4).
+// Every wait is bounded: on timeout the kernel sets FSMI_STATUS_TIMEOUT, writes NaN and stops.
+
+constexpr int kTcRows = 128, kTcK = 64, kTcStages = 4, kTcThreads = 128;
+constexpr int kTcStageBytes = (kTcRows + kHid) * kTcK * 2;  // 48 KB
+constexpr int kTcChunks = kFlat / kTcK;                      // 16
+constexpr unsigned kTcCols = 256;                            // TMEM columns (FP32 accumulators)
+constexpr size_t kTcSmem = 1024 + (size_t)kTcStages * kTcStageBytes + 8 * (kTcStages + 1) + 16;
+// instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1), B BF16
+// (bits 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28
+constexpr unsigned kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kHid >> 3) << 17) |
+                              ((unsigned)(kTcRows >> 4) << 24);
+constexpr long long kWaitPolls = 1LL << 22;
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ unsigned long long sdesc_sw128(unsigned saddr)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16 *st = (bf16 *)smem_raw;  // [2][128 + 256][64]
-    float *red = (float *)(st + 2 * kFcStage);  // [128][4]
-    const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const int wm = warp >> 2, wn = warp & 3;
+    unsigned long long d = (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+    d |= 1ull << 16;                      // leading byte offset: not used by swizzled K-major operands
+    d |= (unsigned long long)(1024 >> 4) << 32;  // stride byte offset
+    d |= 1ull << 46;                      // descriptor version of the sm_100 family
+    d |= 2ull << 61;                      // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned addr, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity)
+{
+    for (long long i = 0; i < kWaitPolls; ++i)
+        if (mbar_test(addr, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(unsigned dtmem, unsigned long long adesc, unsigned long long bdesc,
+                                       unsigned idesc, unsigned accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(unsigned mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32])
+{
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_fc_tc(const bf16 *__restrict__ h0, long long N, const bf16 *__restrict__ w, const float *__restrict__ params,
+            float *__restrict__ pred, int *status)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned long long *mbar = (unsigned long long *)(base + (size_t)kTcStages * kTcStageBytes);
+    unsigned *tmem_slot = (unsigned *)(mbar + kTcStages + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     const bf16 *W4 = w + oW4;
-    for (long long r0 = (long long)blockIdx.x * kFcRows; r0 < N; r0 += (long long)gridDim.x * kFcRows) {
-        auto load = [&](int stage, int kc) {
-            bf16 *sa = st + stage * kFcStage, *sbm = sa + kFcRows * kFcK;
-            for (int e = tid; e < (kFcRows + kHid) * 8; e += kFcThreads) {
-                const int row = e >> 3, ch = e & 7;
-                if (row < kFcRows) {
-                    const long long gr = r0 + row;
-                    const bool ok = gr < N;
-                    cp_async16(smem_u32(sa + swz(row, ch)), h0 + (ok ? gr : 0) * kFlat + kc * kFcK + ch * 8, ok ? 16 : 0);
-                } else {
-                    const int j = row - kFcRows;
-                    cp_async16(smem_u32(sbm + swz(j, ch)), W4 + (long long)j * kFlat + kc * kFcK + ch * 8, 16);
-                }
-            }
-            asm volatile("cp.async.commit_group;");
-        };
-        float acc[2][8][4];
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.0f;
-        constexpr int nk = kFlat / kFcK;
-        load(0, 0);
-        for (int kc = 0; kc < nk; ++kc) {
-            if (kc + 1 < nk) {
-                load((kc + 1) & 1, kc + 1);
-                asm volatile("cp.async.wait_group 1;");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kTcStages; ++i) mbar_init(smem_u32(mbar + i), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+    unsigned phase = 0u;        // bit s: parity of stage s's next completion
+    unsigned pending = 0u;      // bit s: a commit on stage s not yet waited for
+    bool ok = true;
+
+    auto load = [&](int stage, int kc, long long r0) {
+        bf16 *sa = (bf16 *)(base + (size_t)stage * kTcStageBytes), *sbm = sa + kTcRows * kTcK;
+        for (int e = tid; e < (kTcRows + kHid) * 8; e += kTcThreads) {
+            const int row = e >> 3, ch = e & 7;
+            if (row < kTcRows) {
+                const long long gr = r0 + row;
+                const bool in = gr < N;
+                cp_async16(smem_u32(sa + swz(row, ch)), h0 + (in ? gr : 0) * kFlat + kc * kTcK + ch * 8, in ? 16 : 0);
             } else {
-                asm volatile("cp.async.wait_group 0;");
+                const int j = row - kTcRows;
+                cp_async16(smem_u32(sbm + swz(j, ch)), W4 + (long long)j * kFlat + kc * kTcK + ch * 8, 16);
             }
+        }
+    };
+    auto wait_stage = [&](int stage) {
+        if (pending & (1u << stage)) {
+            ok = ok && mbar_wait(smem_u32(mbar + stage), (phase >> stage) & 1u);
+            phase ^= 1u << stage;
+            pending &= ~(1u << stage);
+        }
+    };
+
+    for (long long r0 = (long long)blockIdx.x * kTcRows; r0 < N && ok; r0 += (long long)gridDim.x * kTcRows) {
+        for (int c = 0; c < kTcStages - 1; ++c) {
+            load(c, c, r0);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        for (int kc = 0; kc < kTcChunks; ++kc) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(kTcStages - 2) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
-            const bf16 *sa = st + (kc & 1) * kFcStage, *sbm = sa + kFcRows * kFcK;
+            const int stage = kc % kTcStages;
+            if (tid == 0) {
+                tc_fence_after();
+                const unsigned a0 = smem_u32(base + (size_t)stage * kTcStageBytes);
+                const unsigned b0 = a0 + kTcRows * kTcK * 2;
 #pragma unroll
-            for (int ks = 0; ks < kFcK / 16; ++ks) {
-                unsigned a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int row = wm * 32 + mt * 16 + (lane & 15);
-                    ldsm_x4(smem_u32(sa + swz(row, ks * 2 + (lane >> 4))), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
-                }
-#pragma unroll
-                for (int np = 0; np < 4; ++np) {
-                    unsigned b0, b1, b2, b3;
-                    const int row = wn * 64 + np * 16 + (lane & 7) + 8 * (lane >> 4);
-                    ldsm_x4(smem_u32(sbm + swz(row, ks * 2 + ((lane >> 3) & 1))), b0, b1, b2, b3);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        mma_bf16(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-                        mma_bf16(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
-                    }
-                }
+                for (int k = 0; k < kTcK / 16; ++k)  // K = 16 per MMA: 32 bytes along the swizzled row
+                    tc_mma(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), kTcIdesc, (kc | k) != 0);
+                tc_commit(smem_u32(mbar + stage));
             }
-            __syncthreads();
-        }
-        // epilogue: relu(acc + b4) * W5, summed over this warp's 64 columns, then over the 4 warps
-        const int g = lane >> 2, c2 = 2 * (lane & 3);
-        float part[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int c = wn * 64 + nt * 8 + c2;
-            const float bb0 = params[oB4 + c], bb1 = params[oB4 + c + 1];
-            const float w0 = bf(w, oW5 + c), w1 = bf(w, oW5 + c + 1);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                part[mt][0] += relu(acc[mt][nt][0] + bb0) * w0 + relu(acc[mt][nt][1] + bb1) * w1;
-                part[mt][1] += relu(acc[mt][nt][2] + bb0) * w0 + relu(acc[mt][nt][3] + bb1) * w1;
+            pending |= 1u << stage;
+            const int next = kc + kTcStages - 1;  // its stage held chunk kc - 1
+            if (next < kTcChunks) {
+                wait_stage(next % kTcStages);
+                load(next % kTcStages, next, r0);
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
+        for (int st = 0; st < kTcStages; ++st) wait_stage(st);  // every MMA of the tile is done
+        ok = __syncthreads_and(ok);
+        tc_fence_after();
+        // epilogue: thread (warp w, lane l) owns row 32 w + l = TMEM lane 32 w + l
+        const long long row = r0 + warp * 32 + lane;
+        float acc = 0.0f;
+        for (int c0 = 0; c0 < kHid; c0 += 32) {
+            float v[32];
+            tc_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float v = part[mt][h];
-                v += __shfl_xor_sync(kFull, v, 1);
-                v += __shfl_xor_sync(kFull, v, 2);
-                if ((lane & 3) == 0) red[(wm * 32 + mt * 16 + g + 8 * h) * 4 + wn] = v;
-            }
-        __syncthreads();
-        if (tid < kFcRows && r0 + tid < N) {
-            const float *rr = red + tid * 4;
-            pred[r0 + tid] = params[oB5] + ((rr[0] + rr[1]) + (rr[2] + rr[3]));
+            for (int j = 0; j < 32; ++j) acc = fmaf(relu(v[j] + params[oB4 + c0 + j]), bf(w, oW5 + c0 + j), acc);
         }
+        if (row < N) pred[row] = ok ? params[oB5] + acc : __int_as_float(0x7fc00000);
+        tc_fence_before();
         __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok && tid == 0) set_status(status, FSMI_STATUS_TIMEOUT);
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
 // ---- selection -------------------------------------------------------------------------------------
@@ -873,13 +992,13 @@ size_t surrogate_infer_bytes(long long N) { return kQueueBytes + (size_t)N * kFl
 
 cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t *poses, const int32_t *dirs, int B,
                                    const void *x, long long N, const void *wbf16, const float *params, float *pred,
-                                   void *ws, cudaStream_t s)
+                                   void *ws, int *status, cudaStream_t s)
 {
     if (N <= 0) return cudaSuccess;
     const bf16 *w = (const bf16 *)wbf16;
     unsigned long long *queue = (unsigned long long *)ws;
     bf16 *h0 = (bf16 *)((char *)ws + kQueueBytes);
-    const size_t smem_conv = (size_t)(kConvWElems + kConvWarps * kConvWarpElems) * sizeof(bf16) + 3 * kCh * sizeof(float);
+    const size_t smem_conv = (size_t)kConvWBytes + (size_t)kConvWarps * kConvWarpUnits * 16;
     cudaError_t e = cudaFuncSetAttribute(k_conv_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_conv);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -894,12 +1013,11 @@ cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t
                                                                      (const __nv_bfloat162 *)x, N, w, params, h0, queue);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem_fc = (size_t)2 * kFcStage * sizeof(bf16) + (size_t)kFcRows * 4 * sizeof(float);
-    e = cudaFuncSetAttribute(k_fc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fc);
+    const long long tiles = (N + kTcRows - 1) / kTcRows;
+    e = cudaFuncSetAttribute(k_fc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (N + kFcRows - 1) / kFcRows;
-    k_fc_infer<<<(unsigned)(tiles < (long long)sm_count() ? tiles : sm_count()), kFcThreads, smem_fc, s>>>(
-        h0, N, w, params, pred);
+    k_fc_tc<<<(unsigned)(tiles < (long long)sm_count() ? tiles : sm_count()), kTcThreads, kTcSmem, s>>>(
+        h0, N, w, params, pred, status);
     return cudaGetLastError();
 }
 
@@ -926,7 +1044,7 @@ cudaError_t prepare_surrogate()
 {
     cudaFuncAttributes a;
     cudaError_t e = cudaFuncGetAttributes(&a, k_conv_infer);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_fc_infer);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_fc_tc);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_topk);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_gather_rows);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_profiles);

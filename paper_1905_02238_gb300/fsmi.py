@@ -29,7 +29,7 @@ FN_EVAL_2D, FN_EVAL_BEAMS, FN_RLE_ENCODE_3D, FN_EVAL_RLE, FN_EVAL_3D, FN_UPDATE_
 QUEUE_BYTES = 256
 SURR_L, SURR_NPARAMS = 256, 269089
 KIND_2D, KIND_RLE = 0, 1
-STATUS_BEAM_OVERFLOW, STATUS_RUN_OVERFLOW, STATUS_BAD_BEAM = 0x1, 0x2, 0x4
+STATUS_BEAM_OVERFLOW, STATUS_RUN_OVERFLOW, STATUS_BAD_BEAM, STATUS_TIMEOUT = 0x1, 0x2, 0x4, 0x10
 MAX_RANGE_2D, MAX_CELLS, MAX_SAMPLES_3D = 1024.0, 2048, 1024
 
 _lock = threading.Lock()
