@@ -225,3 +225,37 @@ def regret(found, exact_scores) -> float:
     """1 - (best exact score among `found`) / (best exact score overall)."""
     sc = _np(exact_scores).astype(np.float64)
     return float(1.0 - sc[_np(found)].max() / sc.max())
+
+
+def _main():
+    """Times the surrogate inference on a 2048x2048 office map (used for profiling):
+    python -m paper_1905_02238_gb300.surrogate --poses 512 --repeat 4"""
+    import argparse
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--poses", type=int, default=4096)
+    ap.add_argument("--beams", type=int, default=360)
+    ap.add_argument("--repeat", type=int, default=4)
+    args = ap.parse_args()
+    from . import build
+
+    build.build()
+    grid, poses, _ = synth.config2(n_poses=args.poses, seed=200, pose_seed=201)
+    g, p = torch.from_numpy(grid).cuda(), torch.from_numpy(poses).cuda()
+    d = torch.from_numpy(synth.beam_dirs_2d(args.beams)).cuda()
+    net = Surrogate(seed=0, scale=0.01, shift=0.06)
+    out = torch.empty(args.poses * args.beams, dtype=torch.float32, device="cuda")
+    ws = torch.empty(fsmi.surrogate_workspace_size(1, out.numel()), dtype=torch.uint8, device="cuda")
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    net.predict(g, p, d, out=out, ws=ws)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(args.repeat):
+        net.predict(g, p, d, out=out, ws=ws)
+    e.record()
+    torch.cuda.synchronize()
+    print(f"surrogate predict {args.poses} x {args.beams} beams: {s.elapsed_time(e) / args.repeat:.3f} ms")
+
+
+if __name__ == "__main__":
+    _main()
