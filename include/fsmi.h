@@ -186,6 +186,55 @@ fsmi_status fsmi_eval_2d_sets(const float *map, int W, int H, const int32_t *pos
                               size_t ws_bytes, fsmi_stream_t stream);
 
 /*
+ * fsmi_eval_mixed - a stream of candidate sets of both kinds in one persistent launch: 2D sets
+ * (beams on the occupancy grid, as fsmi_eval_2d) and 3D sets (rays through voxel submaps,
+ * sampled, run-length encoded and evaluated as fsmi_eval_3d). The sets form one ordered list of
+ * work items (one beam or ray each), taken by the warps in list order through the work queue, so
+ * sets complete roughly in the order given.
+ *   map, W, H, poses2 [P2][4], dirs2 [B2][2], prm2: the 2D part (prm2 NULL if there is no 2D set);
+ *     prm2->max_range bounds the sets' beam lengths.
+ *   vols [nvol] (device array of fsmi_volume), poses3 [P3][12], dirs3 [R3][3], prm3: the 3D part
+ *     (prm3 NULL if there is no 3D set); prm3->max_range bounds the sets' virtual cells per ray.
+ *   sets [nsets] (device array), sorted by out_offset, contiguous: out_offset[0] = 0,
+ *     out_offset[s+1] = out_offset[s] + npose[s] * ndir[s]; nitems = the total.
+ *   out float32 [nitems]: out[out_offset + p * ndir + d] in nats.
+ *   times (optional) uint64 [nitems + 1]: times[0] = the earliest block start, times[1 + i] = the
+ *     %globaltimer value (ns) when item i finished; a set's latency is the largest of its items'
+ *     times minus times[0].
+ *   ws: 16-byte aligned; fsmi_workspace_size(FSMI_FN_EVAL_2D, W*H) bytes (queue counter and 2D
+ *     per-cell gains), or FSMI_QUEUE_BYTES without 2D sets.
+ * Descriptors are checked per item in the kernel: an item of a malformed set (indices past the
+ * pose or direction arrays, a range outside its bound, a kind without parameters, a volume index
+ * outside [0, nvol)) gets NaN and sets FSMI_STATUS_BAD_BEAM. The work schedule is the 2D family's.
+ */
+#define FSMI_SET_2D 0
+#define FSMI_SET_3D 1
+typedef struct {
+    const float *vox; /* float32 [Z][Y][X] voxel occupancy, device memory */
+    int X, Y, Z;
+    int reserved;     /* 0 */
+} fsmi_volume;
+
+typedef struct {
+    int kind;              /* FSMI_SET_2D or FSMI_SET_3D */
+    int pose_offset;       /* first pose of the set in its kind's pose array */
+    int npose;             /* poses, >= 0 */
+    int dir_offset;        /* first direction in its kind's direction array */
+    int ndir;              /* beams (rays) per pose, >= 1 */
+    float max_range;       /* 2D: beam length, cells; 3D: virtual cells per ray (its floor) */
+    int volume;            /* 3D: index into vols */
+    int reserved;          /* 0 */
+    long long out_offset;  /* first output index */
+} fsmi_set;
+
+fsmi_status fsmi_eval_mixed(const float *map, int W, int H, const int32_t *poses2, int P2,
+                            const int32_t *dirs2, int B2, const fsmi_params *prm2,
+                            const fsmi_volume *vols, int nvol, const int32_t *poses3, int P3,
+                            const int32_t *dirs3, int R3, const fsmi_params *prm3, const fsmi_set *sets,
+                            int nsets, long long nitems, float *out, unsigned long long *times, void *ws,
+                            size_t ws_bytes, fsmi_stream_t stream);
+
+/*
  * fsmi_eval_beams - the same pair sums on explicit beams (Theorem 1's inputs: o_i, l_i).
  *   off    int32 [nbeams+1] CSR offsets; beam b owns cells off[b] .. off[b+1]-1
  *          (at most FSMI_MAX_CELLS cells).

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsmi.so")
-SOURCES = ["fsmi_api.cu", "fsmi_2d.cu", "fsmi_rle.cu", "fsmi_explore.cu", "fsmi_surrogate.cu"]
-HEADERS = ["fsmi_internal.h", "fsmi_device.cuh", "gauss_tail.cuh", "dda2d.cuh"]
+SOURCES = ["fsmi_api.cu", "fsmi_2d.cu", "fsmi_rle.cu", "fsmi_explore.cu", "fsmi_surrogate.cu", "fsmi_mixed.cu"]
+HEADERS = ["fsmi_internal.h", "fsmi_device.cuh", "gauss_tail.cuh", "dda2d.cuh", "eval2d.cuh", "evalrle.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

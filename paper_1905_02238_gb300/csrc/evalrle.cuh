@@ -1,0 +1,482 @@
+// 3D hot path (Section 4): virtual-cell sampling of each ray, run-length encoding (eq.
+// occup_rle), run prefixes P_E(u), D_E(v), and the run-pair sums of FSMI-RLE (Theorem 3),
+// Approx-FSMI-RLE (Theorem 5) and Uniform-FSMI-RLE (Theorem 6). One warp per ray.
+//
+// Run-pair terms. With x = 1 - o_u and a shift-invariant noise kernel g between virtual cells,
+//   A[x, Lu, Lv, t] = sum_{j<Lu} sum_{k<Lv} x^j g(j + t - k),  B = same with weight k.
+// The k-sum is a window of g: W0(m) = sum_{k<Lv} g(m - k) = Psi(m) - Psi(m - Lv) and
+// W1(m) = sum_{k<Lv} k g(m - k) = m W0(m) - (Psi1(m) - Psi1(m - Lv)), with the prefix tables
+// Psi(m) = sum_{d<=m} g(d), Psi1(m) = sum_{d<=m} d g(d) held in shared memory. Then
+// A = sum_j x^j W0(j + t), B = sum_j x^j W1(j + t), summed only where W0 can be non-zero
+// (j + t in [-K, Lv - 1 + K], K the kernel's support radius). No power x^{-t} is ever formed,
+// which avoids the instability the paper notes for its alpha/beta tables (Section 4.1).
+//
+// Short runs. The run-pair sum is Theorem 3's regrouping of the cell-level double sum
+// sum_j sum_k P(e_j) C_k g(k - j) over the virtual cells (eq. eqn_from_fsmi). When a ray's runs
+// are short (mean length below kCellRunLen) that cell-level form, a banded convolution of width
+// 2K + 1, costs less than the run pairs, so the ray is decompressed in shared memory and
+// evaluated that way -- the switch Section 5.4 recommends between the RLE algorithm and the
+// algorithm on the decompressed sequence. Both forms give the same value (pinned in the tests).
+#pragma once
+
+
+#include "../../include/fsmi.h"
+#include "fsmi_device.cuh"
+#include "fsmi_internal.h"
+
+namespace fsmi {
+
+// ---- noise-kernel prefix tables --------------------------------------------------------------
+
+// tab[i] = (Psi(m), Psi1(m)) for m = i - K - 1, i in [0, 2K + 1]; Psi(-K-1) = 0, Psi(K) = total.
+// kind: 0 Gaussian density (Theorem 3), 1 Gaussian cell mass, 2 box 1[|d| <= H] (Theorem 6).
+// band >= 0 zeroes |d| > band (strict-band reading of Approx-FSMI-RLE). The normalisation
+// (1/(sqrt(2 pi) sigma), 1 or 1/(2H+1)) is folded into g. Built in double, stored as float.
+static __device__ void build_table(float2 *tab, double *gs, float *gtab, int K, int kind, double sigma, int H, int band)
+{
+    for (int a = threadIdx.x; a <= K; a += blockDim.x) {  // g(|d|), d = a
+        double g;
+        if (kind == 2)
+            g = (a <= H) ? 1.0 / (2.0 * H + 1.0) : 0.0;
+        else if (kind == 1)
+            g = 0.5 * (erfc(-(a + 0.5) / (sigma * 1.4142135623730951)) - erfc(-(a - 0.5) / (sigma * 1.4142135623730951)));
+        else
+            g = exp(-(double)a * a / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
+        if (band >= 0 && a > band) g = 0.0;
+        gs[a] = g;
+        gtab[K + a] = (float)g;  // gtab[K + d] = g(d), d in [-K, K]
+        gtab[K - a] = (float)g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        tab[0] = make_float2(0.0f, 0.0f);
+        for (int d = -K; d <= K; ++d) {
+            const double g = gs[d < 0 ? -d : d];
+            s0 += g;
+            s1 += (double)d * g;
+            tab[d + K + 1] = make_float2((float)s0, (float)(d == K ? 0.0 : s1));
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float2 tab_at(const float2 *tab, int K, int m)
+{
+    return tab[min(max(m, -K - 1), K) + K + 1];
+}
+
+// A and B of one run pair (see the file comment).
+__device__ __forceinline__ void pair_AB(float x, int Lu, int Lv, int t, const float2 *tab, int K, float &A,
+                                        float &B)
+{
+    A = 0.0f;
+    B = 0.0f;
+    const int jlo = max(0, -K - t);
+    const int jhi = min(Lu - 1, Lv - 1 + K - t);
+    if (jlo > jhi) return;
+    float xp = ipowf(x, jlo);
+    for (int j = jlo; j <= jhi; ++j) {
+        const int m = j + t;
+        const float2 a = tab_at(tab, K, m);
+        const float2 b = tab_at(tab, K, m - Lv);
+        const float w0 = a.x - b.x;
+        const float w1 = fmaf((float)m, w0, -(a.y - b.y));
+        A = fmaf(xp, w0, A);
+        B = fmaf(xp, w1, B);
+        xp *= x;
+    }
+}
+
+// ---- per-ray run arrays in shared memory ----------------------------------------------------
+
+struct RunSmem {
+    float *O;  // o_u, then P_E(u) o_u
+    float *X;  // 1 - o_u
+    float *A;  // D_E(u) + f(delta_occ, r_u)
+    float *F;  // f(delta_emp, r_u)
+    int *S;    // s_u (first virtual cell of run u); S[nr] = n
+    int *L;    // L_u
+};
+
+__device__ __forceinline__ RunSmem run_smem(float *base, int stride)
+{
+    RunSmem r;
+    r.O = base;
+    r.X = base + stride;
+    r.A = base + 2 * stride;
+    r.F = base + 3 * stride;
+    r.S = (int *)(base + 4 * stride);
+    r.L = (int *)(base + 5 * stride);
+    return r;
+}
+
+// Run starts s_u = sum_{i<u} L_i (and S[nr] = n) from the lengths, or lengths from the starts.
+static __device__ void run_starts(const RunSmem &r, int nr, bool have_s)
+{
+    const int lane = lane_id();
+    const int K = (nr + 31) >> 5;
+    const int lo = min(nr, lane * K), hi = min(nr, lo + K);
+    if (!have_s) {
+        int cs = 0;
+        for (int u = lo; u < hi; ++u) cs += r.L[u];
+        const int ic = warp_incl_add_int(cs);
+        int s = __shfl_up_sync(kFull, ic, 1);
+        if (lane == 0) s = 0;
+        for (int u = lo; u < hi; ++u) {
+            r.S[u] = s;
+            s += r.L[u];
+        }
+        if (lane == 31) r.S[nr] = ic;
+    } else {
+        for (int u = lo; u < hi; ++u) r.L[u] = r.S[u + 1] - r.S[u];
+    }
+    __syncwarp();
+}
+
+// Run prefixes (Algorithms for P_E(u) and D_E(v)): P_E(u) = prod_{i<u} (1 - o_i)^{L_i},
+// D_E(u) = sum_{i<u} L_i f(delta_emp, r_i). On entry O, L and S are set.
+static __device__ void run_prefixes(const RunSmem &r, int nr, float docc, float demp)
+{
+    const int lane = lane_id();
+    const int K = (nr + 31) >> 5;
+    const int lo = min(nr, lane * K), hi = min(nr, lo + K);
+    float prod = 1.0f, sum = 0.0f;
+    for (int u = lo; u < hi; ++u) {
+        const float o = r.O[u];
+        const int L = r.L[u];
+        prod *= ipowf(1.0f - o, L);
+        sum = fmaf((float)L, cell_gain(demp, o), sum);
+    }
+    const float ip = warp_incl_mul(prod);
+    const float is = warp_incl_add(sum);
+    float E = __shfl_up_sync(kFull, ip, 1);
+    float D = __shfl_up_sync(kFull, is, 1);
+    if (lane == 0) {
+        E = 1.0f;
+        D = 0.0f;
+    }
+    for (int u = lo; u < hi; ++u) {
+        const float o = r.O[u];
+        const int L = r.L[u];
+        const float x = 1.0f - o;
+        const float fe = cell_gain(demp, o);
+        r.X[u] = x;
+        r.F[u] = fe;
+        r.A[u] = D + cell_gain(docc, o);
+        r.O[u] = E * o;
+        E *= ipowf(x, L);
+        D = fmaf((float)L, fe, D);
+    }
+    __syncwarp();
+}
+
+// Eq. (group_fsmi_rle_exact) over every run pair whose A, B can be non-zero (FSMI-RLE,
+// Uniform-FSMI-RLE, strict-band Approx-FSMI-RLE); returns this lane's partial sum.
+static __device__ float pairs_all(const RunSmem &r, int nr, const float2 *tab, int K)
+{
+    float tot = 0.0f;
+    for (int u = lane_id(); u < nr; u += 32) {
+        const float Pu = r.O[u];
+        if (Pu == 0.0f) continue;
+        const float x = r.X[u];
+        const int su = r.S[u], Lu = r.L[u];
+        float acc = 0.0f;
+        for (int v = 0; v < nr; ++v) {
+            const int t = su - r.S[v];
+            const int Lv = r.L[v];
+            if (t + Lu - 1 < -K || t > Lv - 1 + K) continue;
+            float A, B;
+            pair_AB(x, Lu, Lv, t, tab, K, A, B);
+            acc = fmaf(r.A[v], A, fmaf(r.F[v], B, acc));
+        }
+        tot = fmaf(Pu, acc, tot);
+    }
+    return tot;
+}
+
+// Theorem 5 as printed: the full diagonal block (theta, gamma) plus, for runs within Delta of
+// each other, the sub-blocks s', L' of eqs. (su')-(Lv') with shift t = s_u' - s_v', weighted by
+// (1 - o_u)^{s_u' - s_u} (u < v) or with D_E(v) + (s_v' - s_v) f(delta_emp, r_v) (u > v).
+static __device__ float pairs_thm5(const RunSmem &r, int nr, const float2 *tab, int K, int D)
+{
+    float tot = 0.0f;
+    for (int u = lane_id(); u < nr; u += 32) {
+        const float Pu = r.O[u];
+        if (Pu == 0.0f) continue;
+        const float x = r.X[u];
+        const int su = r.S[u], Lu = r.L[u];
+        float A, B;
+        pair_AB(x, Lu, Lu, 0, tab, K, A, B);
+        float acc = fmaf(r.A[u], A, r.F[u] * B);
+        for (int v = u + 1; v < nr; ++v) {
+            const int sv = r.S[v];
+            if (!(sv < su + Lu + D)) break;
+            const int Lv = r.L[v];
+            const int su2 = max(su, sv - D);
+            const int Lu2 = su + Lu - su2;
+            const int Lv2 = min(Lv, su + Lu + D - sv);
+            pair_AB(x, Lu2, Lv2, su2 - sv, tab, K, A, B);
+            acc = fmaf(ipowf(x, su2 - su), fmaf(r.A[v], A, r.F[v] * B), acc);
+        }
+        for (int v = u - 1; v >= 0; --v) {
+            const int sv = r.S[v], Lv = r.L[v];
+            if (!(su < sv + Lv + D)) break;
+            const int Lu2 = min(Lu, sv + Lv + D - su);
+            const int sv2 = max(sv, su - D);
+            const int Lv2 = sv + Lv - sv2;
+            pair_AB(x, Lu2, Lv2, su - sv2, tab, K, A, B);
+            acc = fmaf(fmaf((float)(sv2 - sv), r.F[v], r.A[v]), A, fmaf(r.F[v], B, acc));
+        }
+        tot = fmaf(Pu, acc, tot);
+    }
+    return tot;
+}
+
+constexpr int kArraysRLE = 7;                  // per-warp shared arrays (each `stride` floats)
+
+// run containing virtual cell i: the last u with S[u] <= i
+__device__ __forceinline__ int run_of(const int *S, int nr, int i)
+{
+    int lo = 0, len = nr;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (S[lo + half] <= i) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo - 1;
+}
+
+// Cell-level evaluation (eq. eqn_from_fsmi) of one ray: decompress the runs into the n virtual
+// cells, form P(e_j) and C_k by warp scans (Algorithms 2 and 3), then
+// I = sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d} (FSMI-RLE, Uniform-FSMI-RLE, strict-band
+// Approx-FSMI-RLE; Theorem 5's sub-blocks stay on the run-pair path, which is O(n_r Delta)).
+// Arrays: 0 run o, 1 run f_occ, 2 run f_emp, 3 P, 4 run starts S, 5 f_emp per cell,
+// 6 C padded by K zeros on both sides.
+static __device__ float ray_mi_cells(float *base, int stride, int nr, int n, const DevParams &p, const float *gtab, int K)
+{
+    const int lane = lane_id();
+    float *O = base, *RFO = base + stride, *RFE = base + 2 * stride, *CP = base + 3 * stride;
+    const int *S = (const int *)(base + 4 * stride);
+    float *CF = base + 5 * stride, *CC = base + 6 * stride;
+    for (int u = lane; u < nr; u += 32) {
+        const float o = O[u];
+        RFO[u] = cell_gain(p.docc, o);
+        RFE[u] = cell_gain(p.demp, o);
+    }
+    for (int i = lane; i < K; i += 32) {
+        CC[i] = 0.0f;
+        CC[K + n + i] = 0.0f;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const int u = run_of(S, nr, i);
+        CP[i] = O[u];
+        CC[K + i] = RFO[u];
+        CF[i] = RFE[u];
+    }
+    __syncwarp();
+    cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
+    float tot = 0.0f;
+    for (int j = lane; j < n; j += 32) {
+        float acc = 0.0f;
+        for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
+        tot = fmaf(CP[j], acc, tot);
+    }
+    return tot;
+}
+
+__device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const DevParams &p, const float2 *tab,
+                                        const float *gtab, int K, bool have_s)
+{
+    if (nr <= 0) return 0.0f;
+    const RunSmem r = run_smem(base, stride);
+    run_starts(r, nr, have_s);
+    const int n = r.S[nr];
+    const bool thm5 = p.variant == FSMI_APPROX && p.approx_reading == 0;
+    float v;
+    if (!thm5 && n < p.cell_runlen * nr) {
+        v = ray_mi_cells(base, stride, nr, n, p, gtab, K);
+    } else {
+        run_prefixes(r, nr, p.docc, p.demp);
+        if (p.variant == FSMI_APPROX && p.approx_reading == 0)
+            v = pairs_thm5(r, nr, tab, K, p.trunc);
+        else
+            v = pairs_all(r, nr, tab, K);
+    }
+    return warp_sum(v);
+}
+
+// ---- sampling and encoding -------------------------------------------------------------------
+
+// Virtual cells of ray `ray` (= pose * R + r): sample i is the voxel holding
+// o + (i + 1/2) d, i.e. floor of the Q31 position (o << 15) + (2i + 1) d, for i < nsamp until the
+// first sample outside the grid. Runs are maximal spans of bit-identical values split every `cap`
+// cells from the span's start. Writes O[u] = value, S[u] = first cell, S[nr] = n; returns nr.
+static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, int Y, int Z, const int32_t *pose,
+                                 const int32_t *u, int nsamp, int cap, float *O, int *S)
+{
+    const int lane = lane_id();
+    long long d[3], o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long acc = (long long)pose[3 + 3 * a] * u[0] + (long long)pose[4 + 3 * a] * u[1] +
+                              (long long)pose[5 + 3 * a] * u[2];
+        d[a] = (acc + (1LL << 29)) >> 30;
+        o[a] = (long long)pose[a] << 15;
+    }
+    int nrun = 0, carried = 0, n = 0;
+    unsigned prev_bits = 0u;
+    for (int base = 0; base < nsamp; base += 32) {
+        const int i = base + lane;
+        bool inb = false;
+        float val = 0.0f;
+        if (i < nsamp) {
+            const long long k = 2LL * i + 1;
+            const long long px = (o[0] + k * d[0]) >> 31;
+            const long long py = (o[1] + k * d[1]) >> 31;
+            const long long pz = (o[2] + k * d[2]) >> 31;
+            inb = px >= 0 && px < X && py >= 0 && py < Y && pz >= 0 && pz < Z;
+            if (inb) val = __ldg(vox + ((pz * Y + py) * X + px));
+        }
+        const unsigned m_in = __ballot_sync(kFull, inb);
+        const int nvalid = (m_in == kFull) ? 32 : (__ffs(~m_in) - 1);
+        const bool valid = lane < nvalid;
+        const unsigned bits = __float_as_uint(val);
+        unsigned pbits = __shfl_up_sync(kFull, bits, 1);
+        if (lane == 0) pbits = prev_bits;
+        const bool newval = valid && (i == 0 || bits != pbits);
+        int st = warp_incl_max_int(newval ? i : -1);
+        st = max(st, carried);
+        const bool brk = valid && ((i - st) % cap == 0);
+        const unsigned mb = __ballot_sync(kFull, brk);
+        if (brk) {
+            const int k = nrun + __popc(mb & ((1u << lane) - 1u));
+            O[k] = val;
+            S[k] = i;
+        }
+        nrun += __popc(mb);
+        n += nvalid;
+        if (nvalid < 32) break;
+        carried = __shfl_sync(kFull, st, 31);
+        prev_bits = __shfl_sync(kFull, bits, 31);
+    }
+    if (lane == 0) S[nrun] = n;
+    __syncwarp();
+    return nrun;
+}
+
+// ray = pose * R + r of a batch
+__device__ __forceinline__ int sample_encode(const Vox3D &v, long long ray, int nsamp, int cap, float *O, int *S)
+{
+    const int pi = (int)(ray / v.R), ri = (int)(ray % v.R);
+    return sample_encode_ray(v.vox, v.X, v.Y, v.Z, v.poses + 12 * (size_t)pi, v.dirs + 3 * (size_t)ri, nsamp, cap, O,
+                             S);
+}
+
+// ---- kernels -----------------------------------------------------------------------------------
+
+struct TabSpec {
+    int kind, H, band, K;
+    double sigma;
+};
+
+__host__ __device__ inline TabSpec table_spec(const DevParams &p)
+{
+    TabSpec t;
+    t.sigma = p.sigma;
+    t.H = p.H;
+    t.band = -1;
+    t.K = p.K;
+    if (p.variant == FSMI_UNIFORM) {
+        t.kind = 2;
+    } else {
+        t.kind = p.g_kernel == FSMI_G_ERF ? 1 : 0;
+        if (p.variant == FSMI_APPROX && p.approx_reading == 1) t.band = p.trunc;
+    }
+    return t;
+}
+
+// shared memory: [table float2 (2K+2)] [g scratch double (K+1)] [g float (2K+1)] [per-warp arrays]
+__host__ __device__ inline size_t rle_table_bytes(int K)
+{
+    return (((size_t)(2 * K + 2) * sizeof(float2) + (size_t)(K + 1) * sizeof(double) +
+             (size_t)(2 * K + 1) * sizeof(float)) + 15) & ~(size_t)15;
+}
+
+// Shared-memory layout of the RLE evaluation kernels: the block's kernel table, then each warp's
+// kArraysRLE arrays of `stride` floats.
+struct RleBlock {
+    TabSpec ts;
+    float2 *tab;
+    float *gtab;
+    float *base;
+};
+
+__device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const DevParams &p, int stride)
+{
+    RleBlock rb;
+    rb.ts = table_spec(p);
+    rb.tab = (float2 *)smem_raw;
+    double *gs = (double *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
+    rb.gtab = (float *)(gs + rb.ts.K + 1);
+    build_table(rb.tab, gs, rb.gtab, rb.ts.K, rb.ts.kind, rb.ts.sigma, rb.ts.H, rb.ts.band);
+    rb.base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * kArraysRLE * stride;
+    return rb;
+}
+
+// sampling, encoding and evaluation of one 3D ray (= pose * R + r)
+__device__ __forceinline__ void eval_ray_3d(const Vox3D &vx, const DevParams &p, const RleBlock &rb, int stride,
+                                            long long ray, float *__restrict__ out, int32_t *__restrict__ nruns)
+{
+    const RunSmem r = run_smem(rb.base, stride);
+    const int nr = sample_encode(vx, ray, p.nmax, p.run_cap, r.O, r.S);
+    const float I = ray_mi(rb.base, stride, nr, p, rb.tab, rb.gtab, rb.ts.K, true);
+    if (lane_id() == 0) {
+        out[ray] = I;
+        if (nruns) nruns[ray] = nr;
+    }
+    __syncwarp();
+}
+
+// evaluation of one run-length-encoded ray given in CSR form
+__device__ __forceinline__ void eval_ray_rle(const int32_t *__restrict__ off, const float *__restrict__ ro,
+                                             const uint8_t *__restrict__ rl, const DevParams &p, const RleBlock &rb,
+                                             int stride, long long ray, float *__restrict__ out, int *status)
+{
+    const int lane = lane_id();
+    const RunSmem r = run_smem(rb.base, stride);
+    const int b = off[ray];
+    const int nr = off[ray + 1] - b;
+    bool bad = nr < 0 || nr > p.nmax;
+    int cells = 0;
+    if (!bad) {
+        for (int u = lane; u < nr; u += 32) {
+            const int L = rl[b + u];
+            r.O[u] = __ldg(ro + b + u);
+            r.L[u] = L;
+            cells += L;
+            bad |= (L == 0);
+        }
+        cells = __reduce_add_sync(kFull, cells);
+        bad = __any_sync(kFull, bad) || cells > p.nmax;
+    }
+    __syncwarp();
+    if (bad) {
+        if (lane == 0) {
+            out[ray] = __int_as_float(0x7fc00000);
+            set_status(status, FSMI_STATUS_BAD_BEAM);
+        }
+        __syncwarp();
+        return;
+    }
+    const float I = ray_mi(rb.base, stride, nr, p, rb.tab, rb.gtab, rb.ts.K, false);
+    if (lane == 0) out[ray] = I;
+    __syncwarp();
+}
+
+}  // namespace fsmi

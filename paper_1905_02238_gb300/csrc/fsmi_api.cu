@@ -415,6 +415,41 @@ fsmi_status fsmi_gather_rows(const int32_t *src, long long nrows, int width, con
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
+fsmi_status fsmi_eval_mixed(const float *map, int W, int H, const int32_t *poses2, int P2, const int32_t *dirs2, int B2,
+                            const fsmi_params *prm2, const fsmi_volume *vols, int nvol, const int32_t *poses3, int P3,
+                            const int32_t *dirs3, int R3, const fsmi_params *prm3, const fsmi_set *sets, int nsets,
+                            long long nitems, float *out, unsigned long long *times, void *ws, size_t ws_bytes,
+                            fsmi_stream_t stream)
+{
+    DevParams d2, d3;
+    if (prm2) {
+        fsmi_status st = make_params(prm2, kUse2D, d2);
+        if (st != FSMI_OK) return st;
+        if (!grid_ok(W) || !grid_ok(H) || P2 < 0 || B2 < 0 || !map || (P2 > 0 && !poses2) || (B2 > 0 && !dirs2))
+            return FSMI_ERR_ARG;
+    }
+    if (prm3) {
+        fsmi_status st = make_params(prm3, kUseRLE, d3);
+        if (st != FSMI_OK) return st;
+        if (nvol < 0 || P3 < 0 || R3 < 0 || (nvol > 0 && !vols) || (P3 > 0 && !poses3) || (R3 > 0 && !dirs3))
+            return FSMI_ERR_ARG;
+    }
+    if (nsets < 0 || nitems < 0) return FSMI_ERR_ARG;
+    if (nitems == 0) return FSMI_OK;
+    if (nsets == 0 || !sets || !out || (!prm2 && !prm3)) return FSMI_ERR_ARG;
+    int *sp = status_ptr();
+    if (!sp) return cuda_fail(cudaGetLastError());
+    cudaStream_t s = (cudaStream_t)stream;
+    float4 *gains = prm2 ? gains_of(ws, ws_bytes, (long long)W * H, nitems, d2.nmax) : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (gains) e = map_gains(map, W, H, d2, gains, s);
+    if (e == cudaSuccess)
+        e = launch_eval_mixed(map, W, H, gains, poses2, P2, dirs2, B2, prm2 ? &d2 : nullptr, vols, nvol, poses3, P3,
+                              dirs3, R3, prm3 ? &d3 : nullptr, sets, nsets, nitems, out, times, sp,
+                              queue_of(FSMI_KIND_2D, ws, ws_bytes), s);
+    return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
 fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                             const fsmi_params *prm, float *out, void *ws, size_t ws_bytes, fsmi_stream_t stream)
 {
@@ -668,6 +703,7 @@ fsmi_status fsmi_prepare(void)
     if (e == cudaSuccess) e = prepare_rle();
     if (e == cudaSuccess) e = prepare_explore();
     if (e == cudaSuccess) e = prepare_surrogate();
+    if (e == cudaSuccess) e = prepare_mixed();
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 

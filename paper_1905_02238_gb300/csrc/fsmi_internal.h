@@ -59,6 +59,7 @@ cudaError_t launch_eval_2d_sets(const float *map, int W, int H, const int32_t *p
 cudaError_t launch_eval_2d_traj(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *traj_off,
                                 int T, const int32_t *stamp, const int32_t *dirs, int B, const DevParams &p, float *out,
                                 float4 *gains, unsigned long long *queue, int *status, cudaStream_t s);
+cudaError_t map_gains(const float *map, int W, int H, const DevParams &p, float4 *gains, cudaStream_t s);
 cudaError_t launch_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,
                               const DevParams &p, float *out, unsigned long long *queue, int *status, cudaStream_t s);
 cudaError_t launch_trace_2d(int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B, long long rfix,
@@ -106,6 +107,14 @@ cudaError_t launch_update_map_2d(float *map, int W, int H, const int32_t *poses,
                                  const float *ranges, long long rfix, int cap, float log_docc, float log_demp,
                                  uint32_t *counts, int *status, cudaStream_t s);
 cudaError_t prepare_explore();
+
+// mixed 2D / 3D candidate sets in one launch (fsmi_mixed.cu)
+cudaError_t launch_eval_mixed(const float *map, int W, int H, const float4 *gains, const int32_t *poses2, int P2,
+                              const int32_t *dirs2, int B2, const DevParams *p2, const fsmi_volume *vols, int nvol,
+                              const int32_t *poses3, int P3, const int32_t *dirs3, int R3, const DevParams *p3,
+                              const fsmi_set *sets, int nsets, long long nitems, float *out, unsigned long long *times,
+                              int *status, unsigned long long *queue, cudaStream_t s);
+cudaError_t prepare_mixed();
 
 // learned surrogate (fsmi_surrogate.cu)
 size_t surrogate_train_floats(int N);

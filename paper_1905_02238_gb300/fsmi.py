@@ -85,6 +85,11 @@ class Schedule:
         return Schedule(c.warps_per_block, c.blocks_per_sm, c.queue_chunk, c.cell_runlen)
 
 
+SET_2D, SET_3D = 0, 1
+# fsmi_set as 10 int32 words: kind, pose_offset, npose, dir_offset, ndir, max_range (float bits),
+# volume, reserved, out_offset (int64, low word first); fsmi_volume as 6: pointer (2), X, Y, Z, 0
+SET_WORDS, VOLUME_WORDS = 10, 6
+
 # fsmi_set_2d as 8 int32 words: pose_offset, npose, dir_offset, nbeam, max_range (float bits),
 # reserved, beam_offset (int64, little-endian low word first)
 SET_2D_WORDS = 8
@@ -157,6 +162,7 @@ def load():
             "fsmi_scan_sums": [p, ll, i, p, p],
             "fsmi_update_map_2d": [p, i, i, p, i, p, i, p, P, p, sz, p],
             "fsmi_profiles_2d": [p, i, i, p, i, p, i, p, ll, p, p],
+            "fsmi_eval_mixed": [p, i, i, p, i, p, i, P, p, i, p, i, p, i, P, p, i, ll, p, p, p, sz, p],
             "fsmi_surrogate_workspace_size": [i, ll, ctypes.POINTER(ctypes.c_size_t)],
             "fsmi_surrogate_loss_grad": [p, p, p, p, i, p, p, p, p, sz, p],
             "fsmi_surrogate_adam": [p, p, p, p, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i, p,
@@ -755,4 +761,68 @@ def gather_rows(src, idx, out=None) -> torch.Tensor:
         out = torch.empty((ii.numel(), w), dtype=torch.int32, device=s_.device)
     _raise(lib.fsmi_gather_rows(_ptr(s_), s_.shape[0], w, _ptr(ii), ii.numel(), _ptr(out), _stream()),
            "fsmi_gather_rows")
+    return out
+
+
+# ---- mixed 2D / 3D candidate sets -------------------------------------------------------------------
+
+def make_sets(sets, device=None):
+    """Packs [(kind, pose_offset, npose, dir_offset, ndir, max_range[, volume]), ...] into the fsmi_set
+    layout (int32 [nsets, 10]), outputs consecutive in list order. Returns (tensor, total items)."""
+    import struct
+    words, off = [], 0
+    for st in sets:
+        kind, po, npose, do, ndir, rng = st[:6]
+        vol = st[6] if len(st) > 6 else 0
+        fbits = struct.unpack("<i", struct.pack("<f", float(rng)))[0]
+        lo, hi = struct.unpack("<ii", struct.pack("<q", off))
+        words.append([int(kind), int(po), int(npose), int(do), int(ndir), fbits, int(vol), 0, lo, hi])
+        off += int(npose) * int(ndir)
+    t = torch.tensor(words, dtype=torch.int32).reshape(len(words), SET_WORDS)
+    return (t.to(device) if device is not None else t), off
+
+
+def make_volumes(volumes, device=None):
+    """fsmi_volume descriptors (int32 [nvol, 6]) of float32 CUDA tensors [Z][Y][X]."""
+    import struct
+    words = []
+    for v in volumes:
+        if not (v.is_cuda and v.dtype == torch.float32 and v.dim() == 3 and v.is_contiguous()):
+            raise TypeError("volumes must be contiguous float32 CUDA tensors [Z][Y][X]")
+        lo, hi = struct.unpack("<ii", struct.pack("<Q", v.data_ptr()))
+        Z, Y, X = v.shape
+        words.append([lo, hi, X, Y, Z, 0])
+    t = torch.tensor(words, dtype=torch.int32).reshape(len(words), VOLUME_WORDS)
+    return t.to(device) if device is not None else t
+
+
+def eval_mixed(sets, nitems: int, out=None, times=None, ws=None, grid=None, poses2=None, dirs2=None,
+               prm2: Params | None = None, volumes=None, poses3=None, dirs3=None, prm3: Params | None = None):
+    """fsmi_eval_mixed: 2D and 3D candidate sets (make_sets) in one persistent launch -> float32
+    [nitems]. volumes: int32 [nvol, 6] from make_volumes (the tensors must stay alive). times
+    (optional) uint64-as-int64 [nitems + 1] receives the block start and per-item completion times."""
+    lib = load()
+    st = _dev_tensor(sets, torch.int32, "sets")
+    dev = st.device
+    if out is None:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass a preallocated `out`")
+        out = torch.empty(nitems, dtype=torch.float32, device=dev)
+    if times is not None:
+        _dev_tensor(times, torch.int64, "times", nitems + 1)
+    if ws is None:
+        if _capturing():
+            raise FsmiError("inside a graph capture pass a preallocated workspace")
+        nb = workspace_size(FN_EVAL_2D, grid.numel()) if grid is not None else QUEUE_BYTES
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    wp, wb = _ws_args(ws)
+    c2 = prm2.c() if prm2 is not None else None
+    c3 = prm3.c() if prm3 is not None else None
+    g = grid
+    args2 = (_ptr(g), g.shape[1], g.shape[0], _ptr(poses2), poses2.shape[0], _ptr(dirs2), dirs2.shape[0],
+             ctypes.byref(c2)) if prm2 is not None else (None, 1, 1, None, 0, None, 0, None)
+    args3 = (_ptr(volumes), volumes.shape[0], _ptr(poses3), poses3.shape[0], _ptr(dirs3), dirs3.shape[0],
+             ctypes.byref(c3)) if prm3 is not None else (None, 0, None, 0, None, 0, None)
+    _raise(lib.fsmi_eval_mixed(*args2, *args3, _ptr(st), st.shape[0], nitems, _ptr(out), _ptr(times), wp, wb,
+                               _stream()), "fsmi_eval_mixed")
     return out
