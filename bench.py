@@ -320,6 +320,114 @@ def surrogate_leg(dev, steps: int = 2500):
     }
 
 
+def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512), len_range=(8, 512, 8, 256)):
+    """Config 5: a stream of candidate sets on a 4096x4096 office map and two 256x256x64 voxel
+    submaps, evaluated exactly (2D FSMI, sigma 2; 3D FSMI-RLE, sigma 2, run cap 64) in one
+    persistent launch (fsmi_eval_mixed), against the same sets launched one after the other.
+    Sets (default): 3 in 4 are 2D (16-8192 poses, log-uniform; 360 beams; range 8-512 cells), the
+    rest 3D (16-512 poses; 64x64 rays; 8-256 virtual cells); pose_range and len_range give other
+    streams. All sets are queued at time 0; a set's latency is the time until its last beam or ray
+    is done."""
+    import numpy as np
+    import torch
+
+    from paper_1905_02238_gb300 import fsmi, synth
+
+    rng = np.random.default_rng(seed)
+    grid = synth.office_grid(4096, n_obst=1600, seed=seed)
+    poses2 = synth.free_cell_poses_2d(grid, 16384, seed=seed + 1)
+    dirs2 = synth.beam_dirs_2d(360)
+    vols = [synth.voxel_world(256, 256, 64, n_boxes=60, seed=seed + 10 + k, noise_seed=seed + 20 + k) for k in range(2)]
+    poses3 = np.concatenate([synth.free_voxel_poses(v, 512, seed=seed + 30 + k, zlo=8, zhi=56)
+                             for k, v in enumerate(vols)])
+    dirs3 = synth.pinhole_dirs(64, 64, 90.0)
+    sets = []
+    for i in range(nsets):
+        if rng.random() < 0.75:
+            npose = int(np.exp(rng.uniform(np.log(pose_range[0]), np.log(pose_range[1]))))
+            po = int(rng.integers(0, poses2.shape[0] - npose + 1))
+            sets.append((fsmi.SET_2D, po, npose, 0, 360, float(rng.uniform(len_range[0], len_range[1]))))
+        else:
+            npose = int(np.exp(rng.uniform(np.log(pose_range[2]), np.log(pose_range[3]))))
+            k = int(rng.integers(0, 2))
+            sets.append((fsmi.SET_3D, 512 * k, npose, 0, 4096, float(rng.integers(len_range[2], len_range[3] + 1)), k))
+    g, p2, d2, p3, d3 = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (grid, poses2, dirs2, poses3, dirs3))
+    vt = [torch.from_numpy(v).to(dev) for v in vols]
+    vd = fsmi.make_volumes(vt, dev)
+    st, n = fsmi.make_sets(sets, dev)
+    prm2 = fsmi.Params(variant=fsmi.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=float(len_range[1]))
+    prm3 = fsmi.Params(variant=fsmi.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=float(len_range[3]),
+                       run_cap=64)
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    times = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=dev)
+
+    def mixed():
+        fsmi.eval_mixed(st, n, out=out, times=times, ws=ws, grid=g, poses2=p2, dirs2=d2, prm2=prm2, volumes=vd,
+                        poses3=p3, dirs3=d3, prm3=prm3)
+
+    # the same sets, one launch each, in order
+    seq_out = torch.empty(n, dtype=torch.float32, device=dev)
+    ws3 = torch.empty(fsmi.QUEUE_BYTES, dtype=torch.uint8, device=dev)
+    views, at = [], 0
+    for s_ in sets:
+        kind, po, npose, do, ndir, r = s_[:6]
+        views.append((s_, seq_out[at:at + npose * ndir].view(npose, ndir)))
+        at += npose * ndir
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(sets) + 1)]
+
+    def sequential(record=False):
+        if record:
+            ev[0].record()
+        for i, (s_, o) in enumerate(views):
+            kind, po, npose, do, ndir, r = s_[:6]
+            if npose:
+                if kind == fsmi.SET_2D:
+                    fsmi.eval_2d(g, p2[po:po + npose], d2[do:do + ndir], fsmi.Params(**{**prm2.__dict__, "max_range": r}),
+                                 out=o, ws=ws)
+                else:
+                    fsmi.eval_3d(vt[s_[6]], p3[po:po + npose], d3[do:do + ndir],
+                                 fsmi.Params(**{**prm3.__dict__, "max_range": r}), out=o, ws=ws3)
+            if record:
+                ev[i + 1].record()
+
+    mixed()
+    sequential()
+    torch.cuda.synchronize()
+    ok = bool(torch.equal(out, seq_out))
+    graph = fsmi.Graph(mixed)
+    ms_mixed = _time_ms(graph.replay, reps=3)
+    graph.replay()
+    torch.cuda.synchronize()
+    t = times.cpu().numpy().view(np.uint64).astype(np.float64)
+    lat, at = [], 0
+    for s_ in sets:
+        m = s_[2] * s_[4]
+        lat.append((t[1 + at:1 + at + m].max() - t[0]) * 1e-6 if m else 0.0)
+        at += m
+    ms_seq = _time_ms(sequential, reps=3)
+    sequential(record=True)
+    torch.cuda.synchronize()
+    lat_seq = [ev[0].elapsed_time(ev[i + 1]) for i in range(len(sets))]
+    graph.close()
+    poses = sum(s_[2] for s_ in sets)
+    n2 = sum(s_[2] * s_[4] for s_ in sets if s_[0] == fsmi.SET_2D)
+    return {
+        "workload": f"{nsets} candidate sets on a 4096x4096 office map ({sum(s_[0] == fsmi.SET_2D for s_ in sets)} 2D sets, "
+                    f"{pose_range[0]}-{pose_range[1]} poses x 360 beams, R {len_range[0]}-{len_range[1]}) and two "
+                    f"256x256x64 voxel submaps (3D sets, {pose_range[2]}-{pose_range[3]} poses x 64x64 rays, "
+                    f"{len_range[2]}-{len_range[3]} virtual cells); exact FSMI / FSMI-RLE; all sets queued at t = 0",
+        "items": n, "beams_2d": n2, "rays_3d": n - n2, "poses": poses,
+        "one_launch": {"ms": ms_mixed, "poses_per_s": poses / (ms_mixed * 1e-3), "items_per_s": n / (ms_mixed * 1e-3),
+                       "set_latency_ms_p50": float(np.percentile(lat, 50)),
+                       "set_latency_ms_p99": float(np.percentile(lat, 99))},
+        "launch_per_set": {"ms": ms_seq, "poses_per_s": poses / (ms_seq * 1e-3),
+                           "set_latency_ms_p50": float(np.percentile(lat_seq, 50)),
+                           "set_latency_ms_p99": float(np.percentile(lat_seq, 99))},
+        "identical_results": ok,
+    }
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -473,6 +581,10 @@ def run_fsmi(args):
             line["variants"] = other_variants(g, p, d, out)
             if not args.no_surrogate:
                 line["surrogate_rerank"] = surrogate_leg(dev)
+            if not args.no_mixed:
+                line["mixed_stream"] = mixed_leg(dev)
+                line["mixed_stream_small_sets"] = mixed_leg(dev, nsets=256, seed=6, pose_range=(16, 128, 4, 16),
+                                                            len_range=(8, 64, 8, 64))
             line["cpu_baseline"] = cpu_baseline(grid, poses, dirs)
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -488,6 +600,7 @@ def main():
     ap.add_argument("--impl", choices=["fsmi", "reference"], default="fsmi")
     ap.add_argument("--poses", type=int, default=N_POSES, help="poses per GPU (smaller for profiling cases)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg (profiling runs)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed candidate-set stream leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

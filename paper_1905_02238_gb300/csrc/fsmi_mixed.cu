@@ -56,8 +56,9 @@ struct MixedSrc {
     int nsets;
 };
 
+// 64 registers (4 blocks of 8 warps): the 2D path needs no more, and residency bounds this kernel
 template <int VAR>
-__global__ void __launch_bounds__(kMaxWarps * 32)
+__global__ void __launch_bounds__(kMaxWarps * 32, 4)
     k_eval_mixed(MixedSrc src, DevParams p2, DevParams p3, long long nitems, int stride2, int stride3, float *out,
                  unsigned long long *times, int *status, unsigned long long *queue, int chunk)
 {
