@@ -317,10 +317,17 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
 // o + (i + 1/2) d, i.e. floor of the Q31 position (o << 15) + (2i + 1) d, for i < nsamp until the
 // first sample outside the grid. Runs are maximal spans of bit-identical values split every `cap`
 // cells from the span's start. Writes O[u] = value, S[u] = first cell, S[nr] = n; returns nr.
+//
+// Fused form (CP != nullptr): also writes every virtual cell's o (CP), f(delta_occ, o) (CCk) and
+// f(delta_emp, o) (CF); the gains are evaluated once per run of equal values, by the lane where the
+// run starts, and passed to the run's other cells by shuffles. Runs past nrcap are counted but not
+// stored; *n_out receives n.
 static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, int Y, int Z, const int32_t *pose,
-                                 const int32_t *u, int nsamp, int cap, float *O, int *S)
+                                        const int32_t *u, int nsamp, int cap, float *O, int *S, int nrcap, int *n_out,
+                                        float *CP, float *CCk, float *CF, float docc, float demp)
 {
     const int lane = lane_id();
+    float carried_fo = 0.0f, carried_fe = 0.0f;
     long long d[3], o[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -356,8 +363,28 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         const unsigned mb = __ballot_sync(kFull, brk);
         if (brk) {
             const int k = nrun + __popc(mb & ((1u << lane) - 1u));
-            O[k] = val;
-            S[k] = i;
+            if (k < nrcap) {
+                O[k] = val;
+                S[k] = i;
+            }
+        }
+        if (CP) {
+            float fo = 0.0f, fe = 0.0f;
+            if (newval) {
+                fo = cell_gain(docc, val);
+                fe = cell_gain(demp, val);
+            }
+            const int src = st - base;  // lane where this cell's run of equal values starts, if in this chunk
+            const float so = __shfl_sync(kFull, fo, src >= 0 ? src : 0);
+            const float se = __shfl_sync(kFull, fe, src >= 0 ? src : 0);
+            const float go = src >= 0 ? so : carried_fo, ge = src >= 0 ? se : carried_fe;
+            if (valid) {
+                CP[i] = val;
+                CCk[i] = go;
+                CF[i] = ge;
+            }
+            carried_fo = __shfl_sync(kFull, go, 31);
+            carried_fe = __shfl_sync(kFull, ge, 31);
         }
         nrun += __popc(mb);
         n += nvalid;
@@ -365,9 +392,76 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         carried = __shfl_sync(kFull, st, 31);
         prev_bits = __shfl_sync(kFull, bits, 31);
     }
-    if (lane == 0) S[nrun] = n;
+    if (lane == 0 && nrun <= nrcap) S[nrun] = n;
+    if (n_out) *n_out = n;
     __syncwarp();
     return nrun;
+}
+
+static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, int Y, int Z, const int32_t *pose,
+                                        const int32_t *u, int nsamp, int cap, float *O, int *S)
+{
+    return sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, cap, O, S, nsamp + 1, nullptr, nullptr, nullptr, nullptr,
+                             0.0f, 0.0f);
+}
+
+// ---- the fused 3D ray (sampling and evaluation in one warp) --------------------------------------
+//
+// Per-warp layout: per-cell o / P (CP), f_emp (CF) and C padded by K zeros on both sides (CC), each
+// cell_stride floats (absent for Theorem 5's sub-blocks, which always use the runs), then the six
+// run arrays sized for the runs the run-pair path can see: a ray takes that path only when
+// n >= cell_runlen * n_r, so n_r <= nmax / cell_runlen.
+
+__host__ __device__ inline bool thm5_of(const DevParams &p) { return p.variant == FSMI_APPROX && p.approx_reading == 0; }
+__host__ __device__ inline int ray3d_cell_stride(const DevParams &p) { return ((p.nmax + 2 * p.K + 2) + 3) & ~3; }
+__host__ __device__ inline int ray3d_nrcap(const DevParams &p)
+{
+    const int T = p.cell_runlen > 0 ? p.cell_runlen : 1;
+    return thm5_of(p) ? p.nmax : min(p.nmax, p.nmax / T + 2);
+}
+__host__ __device__ inline int ray3d_run_stride(const DevParams &p) { return ((ray3d_nrcap(p) + 2) + 3) & ~3; }
+__host__ __device__ inline int ray3d_warp_floats(const DevParams &p)
+{
+    return (thm5_of(p) ? 0 : 3 * ray3d_cell_stride(p)) + 6 * ray3d_run_stride(p);
+}
+
+// Samples, encodes and evaluates one ray into the warp's region `w` (ray3d_warp_floats floats);
+// returns the MI (warp-reduced) and the run count in *nr_out.
+__device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, int Z, const int32_t *pose,
+                                              const int32_t *u, int nsamp, const DevParams &p, const float2 *tab,
+                                              const float *gtab, int K, float *w, int *nr_out)
+{
+    const int lane = lane_id();
+    const bool thm5 = thm5_of(p);
+    const int cst = ray3d_cell_stride(p);
+    float *CP = thm5 ? nullptr : w, *CF = w + cst, *CC = w + 2 * cst;
+    const RunSmem r = run_smem(w + (thm5 ? 0 : 3 * cst), ray3d_run_stride(p));
+    int n = 0;
+    const int nr = sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, p.run_cap, r.O, r.S, ray3d_nrcap(p), &n, CP,
+                                     CC + K, CF, p.docc, p.demp);
+    *nr_out = nr;
+    if (nr <= 0) return 0.0f;
+    float v;
+    if (!thm5 && n < p.cell_runlen * nr) {
+        // eq. eqn_from_fsmi on the virtual cells: Algorithms 2 and 3, then the banded convolution
+        for (int i = lane; i < K; i += 32) {
+            CC[i] = 0.0f;
+            CC[K + n + i] = 0.0f;
+        }
+        __syncwarp();
+        cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
+        v = 0.0f;
+        for (int j = lane; j < n; j += 32) {
+            float acc = 0.0f;
+            for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
+            v = fmaf(CP[j], acc, v);
+        }
+    } else {  // here n_r <= nrcap, so every run was stored
+        run_starts(r, nr, true);
+        run_prefixes(r, nr, p.docc, p.demp);
+        v = thm5 ? pairs_thm5(r, nr, tab, K, p.trunc) : pairs_all(r, nr, tab, K);
+    }
+    return warp_sum(v);
 }
 
 // ray = pose * R + r of a batch
@@ -417,7 +511,7 @@ struct RleBlock {
     float *base;
 };
 
-__device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const DevParams &p, int stride)
+__device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const DevParams &p, int warp_floats)
 {
     RleBlock rb;
     rb.ts = table_spec(p);
@@ -425,17 +519,18 @@ __device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const Dev
     double *gs = (double *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
     rb.gtab = (float *)(gs + rb.ts.K + 1);
     build_table(rb.tab, gs, rb.gtab, rb.ts.K, rb.ts.kind, rb.ts.sigma, rb.ts.H, rb.ts.band);
-    rb.base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * kArraysRLE * stride;
+    rb.base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * warp_floats;
     return rb;
 }
 
-// sampling, encoding and evaluation of one 3D ray (= pose * R + r)
-__device__ __forceinline__ void eval_ray_3d(const Vox3D &vx, const DevParams &p, const RleBlock &rb, int stride,
+// sampling, encoding and evaluation of one 3D ray (= pose * R + r), fused layout
+__device__ __forceinline__ void eval_ray_3d(const Vox3D &vx, const DevParams &p, const RleBlock &rb,
                                             long long ray, float *__restrict__ out, int32_t *__restrict__ nruns)
 {
-    const RunSmem r = run_smem(rb.base, stride);
-    const int nr = sample_encode(vx, ray, p.nmax, p.run_cap, r.O, r.S);
-    const float I = ray_mi(rb.base, stride, nr, p, rb.tab, rb.gtab, rb.ts.K, true);
+    const int pi = (int)(ray / vx.R), ri = (int)(ray % vx.R);
+    int nr = 0;
+    const float I = ray_mi_fused(vx.vox, vx.X, vx.Y, vx.Z, vx.poses + 12 * (size_t)pi, vx.dirs + 3 * (size_t)ri, p.nmax,
+                                 p, rb.tab, rb.gtab, rb.ts.K, rb.base, &nr);
     if (lane_id() == 0) {
         out[ray] = I;
         if (nruns) nruns[ray] = nr;

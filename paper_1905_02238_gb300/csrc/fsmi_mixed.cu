@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     double *gs = (double *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
     rb.gtab = (float *)(gs + rb.ts.K + 1);
     if (src.has3d) build_table(rb.tab, gs, rb.gtab, rb.ts.K, rb.ts.kind, rb.ts.sigma, rb.ts.H, rb.ts.band);
-    const int per_warp = max(kArrays2D * stride2, kArraysRLE * stride3);
+    const int per_warp = max(kArrays2D * stride2, ray3d_warp_floats(p3));
     float *base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * per_warp;
     rb.base = base;
     if (times && threadIdx.x == 0) atomicMin(times, global_ns());
@@ -101,10 +101,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
         } else if (ok && st.kind == FSMI_SET_3D && src.has3d && pi < src.P3 && di < src.R3 && st.volume >= 0 &&
                    st.volume < src.nvol && st.max_range >= 1.0f && st.max_range <= (float)p3.nmax) {
             const fsmi_volume v = src.vols[st.volume];
-            const RunSmem r = run_smem(base, stride3);
-            const int nr = sample_encode_ray(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di,
-                                             (int)st.max_range, p3.run_cap, r.O, r.S);
-            I = ray_mi(base, stride3, nr, p3, rb.tab, rb.gtab, rb.ts.K, true);
+            int nr = 0;
+            I = ray_mi_fused(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range, p3,
+                             rb.tab, rb.gtab, rb.ts.K, base, &nr);
         } else {
             bad = FSMI_STATUS_BAD_BEAM;  // a malformed descriptor is never used to index
         }
@@ -125,7 +124,7 @@ cudaError_t launch_mixed_variant(const MixedSrc &src, const DevParams &p2, const
     const Schedule &sc = current_schedule(FSMI_KIND_2D);
     const int stride2 = ((p2.nmax + 2) + 3) & ~3;
     const int stride3 = ((p3.nmax + 2 * p3.K + 4) + 3) & ~3;
-    const size_t per_warp = (size_t)max(kArrays2D * stride2, kArraysRLE * stride3) * sizeof(float);
+    const size_t per_warp = (size_t)max(kArrays2D * stride2, ray3d_warp_floats(p3)) * sizeof(float);
     const size_t table = rle_table_bytes(table_spec(p3).K);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, table);
     const size_t smem = table + (size_t)wpb * per_warp;

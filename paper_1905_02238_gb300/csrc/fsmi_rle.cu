@@ -6,12 +6,12 @@
 namespace fsmi {
 
 __global__ void __launch_bounds__(kMaxWarps * 32)
-    k_eval_3d(Vox3D vx, DevParams p, long long nrays, int stride, float *__restrict__ out, int32_t *__restrict__ nruns,
-              unsigned long long *queue, int chunk)
+    k_eval_3d(Vox3D vx, DevParams p, long long nrays, int warp_floats, float *__restrict__ out,
+              int32_t *__restrict__ nruns, unsigned long long *queue, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RleBlock rb = rle_block(smem_raw, p, stride);
-    for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d(vx, p, rb, stride, ray, out, nruns); });
+    const RleBlock rb = rle_block(smem_raw, p, warp_floats);
+    for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d(vx, p, rb, ray, out, nruns); });
 }
 
 __global__ void __launch_bounds__(kMaxWarps * 32)
@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
                unsigned long long *queue, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RleBlock rb = rle_block(smem_raw, p, stride);
+    const RleBlock rb = rle_block(smem_raw, p, kArraysRLE * stride);
     for_each_item(nrays, queue, chunk,
                   [&](long long ray) { eval_ray_rle(off, ro, rl, p, rb, stride, ray, out, status); });
 }
@@ -162,15 +162,15 @@ cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32
     const long long nrays = (long long)v.P * v.R;
     if (nrays <= 0) return cudaSuccess;
     const Schedule &sc = current_schedule(FSMI_KIND_RLE);
-    const int stride = rle_stride(p.nmax, p.K);
-    const size_t per_warp = (size_t)kArraysRLE * stride * sizeof(float);
+    const int wf = ray3d_warp_floats(p);
+    const size_t per_warp = (size_t)wf * sizeof(float);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, rle_table_bytes(p.K));
     const size_t smem = rle_table_bytes(p.K) + (size_t)wpb * per_warp;
     long long grid;
     cudaError_t e = grid_for(k_eval_3d, smem, nrays, wpb, sc.blocks_per_sm, grid);
     if (e == cudaSuccess) e = reset_queue(queue, s);
     if (e != cudaSuccess) return e;
-    k_eval_3d<<<(unsigned)grid, wpb * 32, smem, s>>>(v, p, nrays, stride, out, nruns, queue,
+    k_eval_3d<<<(unsigned)grid, wpb * 32, smem, s>>>(v, p, nrays, wf, out, nruns, queue,
                                                      sc.queue_chunk > 0 ? sc.queue_chunk : 1);
     return cudaGetLastError();
 }
