@@ -15,8 +15,12 @@
 // through one split-K SIMT GEMM whose operands are read through index functions (convolutions
 // gather their im2col entries on the fly); every sum is taken in a fixed order, so a training
 // step gives the same floats on every run.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched through the runtime, no -lcuda)
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <float.h>
+
+#include <mutex>
 
 #include "../../include/fsmi.h"
 #include "fsmi_device.cuh"
@@ -620,33 +624,28 @@ __global__ void __launch_bounds__(kConvWarps * 32)
     });
 }
 
-// Shared-memory layout of the fc operands: rows of 64 bf16 (128 B) with the 16-byte chunks
-// XOR-swizzled by row (the tensor cores' 128-byte swizzle when groups of 8 rows are 1024-B aligned).
-constexpr int kFcK = 64;
-
-__device__ __forceinline__ int swz(int row, int chunk) { return row * kFcK + ((chunk ^ (row & 7)) << 3); }
-
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, int bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes));
-}
-
 // ---- fc1 + ReLU + fc2 on the 5th-generation tensor cores (tcgen05, accumulators in TMEM) ------------
 //
-// One CTA of 4 warps per 128-row tile: D[128][256] = h0_tile[128][1024] W4^T accumulates in
-// 256 TMEM columns (FP32, row i in TMEM lane i). K runs in chunks of 64 through a 4-stage
-// cp.async pipeline; each stage holds A (128 x 64) and B (256 x 64) in the K-major layout with
-// the 128-byte swizzle (16-byte chunk c of row r at c ^ (r & 7), 8-row groups 1024 B apart,
-// 1024-byte aligned). One thread issues 4 MMAs (M = 128, N = 256, K = 16) per chunk and commits
-// them to the stage's mbarrier, which frees the stage for the chunk S - 1 ahead. The epilogue
-// reads each row's 256 accumulators (one row per thread) and forms b5 + sum_j W5[j] relu(D + b4).
-// Every wait is bounded: on timeout the kernel sets FSMI_STATUS_TIMEOUT, writes NaN and stops.
+// Persistent CTAs of 6 warps, one per SM, each taking 128-row tiles: D[128][256] = h0_tile[128][1024]
+// W4^T accumulates in 256 TMEM columns (FP32, row i in TMEM lane i), in one of two accumulators so
+// that a tile's epilogue overlaps the next tile's MMAs. K runs in chunks of 64 through a 4-stage
+// TMA pipeline; each stage holds A (128 x 64) and B (256 x 64) in the K-major layout with the
+// 128-byte swizzle (16-byte chunk c of row r at c ^ (r & 7), 8-row groups 1024 B apart, 1024-byte
+// aligned), written so by the tensor-map copies. Roles: warp 4 issues the copies (stage ring with
+// "full" / "empty" mbarriers), warp 5 issues 4 MMAs (M = 128, N = 256, K = 16) per chunk, commits
+// them to the stage's "empty" barrier and, after a tile's last chunk, to the accumulator's "tfull"
+// barrier; warps 0-3 read their 32 TMEM lanes each (one row per thread), release the accumulator
+// ("tempty") and form b5 + sum_j W5[j] relu(D + b4). Every wait is bounded: on timeout the kernel
+// sets FSMI_STATUS_TIMEOUT, writes NaN for the rows it could not finish and returns after its
+// copies and MMAs in flight have landed (again with bounded waits).
 
-constexpr int kTcRows = 128, kTcK = 64, kTcStages = 4, kTcThreads = 128;
+constexpr int kTcRows = 128, kTcK = 64, kTcStages = 4, kTcThreads = 192;
 constexpr int kTcStageBytes = (kTcRows + kHid) * kTcK * 2;  // 48 KB
 constexpr int kTcChunks = kFlat / kTcK;                      // 16
-constexpr unsigned kTcCols = 256;                            // TMEM columns (FP32 accumulators)
-constexpr size_t kTcSmem = 1024 + (size_t)kTcStages * kTcStageBytes + 8 * (kTcStages + 1) + 16;
+constexpr unsigned kTcAcc = 256;                             // TMEM columns per accumulator (FP32)
+constexpr unsigned kTcCols = 2 * kTcAcc;
+constexpr int kTcBars = 2 * kTcStages + 5;                   // full, empty, tfull[2], tempty[2], drain
+constexpr size_t kTcSmem = 1024 + (size_t)kTcStages * kTcStageBytes + 8 * kTcBars + kHid * 8 + 16;
 // instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1), B BF16
 // (bits 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28
 constexpr unsigned kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kHid >> 3) << 17) |
@@ -721,103 +720,164 @@ __device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+// TMA: a box of the 2D tensor map at (x = element along K, y = row) into shared memory, completing
+// `bytes` of the mbarrier's transaction count
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, int x, int y, unsigned mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ int flag_of(const int *flag) { return *(const volatile int *)flag; }
+
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_fc_tc(const bf16 *__restrict__ h0, long long N, const bf16 *__restrict__ w, const float *__restrict__ params,
-            float *__restrict__ pred, int *status)
+    k_fc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, long long N,
+            const bf16 *__restrict__ w, const float *__restrict__ params, float *__restrict__ pred, int *status)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned long long *mbar = (unsigned long long *)(base + (size_t)kTcStages * kTcStageBytes);
-    unsigned *tmem_slot = (unsigned *)(mbar + kTcStages + 1);
+    unsigned long long *full = (unsigned long long *)(base + (size_t)kTcStages * kTcStageBytes);
+    unsigned long long *empty = full + kTcStages;
+    unsigned long long *tfull = empty + kTcStages;
+    unsigned long long *tempty = tfull + 2;
+    unsigned long long *drain = tempty + 2;
+    float2 *bw = (float2 *)(drain + 1);  // (b4[j], W5[j])
+    unsigned *tmem_slot = (unsigned *)(bw + kHid);
+    __shared__ int flag;  // 0 while every wait succeeded
     const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
-    const bf16 *W4 = w + oW4;
-    if (warp == 0) {
+    if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTcCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < kTcStages; ++i) mbar_init(smem_u32(mbar + i), 1);
+        for (int i = 0; i < kTcStages; ++i) {
+            mbar_init(smem_u32(full + i), 1);
+            mbar_init(smem_u32(empty + i), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(tfull + i), 1);
+            mbar_init(smem_u32(tempty + i), 4);  // lane 0 of each epilogue warp
+        }
+        mbar_init(smem_u32(drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        flag = 0;
     }
+    if (tid == 4 * 32) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmB)) : "memory");
+    }
+    for (int j = tid; j < kHid; j += kTcThreads) bw[j] = make_float2(params[oB4 + j], bf(w, oW5 + j));
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = *tmem_slot;
-    unsigned phase = 0u;        // bit s: parity of stage s's next completion
-    unsigned pending = 0u;      // bit s: a commit on stage s not yet waited for
-    bool ok = true;
-
-    auto load = [&](int stage, int kc, long long r0) {
-        bf16 *sa = (bf16 *)(base + (size_t)stage * kTcStageBytes), *sbm = sa + kTcRows * kTcK;
-        for (int e = tid; e < (kTcRows + kHid) * 8; e += kTcThreads) {
-            const int row = e >> 3, ch = e & 7;
-            if (row < kTcRows) {
-                const long long gr = r0 + row;
-                const bool in = gr < N;
-                cp_async16(smem_u32(sa + swz(row, ch)), h0 + (in ? gr : 0) * kFlat + kc * kTcK + ch * 8, in ? 16 : 0);
-            } else {
-                const int j = row - kTcRows;
-                cp_async16(smem_u32(sbm + swz(j, ch)), W4 + (long long)j * kFlat + kc * kTcK + ch * 8, 16);
-            }
+    const long long tiles = (N + kTcRows - 1) / kTcRows;
+    if (warp == 4) {
+        if (lane == 0) {  // TMA producer
+            long long it = 0;  // chunks issued by this CTA; stage it % S, its use number it / S
+            bool ok = true;
+            for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x)
+                for (int kc = 0; kc < kTcChunks; ++kc) {
+                    const int st = (int)(it % kTcStages);
+                    const long long u = it / kTcStages;
+                    if (u > 0 && !mbar_wait(smem_u32(empty + st), (unsigned)((u - 1) & 1))) ok = false;
+                    if (!ok || flag_of(&flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned a0 = smem_u32(base + (size_t)st * kTcStageBytes);
+                    mbar_expect_tx(smem_u32(full + st), (unsigned)kTcStageBytes);
+                    tma_load_2d(a0, &tmA, kc * kTcK, (int)(t * kTcRows), smem_u32(full + st));
+                    tma_load_2d(a0 + kTcRows * kTcK * 2, &tmB, kc * kTcK, 0, smem_u32(full + st));
+                    ++it;
+                }
+            // copies in flight: the last fill of every stage has landed
+            for (long long j = it - 1; j >= 0 && j >= it - kTcStages; --j)
+                if (!mbar_wait(smem_u32(full + (int)(j % kTcStages)), (unsigned)((j / kTcStages) & 1))) ok = false;
+            if (!ok) atomicOr(&flag, 1);
         }
-    };
-    auto wait_stage = [&](int stage) {
-        if (pending & (1u << stage)) {
-            ok = ok && mbar_wait(smem_u32(mbar + stage), (phase >> stage) & 1u);
-            phase ^= 1u << stage;
-            pending &= ~(1u << stage);
-        }
-    };
-
-    for (long long r0 = (long long)blockIdx.x * kTcRows; r0 < N && ok; r0 += (long long)gridDim.x * kTcRows) {
-        for (int c = 0; c < kTcStages - 1; ++c) {
-            load(c, c, r0);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        }
-        for (int kc = 0; kc < kTcChunks; ++kc) {
-            asm volatile("cp.async.wait_group %0;" ::"n"(kTcStages - 2) : "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            const int stage = kc % kTcStages;
-            if (tid == 0) {
+    } else if (warp == 5) {
+        if (lane == 0) {  // MMA issuer
+            long long it = 0;
+            int tl = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+                const int b = tl & 1, v = tl >> 1;
+                if (v > 0 && !mbar_wait(smem_u32(tempty + b), (unsigned)((v - 1) & 1))) ok = false;
+                if (!ok || flag_of(&flag)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
-                const unsigned a0 = smem_u32(base + (size_t)stage * kTcStageBytes);
-                const unsigned b0 = a0 + kTcRows * kTcK * 2;
+                const unsigned d = tmem + (unsigned)b * kTcAcc;
+                for (int kc = 0; kc < kTcChunks; ++kc, ++it) {
+                    const int st = (int)(it % kTcStages);
+                    if (!mbar_wait(smem_u32(full + st), (unsigned)((it / kTcStages) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned a0 = smem_u32(base + (size_t)st * kTcStageBytes), b0 = a0 + kTcRows * kTcK * 2;
 #pragma unroll
-                for (int k = 0; k < kTcK / 16; ++k)  // K = 16 per MMA: 32 bytes along the swizzled row
-                    tc_mma(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), kTcIdesc, (kc | k) != 0);
-                tc_commit(smem_u32(mbar + stage));
+                    for (int k = 0; k < kTcK / 16; ++k)  // K = 16 per MMA: 32 bytes along the swizzled row
+                        tc_mma(d, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), kTcIdesc, (kc | k) != 0);
+                    tc_commit(smem_u32(empty + st));
+                }
+                if (ok) tc_commit(smem_u32(tfull + b));
             }
-            pending |= 1u << stage;
-            const int next = kc + kTcStages - 1;  // its stage held chunk kc - 1
-            if (next < kTcChunks) {
-                wait_stage(next % kTcStages);
-                load(next % kTcStages, next, r0);
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (!ok) atomicOr(&flag, 1);
+            tc_commit(smem_u32(drain));  // every MMA issued has completed once this arrives
+            if (!mbar_wait(smem_u32(drain), 0u)) atomicOr(&flag, 1);
         }
-        for (int st = 0; st < kTcStages; ++st) wait_stage(st);  // every MMA of the tile is done
-        ok = __syncthreads_and(ok);
-        tc_fence_after();
-        // epilogue: thread (warp w, lane l) owns row 32 w + l = TMEM lane 32 w + l
-        const long long row = r0 + warp * 32 + lane;
-        float acc = 0.0f;
-        for (int c0 = 0; c0 < kHid; c0 += 32) {
-            float v[32];
-            tc_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+    } else {  // epilogue: warp w holds TMEM lanes 32w .. 32w + 31, one row per thread
+        int tl = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+            const int b = tl & 1, v = tl >> 1;
+            const long long row = t * kTcRows + warp * 32 + lane;
+            float acc = 0.0f;
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(tfull + b), (unsigned)(v & 1)));
+            if (ok) {
+                tc_fence_after();
+                const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)b * kTcAcc;
+                for (int c0 = 0; c0 < kHid; c0 += 32) {
+                    float x[32];
+                    tc_ld32(ta + (unsigned)c0, x);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc = fmaf(relu(v[j] + params[oB4 + c0 + j]), bf(w, oW5 + c0 + j), acc);
+                    for (int j = 0; j < 32; ++j) {
+                        const float2 q = bw[c0 + j];
+                        acc = fmaf(relu(x[j] + q.x), q.y, acc);
+                    }
+                }
+                tc_fence_before();
+            } else if (lane == 0) {
+                atomicOr(&flag, 1);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(tempty + b));
+            if (row < N) pred[row] = ok ? params[oB5] + acc : __int_as_float(0x7fc00000);
         }
-        if (row < N) pred[row] = ok ? params[oB5] + acc : __int_as_float(0x7fc00000);
-        tc_fence_before();
-        __syncthreads();
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (!ok && tid == 0) set_status(status, FSMI_STATUS_TIMEOUT);
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+    if (tid == 0 && flag != 0) set_status(status, FSMI_STATUS_TIMEOUT);
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
 }
 
 // ---- selection -------------------------------------------------------------------------------------
@@ -990,6 +1050,43 @@ namespace fsmi {
 
 size_t surrogate_infer_bytes(long long N) { return kQueueBytes + (size_t)N * kFlat * sizeof(bf16); }
 
+namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (looked up once)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// Row-major BF16 matrix [rows][cols] (16-byte aligned, rows of cols * 2 bytes) as a 2D tensor map
+// with boxes of box_cols x box_rows and the 128-byte swizzle; out-of-range rows read as zero.
+cudaError_t encode_bf16_2d(CUtensorMap *map, const void *ptr, unsigned long long cols, unsigned long long rows,
+                           unsigned box_cols, unsigned box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
 cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t *poses, const int32_t *dirs, int B,
                                    const void *x, long long N, const void *wbf16, const float *params, float *pred,
                                    void *ws, int *status, cudaStream_t s)
@@ -1014,10 +1111,14 @@ cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long tiles = (N + kTcRows - 1) / kTcRows;
+    CUtensorMap tmA, tmB;
+    e = encode_bf16_2d(&tmA, h0, kFlat, (unsigned long long)N, kTcK, kTcRows);
+    if (e == cudaSuccess) e = encode_bf16_2d(&tmB, w + oW4, kFlat, kHid, kTcK, kHid);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_fc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
     k_fc_tc<<<(unsigned)(tiles < (long long)sm_count() ? tiles : sm_count()), kTcThreads, kTcSmem, s>>>(
-        h0, N, w, params, pred, status);
+        tmA, tmB, N, w, params, pred, status);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,11 @@ def test_tensor_core_inference_matches_oracle():
     # profiles sampled inside the kernel give the same floats
     got_map = fsmi.surrogate_predict(params, wb, grid=_cuda(grid), poses=_cuda(poses), dirs=_cuda(dirs))
     np.testing.assert_array_equal(got_map.cpu().numpy(), got.astype(np.float32))
+    # many row tiles per persistent block and a ragged last tile: every row equals its own value
+    # from the small launch (rows are independent and each row's sums run in a fixed order)
+    idx = np.random.default_rng(11).integers(0, x.shape[0], 152 * 128 * 3 + 77)
+    big = fsmi.surrogate_predict(params, wb, x=x[torch.from_numpy(idx).cuda()]).cpu().numpy()
+    np.testing.assert_array_equal(big, got.astype(np.float32)[idx])
 
 
 def test_topk_and_gather():
