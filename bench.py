@@ -39,7 +39,7 @@ SFU_PER_SM_CLK = 32  # SFU (ex2, rcp) results per SM per clock, measured by a th
 OPS_PER_TERM = 12  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh):
 #                    distance, square, 1 + p|d|, 6 Horner FMAs, two products, accumulate;
 #                    plus 2 SFU operations (ex2, rcp), for which the SFU has room to spare
-TAIL_CUT = 11.3  # scaled distance beyond which the tail term is exactly zero in FP32 (fsmi_2d.cu)
+TAIL_CUT = 5.75  # scaled half-width of the exact kernel's default window (csrc/eval2d.cuh)
 
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
 # ncu capture (profiles/k_eval_2d_exact_office2048.md), valid only for the kernel sources whose
@@ -148,7 +148,7 @@ def workload(rank: int, n_poses: int = N_POSES):
     return grid, poses, dirs
 
 
-def cpu_baseline(grid, poses, dirs, n_pose_sample: int = 24):
+def cpu_baseline(grid, poses, dirs, n_pose_sample: int = 288):
     """The FP64 oracle as it stands, on all host cores, on the first n_pose_sample poses."""
     import oracle
 
@@ -219,6 +219,7 @@ def other_variants(g, p, d, out):  # noqa: C901
     nb = p.shape[0] * d.shape[0]
     gains_ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=g.device)
     for name, kw in (("exact_fsmi_full_sweep", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP)),
+                     ("exact_fsmi_full_window", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_WINDOW)),
                      ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
                      ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4))):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)

@@ -85,11 +85,16 @@ typedef struct {
     int flags;          /* FSMI_FLAG_* bits, 0 by default */
 } fsmi_params;
 
-/* Exact 2D FSMI normally evaluates, for each first-hit cell, only the boundary terms whose
- * Gaussian tail is non-zero in FP32 (the tail underflows to exactly 0 beyond about 26 sigma/2),
- * which gives the same result bit for bit as evaluating all n(n+1) terms of Theorem 1. This flag
- * forces the full sweep (for verification and timing comparisons). */
+/* Exact 2D FSMI evaluates, for each first-hit cell j, the boundary terms of Theorem 1's pair sum
+ * within about 6.8 sigma of the cell's centre: every term beyond weighs less than 2^-37 of its
+ * factor |C_m - C_{m-1}|, so the MI differs from the full n(n+1) sweep by far less than FP32
+ * resolution (but not bit for bit).
+ * FSMI_FLAG_FULL_WINDOW widens the window to every term whose Gaussian tail is non-zero in FP32
+ * (about 13.3 sigma; the tail underflows to exactly 0 beyond), which gives the full sweep's result
+ * bit for bit; FSMI_FLAG_FULL_SWEEP evaluates all n(n+1) terms (both for verification and timing
+ * comparisons). */
 #define FSMI_FLAG_FULL_SWEEP 0x1
+#define FSMI_FLAG_FULL_WINDOW 0x2
 
 /*
  * Launch schedule of the evaluation kernels, one per kernel family:

@@ -60,13 +60,15 @@ struct Src2D {
 
 // One register-blocked pass of the exact pair sum over scaled distances: each lane owns J
 // first-hit slots j = jb + lane + 32 t and streams every boundary m = 0..n from shared memory.
-// Slot n is the no-return event when e0 is set (centre mu0, C_0 = 0).
+// Slot n is the no-return event when e0 is set (centre mu0, C_0 = 0). Terms of even and odd m
+// accumulate separately, each in increasing m, and are added at the end (the order the window
+// sum uses, so that the two agree bit for bit).
 template <int J>
 __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, const float *sp, int n, int jb,
                                             bool e0, float pe0, float mu0)
 {
     const int lane = lane_id();
-    float mu[J], acc[J];
+    float mu[J], acc[J], acc1[J];
     int mid[J];  // boundaries m < mid lie before the centre
 #pragma unroll
     for (int t = 0; t < J; ++t) {
@@ -74,6 +76,7 @@ __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, co
         mu[t] = (j < n) ? 0.5f * (sl[j] + sl[j + 1]) : ((j == n && e0) ? mu0 : 3.0e30f);
         mid[t] = (j < n) ? j + 1 : 0;
         acc[t] = 0.0f;
+        acc1[t] = 0.0f;
     }
     float cprev = 0.0f;
     for (int m = 0; m <= n; ++m) {
@@ -81,17 +84,23 @@ __device__ __forceinline__ float exact_pass(const float *sl, const float *sc, co
         const float cm = sc[m];  // sc[n] = 0 (C_{n+1})
         const float dc = cm - cprev;
         cprev = cm;
+        if (m & 1) {
 #pragma unroll
-        for (int t = 0; t < J; ++t) acc[t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc[t]);
+            for (int t = 0; t < J; ++t) acc1[t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc1[t]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < J; ++t) acc[t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc[t]);
+        }
     }
     float r = 0.0f;
 #pragma unroll
     for (int t = 0; t < J; ++t) {
         const int j = jb + lane + 32 * t;
+        const float a = acc[t] + acc1[t];
         if (j < n)
-            r = fmaf(sp[j], sc[j] + acc[t], r);
+            r = fmaf(sp[j], sc[j] + a, r);
         else if (j == n && e0)
-            r = fmaf(pe0, acc[t], r);
+            r = fmaf(pe0, a, r);
     }
     return r;
 }
@@ -119,6 +128,11 @@ __device__ __forceinline__ float exact_sum(const float *sl, const float *sc, con
 // Largest scaled distance whose tail is not flushed to zero: beyond |d| = 11.3 the factor
 // 2^(-d^2) <= 2^(-127.69) is subnormal and ex2.approx.ftz returns exactly 0, so the term is +-0.
 constexpr float kTailCut = 11.3f;
+// Default window of the exact sum: T(5.75) = 6.4e-12 < 2^-37. Boundaries come at most two per
+// major-axis crossing interval (scaled length >= cs = sqrt(log2 e) / (sigma sqrt 2)), so the terms
+// skipped on one side weigh at most 2 T(5.75) / (1 - 2^(-11.5 cs)) times max |C_m - C_{m-1}|:
+// below 2^-34 of it for sigma <= 20 cells, far under the FP32 rounding of the sums.
+constexpr float kTailCutDefault = 5.75f;
 
 __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
 {
@@ -135,48 +149,72 @@ __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
     return lo;
 }
 
-// Boundary terms m in [a, b) of one first-hit cell, added in increasing m to acc: on the lower
-// side (NEG, boundaries before the centre) the term is -dC_m T(mu - l_m), above it +dC_m T(l_m - mu).
-// Aligned pairs of boundaries go through the packed tail; results equal the scalar path bit for bit.
+// The same index (first g in [0, N] with a[g] >= x, a ascending, N >= 2, a[N] readable and
+// >= x) when it lies in [g0, g0 + 3]: three independent loads count the entries below x from g0;
+// two checks confirm the range, else bisection decides. Along a traversed beam boundaries are
+// nearly evenly spaced, so a guess from the mean spacing lands in that range.
+__device__ __forceinline__ int lower_bound_from(const float *a, int N, float x, int g0)
+{
+    g0 = min(max(g0, 0), N - 2);
+    const int c = (a[g0] < x ? 1 : 0) + (a[g0 + 1] < x ? 1 : 0) + (a[g0 + 2] < x ? 1 : 0);
+    const int g = g0 + c;
+    if ((c == 3 && a[g] < x) || (g0 > 0 && a[g0 - 1] >= x)) return lower_bound_f(a, N, x);
+    return g;
+}
+
+// Boundary terms m in [lo, hi) of one first-hit cell with centre mu, the range widened to even
+// bounds so that every term goes through the packed tail (a term added that way lies outside the
+// window: zero in FP32 or below the window's cut; index n + 1 is padding with l = 3e30, dC = 0).
+// A boundary m < mid lies before the centre: -dC_m T(mu - l_m); above it +dC_m T(l_m - mu).
+// Returns the packed sums over even and odd m, each added in increasing m.
 #ifndef FSMI_PAIR_UNROLL
 #define FSMI_PAIR_UNROLL 4
 #endif
 constexpr int kPairUnroll = FSMI_PAIR_UNROLL;  // boundary pairs in flight per lane, exact window loop
 
-template <bool NEG>
-__device__ __forceinline__ float side_terms(const float *sl, const float *sdc, int a, int b, float mu, float acc)
+__device__ __forceinline__ f32x2 window_terms(const float *sl, const float *sdc, int lo, int hi, int mid, float mu)
 {
-    int m = a;
-    if (m < b && (m & 1)) {
-        const float d = NEG ? mu - sl[m] : sl[m] - mu;
-        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(d), acc);
-        ++m;
-    }
+    int m = lo & ~1;
+    const int end = (hi + 1) & ~1;
     const f32x2 mu2 = pack2(mu, mu);
+    f32x2 acc = pack2(0.0f, 0.0f);
+    const int nb = min(max(mid & ~1, m), end);  // pairs (m, m + 1) with m + 1 < mid
 #pragma unroll kPairUnroll
-    for (; m + 1 < b; m += 2) {
+    for (; m < nb; m += 2) {
         const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
-        const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
-        float T0, T1;
-        gauss_tail2(NEG ? sub2(mu2, L) : sub2(L, mu2), T0, T1);
-        acc = fmaf(NEG ? -dc.x : dc.x, T0, acc);
-        acc = fmaf(NEG ? -dc.y : dc.y, T1, acc);
+        const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
+        acc = fma2(dc, gauss_tail2p<true>(sub2(mu2, L)), acc);
     }
-    if (m < b) {
-        const float d = NEG ? mu - sl[m] : sl[m] - mu;
-        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(d), acc);
+    if (m < end && m == mid - 1) {  // the pair around the centre: m below, m + 1 above
+        const float2 L = *reinterpret_cast<const float2 *>(sl + m);
+        const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
+        acc = fma2(pack2(-dc.x, dc.y), gauss_tail2p<false>(pack2(mu - L.x, L.y - mu)), acc);
+        m += 2;
+    }
+#pragma unroll kPairUnroll
+    for (; m < end; m += 2) {
+        const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
+        const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
+        acc = fma2(dc, gauss_tail2p<false>(sub2(L, mu2)), acc);
     }
     return acc;
 }
 
-// Exact pair sum over the boundaries whose tail term can be non-zero: for slot j only
-// m with |l_m - mu_j| < kTailCut (scaled) are visited, in increasing m, so every non-zero term
-// of the full sweep is added in the same order and the FP32 result is the same bit for bit.
+// Exact pair sum over the boundaries within the window: for slot j only m with
+// |l_m - mu_j| < cut (scaled) are visited, in increasing m. With cut = kTailCut every non-zero
+// term of the full sweep is added in the same order and the FP32 result is the same bit for bit;
+// with kTailCutDefault the terms skipped are below 2^-37 of their weights.
 // sdc[m] = C_m - C_{m-1} for m = 0..n.
 __device__ __forceinline__ float exact_window_sum(const float *sl, const float *sdc, const float *sc,
-                                                  const float *sp, int n, bool e0, float pe0, float mu0)
+                                                  const float *sp, int n, bool e0, float pe0, float mu0, float cut)
 {
     const int nslots = n + (e0 ? 1 : 0);
+    // search guesses: the window of slot j reaches about `half` boundaries to either side of
+    // boundary j + 1 (boundaries per unit of scaled distance from the beam's mean spacing); the
+    // guesses err by -1 .. +2 (lower end) and -2 .. +1 (upper end) along traversed beams
+    const float span = sl[n] - sl[0];
+    const float per = span > 0.0f ? (float)n / span : 0.0f;
+    const int half = (int)fminf(cut * per, (float)(n + 1));
     float r = 0.0f;
     for (int j = lane_id(); j < nslots; j += 32) {
         float mu, Cj, Pj;
@@ -192,11 +230,13 @@ __device__ __forceinline__ float exact_window_sum(const float *sl, const float *
             Pj = pe0;
             mid = 0;
         }
-        const int lo = lower_bound_f(sl, n + 1, mu - kTailCut);
-        const int hi = lower_bound_f(sl, n + 1, mu + kTailCut);
-        float acc = side_terms<true>(sl, sdc, lo, min(max(mid, lo), hi), mu, 0.0f);
-        acc = side_terms<false>(sl, sdc, max(mid, lo), hi, mu, acc);
-        r = fmaf(Pj, Cj + acc, r);
+        const int anchor = mid;  // j + 1, or 0 for the no-return slot (centre before l_0)
+        // sl[n + 1] is the padding boundary (3e30), above every target
+        const int lo = lower_bound_from(sl, n + 1, mu - cut, anchor - half - 2);
+        const int hi = lower_bound_from(sl, n + 1, mu + cut, anchor + half - 1);
+        float a0, a1;
+        unpack2(window_terms(sl, sdc, lo, hi, mid, mu), a0, a1);
+        r = fmaf(Pj, Cj + (a0 + a1), r);
     }
     return r;
 }
@@ -256,7 +296,7 @@ __device__ __forceinline__ float uniform_sum(const float *sd, const float *sp, i
 }
 
 #ifndef FSMI_MIN_BLOCKS_2D
-#define FSMI_MIN_BLOCKS_2D 1  // minimum resident blocks per SM requested from the register allocator
+#define FSMI_MIN_BLOCKS_2D 4  // resident 8-warp blocks per SM requested from the register allocator (64 registers)
 #endif
 
 // the candidate set holding flat beam index `beam` (sets sorted by beam_offset)
@@ -355,8 +395,13 @@ __device__ __forceinline__ float beam_sum(const DevParams &p, int n, float *sl, 
         if (VAR == kExactFullSweep) I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
         if (VAR == FSMI_EXACT) {
             for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
+            if (lane == 0) {  // padding boundary n + 1 for the even-aligned window pairs
+                sl[n + 1] = 3.0e30f;
+                sx[n + 1] = 0.0f;
+            }
             __syncwarp();
-            I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0);
+            I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0,
+                                 (p.flags & FSMI_FLAG_FULL_WINDOW) ? kTailCut : kTailCutDefault);
         }
         if (VAR == FSMI_APPROX) I = approx_sum(sl, sc, sp, n, e0, pe0, mu0, p.trunc);
         if (VAR == FSMI_UNIFORM) I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);

@@ -76,7 +76,7 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     if (prm->g_kernel != FSMI_G_PDF && prm->g_kernel != FSMI_G_ERF) return FSMI_ERR_ARG;
     if (prm->approx_reading != 0 && prm->approx_reading != 1) return FSMI_ERR_ARG;
     if (use != kUseBeams && !finite_pos(prm->max_range)) return FSMI_ERR_ARG;
-    if (prm->flags & ~FSMI_FLAG_FULL_SWEEP) return FSMI_ERR_ARG;
+    if (prm->flags & ~(FSMI_FLAG_FULL_SWEEP | FSMI_FLAG_FULL_WINDOW)) return FSMI_ERR_ARG;
     d.variant = prm->variant;
     d.sigma = prm->variant == FSMI_UNIFORM ? 1.0f : prm->sigma;
     d.inv_s2 = (float)(1.0 / ((double)d.sigma * 1.4142135623730951));

@@ -25,6 +25,7 @@ from . import build as _build
 EXACT, APPROX, UNIFORM = 0, 1, 2
 G_PDF, G_ERF = 0, 1
 FLAG_FULL_SWEEP = 0x1
+FLAG_FULL_WINDOW = 0x2
 FN_EVAL_2D, FN_EVAL_BEAMS, FN_RLE_ENCODE_3D, FN_EVAL_RLE, FN_EVAL_3D, FN_UPDATE_MAP_2D = 0, 1, 2, 3, 4, 5
 QUEUE_BYTES = 256
 SURR_L, SURR_NPARAMS = 256, 269089

@@ -215,21 +215,53 @@ def test_gauss_tail_against_cuda_erfc():
     assert bool(torch.all(err <= 1.5e-6 * ref + 2.5e-8))
 
 
+WINDOW_CASES = ((64.0, 1.5, 0), (256.0, 2.0, 24), (256.0, 0.4, 8), (256.0, 12.0, 8))
+
+
+def _window_case(R, sigma, n_poses):
+    if n_poses == 0:
+        return synth.config1()
+    return synth.config2(n_poses=n_poses, size=512)
+
+
 @pytest.mark.parametrize("e0", [0, 1])
-def test_exact_window_is_bit_identical_to_full_sweep(e0):
-    # skipping the tail terms that flush to zero in FP32 must not change a single bit
-    for grid, poses, dirs, R, sigma in (synth.config1() + (64.0, 1.5), synth.config2(n_poses=24, size=512) + (256.0, 2.0),
-                                        synth.config2(n_poses=8, size=512) + (256.0, 0.4)):
+def test_exact_full_window_is_bit_identical_to_full_sweep(e0):
+    # skipping only the tail terms that flush to zero in FP32 must not change a single bit
+    for R, sigma, npo in WINDOW_CASES:
+        grid, poses, dirs = _window_case(R, sigma, npo)
         gp, _ = _prms(sigma, R, e0)
+        gp.flags = fsmi.FLAG_FULL_WINDOW
         win = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp)
         gp.flags = fsmi.FLAG_FULL_SWEEP
         full = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp)
         assert torch.equal(win, full)
     off, o, l, lend = synth.random_beams(200, 0, 400, seed=77)
     gp, _ = _prms(3.0, 64.0, e0)
+    gp.flags = fsmi.FLAG_FULL_WINDOW
     win = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp)
     gp.flags = fsmi.FLAG_FULL_SWEEP
     assert torch.equal(win, fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp))
+
+
+@pytest.mark.parametrize("e0", [0, 1])
+def test_exact_default_window_against_full_sweep(e0):
+    # the default window skips terms below 2^-37 of their weights: the MI moves by a few FP32
+    # roundings of the running sums at most, far inside the parity tolerance (in practice a
+    # skipped term shifts a slot sum by ~1e-4 of its last bit, so the results are rarely changed)
+    for R, sigma, npo in WINDOW_CASES:
+        grid, poses, dirs = _window_case(R, sigma, npo)
+        gp, _ = _prms(sigma, R, e0)
+        win = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy().astype(np.float64)
+        gp.flags = fsmi.FLAG_FULL_SWEEP
+        full = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy().astype(np.float64)
+        err = np.abs(win - full)
+        assert np.all(err <= 2.0 ** -20 * np.abs(full) + 1e-9), (sigma, err.max())
+    off, o, l, lend = synth.random_beams(200, 0, 400, seed=77)
+    gp, _ = _prms(3.0, 64.0, e0)
+    win = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy().astype(np.float64)
+    gp.flags = fsmi.FLAG_FULL_SWEEP
+    full = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(win - full) <= 2.0 ** -20 * np.abs(full) + 1e-9)
 
 
 def test_zero_length_cells():
@@ -249,7 +281,7 @@ def test_zero_length_cells():
     l = np.concatenate([d[:-1] for d in dists]).astype(np.float32)
     lend = np.array([d[-1] for d in dists], np.float32)
     for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP),
-               dict(variant=fsmi.APPROX, trunc_delta=3)):
+               dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_WINDOW), dict(variant=fsmi.APPROX, trunc_delta=3)):
         for e0 in (0, 1):
             gp, op = _prms(1.0, 64.0, e0, **kw)
             op_kw = {k: v for k, v in kw.items() if k != "flags"}
