@@ -44,7 +44,7 @@ TAIL_CUT = 5.75  # scaled half-width of the exact kernel's default window (csrc/
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
 # ncu capture (profiles/k_eval_2d_exact_office2048.md), valid only for the kernel sources whose
 # hash is recorded with it; reported as null once those sources change.
-TRAFFIC = {"sources_sha1": "6880f5ab5a87372fbc9013813e804436eff59e77", "bytes_per_launch": 99.73e6}
+TRAFFIC = {"sources_sha1": "c950a0ea0b5ff062b7f23be860529cbb26fb77fd", "bytes_per_launch": 110.63e6}
 KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb300/csrc/eval2d.cuh",
                   "paper_1905_02238_gb300/csrc/dda2d.cuh", "paper_1905_02238_gb300/csrc/gauss_tail.cuh",
                   "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]
