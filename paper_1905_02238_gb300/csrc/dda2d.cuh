@@ -29,9 +29,15 @@ __device__ __forceinline__ void beam_dir(const int32_t *pose, int32_t ux, int32_
 // into intervals [lambda_M(k), lambda_M(k+1)), k = -1, 0, 1, ... (lambda_M(-1) = 0). Minor
 // crossings are at least as far apart as major ones, so each interval holds the cell entered at
 // its start plus at most one cell entered at a minor crossing strictly inside it. Lane L walks a
-// contiguous block of intervals; its starting minor coordinate is the number of minor crossings
-// at or before lambda_M(k0) (one integer division). A warp scan of per-lane cell counts places the
-// cells; the first lane that meets the range limit or the grid boundary ends the beam.
+// contiguous block of intervals k0..k1; its starting minor coordinate is the number of minor
+// crossings at or before lambda_M(k0) (one integer division). Its cell count, unless the beam
+// ends inside the block, is (k1 - k0 + 1) + (minor crossings in (lambda_M(k0), lambda_M(k1+1)])
+// minus the crossings among those that coincide with a major crossing (diagonal steps, which
+// enter one cell, not two). The lanes write their cells at offsets from a warp scan of that count
+// taken without the coincidences, and count the coincidences as they walk; if a lane before the
+// one where the beam ends met any, the offsets were too large and the lanes walk again at the
+// exact offsets (beams along a lattice diagonal through cell centres; rare otherwise). The first
+// lane that meets the range limit or the grid boundary ends the beam.
 
 struct Geo {
     int sM, sm, cM0, cm0, dimM, dimm, xmaj, W;
@@ -60,14 +66,18 @@ __device__ __forceinline__ int minor_before(const Geo &g, int k)
     return (int)q + 1;
 }
 
+// Walks intervals k0..k1 from minor crossing i0 = minor_before(k0), writing (WRITE) its cells
+// from index `base`; cnt = cells entered, ties = minor crossings that coincided with a major one
+// (diagonal steps) before the walk ended.
 template <bool WRITE>
-__device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int base, int cap, int *ids, float *l, int &cnt,
-                                     bool &ended, float &endl, bool &by_range)
+__device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int base, int cap, int *ids, float *l,
+                                     int &cnt, int &ties, bool &ended, float &endl, bool &by_range)
 {
     int cM = g.cM0 + g.sM * (k0 + 1);
-    int i = minor_before(g, k0);
+    int i = i0;
     int cm = g.cm0 + g.sm * i;
     cnt = 0;
+    ties = 0;
     ended = false;
     endl = 0.0f;
     by_range = false;
@@ -114,6 +124,7 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int base, int
         if (tie) {
             cm += g.sm;
             ++i;
+            ++ties;
         }
         if ((unsigned)cM >= (unsigned)g.dimM || (unsigned)cm >= (unsigned)g.dimm) {
             ended = true;
@@ -170,10 +181,16 @@ static __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, lon
     const int q = (NI + 31) >> 5;
     const int k0 = -1 + lane * q;
     const int k1 = min(K - 1, k0 + q - 1);
-    int cnt = 0;
+    int cnt = 0, ties = 0;
     bool ended = false, rng = false;
     float endl = 0.0f;
-    if (k0 <= k1) walk<false>(g, k0, k1, 0, cap, ids, l, cnt, ended, endl, rng);
+    int i0 = 0, pred = 0;
+    if (k0 <= k1) {
+        i0 = minor_before(g, k0);
+        pred = (k1 - k0 + 1) + minor_before(g, k1 + 1) - i0;
+    }
+    const int pinc = warp_incl_add_int(pred);
+    if (k0 <= k1) walk<true>(g, k0, k1, i0, pinc - pred, cap, ids, l, cnt, ties, ended, endl, rng);
     const unsigned eb = __ballot_sync(kFull, ended);
     const int first = eb ? __ffs(eb) - 1 : 31;
     const int c = lane <= first ? cnt : 0;
@@ -183,7 +200,11 @@ static __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, lon
     const unsigned rb = __ballot_sync(kFull, rng);
     if (end_by_range) *end_by_range = (rb >> first) & 1u;
     if (n > cap) return -1;
-    if (lane <= first && k0 <= k1) walk<true>(g, k0, k1, inc - c, cap, ids, l, cnt, ended, endl, rng);
+    // offsets of lanes after a diagonal step were too large: place the cells again
+    if (__any_sync(kFull, lane < first && ties > 0)) {
+        __syncwarp();
+        if (lane <= first && k0 <= k1) walk<true>(g, k0, k1, i0, inc - c, cap, ids, l, cnt, ties, ended, endl, rng);
+    }
     if (lane == 0) l[n] = lend;
     __syncwarp();
     return n;

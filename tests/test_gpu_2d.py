@@ -79,6 +79,27 @@ def test_trace_random_poses_bit_exact():
     _trace_compare(W, H, poses, dirs, 40.5)
 
 
+def test_trace_lattice_diagonals_bit_exact():
+    # directions with exact integer slope ratios from cell centres and corners: minor crossings
+    # coincide with major ones (diagonal steps) all along the beam, which moves the cell offsets
+    # of every later lane of the warp
+    W, H = 64, 48
+    poses = []
+    for ix, iy, frac in ((5, 7, 0.5), (30, 20, 0.5), (12, 40, 0.0), (63, 0, 0.5), (0, 47, 0.0), (33, 9, 0.25)):
+        p = synth.pose_2d(0, 0, 0.0)
+        p[0], p[1] = int((ix + frac) * 65536), int((iy + frac) * 65536)
+        poses.append(p)
+    poses = np.stack(poses)
+    ratios = [(1, 1), (-1, 1), (1, -1), (-1, -1), (2, 1), (1, 2), (-2, 1), (3, 2), (2, -3), (4, 1), (1, 0), (0, -1)]
+    dirs = []
+    for a, b in ratios:  # near-unit Q30 vectors with an exact integer ratio a : b
+        c = int(round(2 ** 30 / np.hypot(a, b)))
+        dirs.append([a * c, b * c])
+    dirs = np.array(dirs, np.int32)
+    _trace_compare(W, H, poses, dirs, 60.0)
+    _trace_compare(W, H, poses, dirs, 9.0)
+
+
 def test_trace_office_map_sampled():
     grid, poses, dirs = synth.config2(n_poses=16, size=512)
     _trace_compare(512, 512, poses, dirs, 256.0)
