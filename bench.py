@@ -18,6 +18,7 @@ bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -148,29 +149,56 @@ def workload(rank: int, n_poses: int = N_POSES):
     return grid, poses, dirs
 
 
-def cpu_baseline(grid, poses, dirs, n_pose_sample: int = 288):
-    """The FP64 oracle as it stands, on all host cores, on the first n_pose_sample poses."""
+def cpu_baseline(grid, poses, dirs, gpu_out=None, n_pose_sample: int = 288, n_single: int = 4):
+    """The FP64 oracle as it stands, on all host cores, on the first n_pose_sample poses (and on one
+    core on the first n_single); with gpu_out (the timed kernel's [P][B] result) also the parity of
+    those beams against the oracle."""
+    import numpy as np
+
     import oracle
 
     prm = oracle.Params(variant=oracle.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.eval_2d(grid, poses[:n_pose_sample], dirs, prm, nthreads=threads)
+    ref = oracle.eval_2d(grid, poses[:n_pose_sample], dirs, prm, nthreads=threads)
     dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oracle.eval_2d(grid, poses[:n_single], dirs, prm, nthreads=1)
+    dt1 = time.perf_counter() - t1
     nb = n_pose_sample * dirs.shape[0]
-    return {"value": nb / dt, "unit": "beams/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {n_pose_sample} poses x {dirs.shape[0]} beams ({nb} beams), FP64, {dt:.1f} s wall"}
+    res = {"value": nb / dt, "unit": "beams/s", "cores": threads, "kind": "oracle",
+           "sample": f"first {n_pose_sample} poses x {dirs.shape[0]} beams ({nb} beams), FP64, {dt:.1f} s wall",
+           "single_core": {"value": n_single * dirs.shape[0] / dt1, "unit": "beams/s",
+                           "sample": f"first {n_single} poses x {dirs.shape[0]} beams, 1 thread, {dt1:.1f} s"}}
+    if gpu_out is not None:
+        got = np.asarray(gpu_out[:n_pose_sample], np.float64).reshape(ref.shape)
+        ref = np.asarray(ref, np.float64)
+        err = np.abs(got - ref)
+        rel = err / np.maximum(np.abs(ref), 1e-30)
+        res["parity_vs_oracle"] = {
+            "beams": int(ref.size), "max_abs_err": float(err.max()), "max_rel_err": float(rel.max()),
+            "median_rel_err": float(np.median(rel)),
+            "within_tolerance": bool(np.all(err <= 1e-4 * np.abs(ref) + 1e-7)),
+            "tolerance": "|gpu - oracle| <= 1e-4 |oracle| + 1e-7 nats per beam"}
+    return res
+
+
+def band_terms(n, delta):
+    """Sum over first-hit cells j of the Approx-FSMI band size |[j - delta, j + delta] n [0, n - 1]|."""
+    full = n * (2 * delta + 1) - delta * (delta + 1)  # n >= delta: each edge loses delta(delta+1)/2
+    return full.where(n > delta, n * n)  # n <= delta: every band is the whole beam
 
 
 def work_counts(fsmi, grid, p, d, chunk=32768):
-    """(cells, Theorem-1 boundary terms n(n+1), terms the exact kernel evaluates) of one launch."""
+    """(cells, Theorem-1 boundary terms n(n+1), terms the exact kernel evaluates, Approx band
+    terms at Delta = 6) of one launch."""
     import torch
 
     cap = int(R_MAX * 1.5) + 4
     _, l, n = fsmi.trace_2d(grid.shape[1], grid.shape[0], p, d, R_MAX, cap)
     cs = float(torch.tensor(1.0 / (SIGMA * 1.4142135623730951), dtype=torch.float32) *
                torch.tensor(1.2011224087864498, dtype=torch.float32))
-    cells = pairs = terms = 0.0
+    cells = pairs = terms = band = 0.0
     col = torch.arange(cap + 1, device=l.device)
     for a in range(0, n.shape[0], chunk):
         nn = n[a:a + chunk].to(torch.int64)
@@ -184,7 +212,59 @@ def work_counts(fsmi, grid, p, d, chunk=32768):
         n64 = nn.to(torch.float64)
         cells += float(n64.sum().item())
         pairs += float((n64 * (n64 + 1)).sum().item())
-    return cells, pairs, terms
+        band += float(band_terms(n64, 6).sum().item())
+    return cells, pairs, terms, band
+
+
+def rle_crossover_leg(dev):
+    """The paper's run-length experiment (beams of 256 unit cells made of groups of L cells of equal
+    occupancy; 100,000 beams rather than the paper's 1000, so that the GPU times throughput and not
+    launch latency): exact FSMI on the cells (fsmi_eval_beams) against FSMI-RLE on the runs
+    (fsmi_eval_rle, Gaussian mass of a unit cell, runs split at 64), same values."""
+    import numpy as np
+    import torch
+
+    from paper_1905_02238_gb300 import fsmi
+
+    rng = np.random.default_rng(15)
+    nb, n = 100_000, 256
+    prm_c = fsmi.Params(variant=fsmi.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=float(n))
+    prm_r = fsmi.Params(variant=fsmi.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=float(n),
+                        run_cap=64, g_kernel=fsmi.G_ERF)
+    off = torch.arange(nb + 1, dtype=torch.int32, device=dev) * n
+    l = torch.arange(n, dtype=torch.float32, device=dev).repeat(nb)
+    lend = torch.full((nb,), float(n), dtype=torch.float32, device=dev)
+    ws = torch.empty(fsmi.QUEUE_BYTES, dtype=torch.uint8, device=dev)
+    rows = []
+    for L in (1, 2, 4, 8, 16, 32, 64, 128):
+        ng = -(-n // L)
+        og = rng.uniform(0.0, 1.0, (nb, ng)).astype(np.float32)
+        o = torch.from_numpy(np.repeat(og, L, axis=1)[:, :n].reshape(-1).copy()).to(dev)
+        lens = [min(L, n - k * L) for k in range(ng)]
+        split = [(g, min(64, ln - s)) for g, ln in enumerate(lens) for s in range(0, ln, 64)]
+        gi = np.array([g for g, _ in split])
+        rl = torch.from_numpy(np.tile(np.array([x for _, x in split], np.uint8), nb)).to(dev)
+        ro = torch.from_numpy(og[:, gi].reshape(-1).copy()).to(dev)
+        roff = torch.arange(nb + 1, dtype=torch.int32, device=dev) * len(split)
+        oc = torch.empty(nb, dtype=torch.float32, device=dev)
+        orr = torch.empty(nb, dtype=torch.float32, device=dev)
+        ms_c = _time_ms(lambda: fsmi.eval_beams(off, o, l, lend, prm_c, out=oc, ws=ws), reps=10)
+        ms_auto = _time_ms(lambda: fsmi.eval_rle(roff, ro, rl, prm_r, out=orr, ws=ws), reps=10)
+        saved = fsmi.get_schedule(fsmi.KIND_RLE)
+        fsmi.set_schedule(fsmi.KIND_RLE, dataclasses.replace(saved, cell_runlen=1))  # run pairs always
+        try:
+            ms_r = _time_ms(lambda: fsmi.eval_rle(roff, ro, rl, prm_r, out=orr, ws=ws), reps=10)
+        finally:
+            fsmi.set_schedule(fsmi.KIND_RLE, saved)
+        diff = float(((orr - oc).abs() / oc.abs().clamp_min(1e-30)).max().item())
+        rows.append({"L": L, "runs_per_beam": len(split), "cells_ms": ms_c, "rle_run_pairs_ms": ms_r,
+                     "rle_default_ms": ms_auto, "run_pairs_speedup": ms_c / ms_r, "max_rel_diff": diff})
+    faster = [r["L"] for r in rows if r["rle_run_pairs_ms"] < r["cells_ms"]]
+    return {"workload": "100,000 beams x 256 unit cells in groups of L cells of equal U(0,1) occupancy; exact FSMI "
+                        "per cell (fsmi_eval_beams) vs FSMI-RLE on the runs (fsmi_eval_rle, unit-cell Gaussian "
+                        "mass; run pairs always, and with the default schedule that takes the cell form for "
+                        "mean run lengths below 32)",
+            "rows": rows, "run_pairs_faster_from_L": faster[0] if faster else None}
 
 
 def _time_ms(fn, reps=5):
@@ -207,7 +287,7 @@ def _sched(s):
             "cell_runlen": s.cell_runlen}
 
 
-def other_variants(g, p, d, out):  # noqa: C901
+def other_variants(g, p, d, out, cells=None, terms=None, band=None):  # noqa: C901
     """Throughput of the other variants on the same devices (context; not the headline). The 3D
     variants run as the 512x512x128 depth-camera batch in one persistent launch with an autotuned
     schedule, captured in a CUDA graph and timed by graph replays."""
@@ -218,13 +298,31 @@ def other_variants(g, p, d, out):  # noqa: C901
     res = {}
     nb = p.shape[0] * d.shape[0]
     gains_ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=g.device)
-    for name, kw in (("exact_fsmi_full_sweep", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP)),
-                     ("exact_fsmi_full_window", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_WINDOW)),
-                     ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6)),
-                     ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4))):
+    for name, kw, nterms in (("exact_fsmi_full_sweep", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP), None),
+                             ("exact_fsmi_full_window", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_WINDOW), None),
+                             ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6), band),
+                             ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4), None)):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)
         ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out, ws=gains_ws))
         res[name] = {"beams_per_s": nb / (ms * 1e-3), "ms": ms}
+        if cells:
+            res[name]["cells_per_s"] = cells / (ms * 1e-3)
+        if nterms:
+            res[name]["band_terms_per_s"] = nterms / (ms * 1e-3)
+    if terms:
+        res["exact_fsmi_window_terms"] = terms
+    # config 1 (correctness configuration, launch-latency bound): one pose x 360 beams, R = 64
+    g1, p1, d1 = (torch.from_numpy(x).to(g.device) for x in synth.config1())
+    o1 = torch.empty((1, 360), dtype=torch.float32, device=g.device)
+    prm1 = fsmi.Params(variant=fsmi.EXACT, sigma=1.5, delta_occ=DOCC, delta_emp=DEMP, max_range=64.0)
+    ws1 = torch.empty(fsmi.QUEUE_BYTES, dtype=torch.uint8, device=g.device)
+    graph1 = fsmi.Graph(lambda: fsmi.eval_2d(g1, p1, d1, prm1, out=o1, ws=ws1))
+    res["config1_exact"] = {"us_per_launch_graph": 1e3 * _time_ms(graph1.replay, reps=200),
+                            "us_per_call": 1e3 * _time_ms(lambda: fsmi.eval_2d(g1, p1, d1, prm1, out=o1, ws=ws1),
+                                                          reps=200),
+                            "workload": "200x200 grid, 1 pose x 360 beams, R = 64, sigma = 1.5; per call = "
+                                        "through the Python binding (host launch overhead included)"}
+    graph1.close()
     vox, vp, vd = synth.config3()
     v, vp, vd = (torch.from_numpy(x).to(g.device) for x in (vox, vp, vd))
     nr = vp.shape[0] * vd.shape[0]
@@ -491,8 +589,8 @@ def run_fsmi(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # algorithmic work of one launch, from the (bit-exact) traversal: Theorem 1 has n(n+1)
-    # boundary terms per beam; the kernel evaluates those whose FP32 tail is not flushed to 0
-    cells, pairs, terms = work_counts(fsmi, grid, p, d)
+    # boundary terms per beam; the kernel evaluates those within its window
+    cells, pairs, terms, band = work_counts(fsmi, grid, p, d)
 
     stream = torch.cuda.current_stream()
 
@@ -579,14 +677,16 @@ def run_fsmi(args):
             "gpu_launches": 2 * args.steps,  # per step: per-cell gains of the map, then the beams
         }
         if ws == 1:
-            line["variants"] = other_variants(g, p, d, out)
+            exact_out = out.cpu().numpy()  # the timed steps' result, before the context runs reuse `out`
+            line["variants"] = other_variants(g, p, d, out, cells=cells, terms=terms, band=band)
+            line["rle_vs_cells"] = rle_crossover_leg(dev)
             if not args.no_surrogate:
                 line["surrogate_rerank"] = surrogate_leg(dev)
             if not args.no_mixed:
                 line["mixed_stream"] = mixed_leg(dev)
                 line["mixed_stream_small_sets"] = mixed_leg(dev, nsets=256, seed=6, pose_range=(16, 128, 4, 16),
                                                             len_range=(8, 64, 8, 64))
-            line["cpu_baseline"] = cpu_baseline(grid, poses, dirs)
+            line["cpu_baseline"] = cpu_baseline(grid, poses, dirs, gpu_out=exact_out)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
