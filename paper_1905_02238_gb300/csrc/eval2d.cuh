@@ -185,10 +185,13 @@ __device__ __forceinline__ f32x2 window_terms(const float *sl, const float *sdc,
         const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
         acc = fma2(dc, gauss_tail2p<true>(sub2(mu2, L)), acc);
     }
-    if (m < end && m == mid - 1) {  // the pair around the centre: m below, m + 1 above
+    if (m < end) {  // first pair at or above the centre; m lies below it when m == mid - 1
         const float2 L = *reinterpret_cast<const float2 *>(sl + m);
         const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
-        acc = fma2(pack2(-dc.x, dc.y), gauss_tail2p<false>(pack2(mu - L.x, L.y - mu)), acc);
+        const bool below = m == mid - 1;
+        const float d0 = below ? mu - L.x : L.x - mu;
+        const float c0 = below ? -dc.x : dc.x;
+        acc = fma2(pack2(c0, dc.y), gauss_tail2p<false>(pack2(d0, L.y - mu)), acc);
         m += 2;
     }
 #pragma unroll kPairUnroll

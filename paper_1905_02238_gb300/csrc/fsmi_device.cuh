@@ -98,7 +98,7 @@ __device__ __forceinline__ float ipowf(float x, int k)
 __device__ __forceinline__ float cell_prefixes(float *sp, float *sc, float *sx, int n, bool want_d)
 {
     const int lane = lane_id();
-    const int K = (n + 31) >> 5;
+    const int K = ((n + 31) >> 5) | 1;  // odd block length: the lanes' blocks start in distinct banks
     const int lo = min(n, lane * K), hi = min(n, lo + K);
     float prod = 1.0f, sum = 0.0f;
     for (int i = lo; i < hi; ++i) {
