@@ -36,16 +36,17 @@ N_POSES = 1024
 L2_FLUSH_BYTES = 512 << 20  # > the 126 MB L2
 SM_COUNT_NOMINAL = 152
 FMA_LANES_PER_SM_CLK = 128  # FP32 FMA-pipe lane operations per SM per clock (4 x 32)
-SFU_PER_SM_CLK = 32  # SFU (ex2, rcp) results per SM per clock, measured by a throughput probe
-OPS_PER_TERM = 12  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh):
-#                    distance, square, 1 + p|d|, 6 Horner FMAs, two products, accumulate;
-#                    plus 2 SFU operations (ex2, rcp), for which the SFU has room to spare
+EX2_PER_SM_CLK = 32  # SFU ex2.approx results per SM per clock (a throughput probe measured 30.2)
+RCP_PER_SM_CLK = 16  # SFU rcp.approx results per SM per clock (measured 15.1)
+SFU_CLK_PER_TERM = 1.0 / EX2_PER_SM_CLK + 1.0 / RCP_PER_SM_CLK  # one ex2 and one rcp per tail term
+OPS_PER_TERM = 11  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh): distance,
+#                    square, 1 + p|d|, 5 Horner FMAs, two products, accumulate
 TAIL_CUT = 5.75  # scaled half-width of the exact kernel's default window (csrc/eval2d.cuh)
 
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
 # ncu capture (profiles/k_eval_2d_exact_office2048.md), valid only for the kernel sources whose
 # hash is recorded with it; reported as null once those sources change.
-TRAFFIC = {"sources_sha1": "c950a0ea0b5ff062b7f23be860529cbb26fb77fd", "bytes_per_launch": 110.63e6}
+TRAFFIC = {"sources_sha1": "966461c706582ae7e2466da61220b31cc8a2cfb2", "bytes_per_launch": 111.40e6}
 KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb300/csrc/eval2d.cuh",
                   "paper_1905_02238_gb300/csrc/dda2d.cuh", "paper_1905_02238_gb300/csrc/gauss_tail.cuh",
                   "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]
@@ -287,7 +288,7 @@ def _sched(s):
             "cell_runlen": s.cell_runlen}
 
 
-def other_variants(g, p, d, out, cells=None, terms=None, band=None):  # noqa: C901
+def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=None):  # noqa: C901
     """Throughput of the other variants on the same devices (context; not the headline). The 3D
     variants run as the 512x512x128 depth-camera batch in one persistent launch with an autotuned
     schedule, captured in a CUDA graph and timed by graph replays."""
@@ -309,6 +310,9 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None):  # noqa: C9
             res[name]["cells_per_s"] = cells / (ms * 1e-3)
         if nterms:
             res[name]["band_terms_per_s"] = nterms / (ms * 1e-3)
+            if peak_terms and cells:
+                # Approx evaluates band + 1 boundary tails per first-hit cell (one ex2, one rcp each)
+                res[name]["roofline_sfu_frac"] = (nterms + cells) / (ms * 1e-3) / peak_terms
     if terms:
         res["exact_fsmi_window_terms"] = terms
     # config 1 (correctness configuration, launch-latency bound): one pose x 360 beams, R = 64
@@ -652,6 +656,8 @@ def run_fsmi(args):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_ops = sms * FMA_LANES_PER_SM_CLK * sm_max * 1e6  # FMA-pipe ops/s at the maximum SM clock
         achieved_ops = terms * OPS_PER_TERM / (ms * 1e-3)
+        peak_terms = sms * sm_max * 1e6 / SFU_CLK_PER_TERM  # tail terms/s the SFU allows
+        achieved_terms = terms / (ms * 1e-3)
         traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha1"] == kernel_sources_sha1() else None
         line = {
             "metric": METRIC, "value": value, "unit": "beams/s", "n_gpus": ws, "steps": args.steps,
@@ -665,12 +671,14 @@ def run_fsmi(args):
                        "autotune_ms": {f"{c.warps_per_block}w/q{c.queue_chunk}": round(t, 4)
                                        for c, t in zip(cands, tune_ms)},
                        "parallelism": f"dp{ws} (poses sharded, map replicated)"},
-            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "T FP32-op/s", "frac": achieved_ops / peak_ops, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved_terms / 1e12, "peak": peak_terms / 1e12,
+                         "unit": "T tail-terms/s (SFU)", "frac": achieved_terms / peak_terms, "traffic": traffic,
                          "kernel": "k_eval_2d<EXACT,map>",
-                         "model": f"{OPS_PER_TERM} FMA-pipe ops per evaluated tail term x {terms:.4g} terms; "
-                                  f"peak = {sms} SMs x {FMA_LANES_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz "
-                                  f"(SFU: 2 ops/term of {SFU_PER_SM_CLK}/clk/SM, not binding)"},
+                         "fma_frac": achieved_ops / peak_ops,
+                         "model": f"{terms:.4g} evaluated tail terms per launch, each one ex2 and one rcp on the "
+                                  f"SFU ({EX2_PER_SM_CLK} and {RCP_PER_SM_CLK} per SM per clock: the binding pipe) "
+                                  f"and {OPS_PER_TERM} FMA-pipe ops ({FMA_LANES_PER_SM_CLK} lanes per SM per clock; "
+                                  f"fma_frac); peak = {sms} SMs x {sm_max:.0f} MHz"},
             "clocks": clocks,
             "e2e": {"value": whole_job_rate(P * B, ws, e2e_s), "unit": "beams/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -678,7 +686,8 @@ def run_fsmi(args):
         }
         if ws == 1:
             exact_out = out.cpu().numpy()  # the timed steps' result, before the context runs reuse `out`
-            line["variants"] = other_variants(g, p, d, out, cells=cells, terms=terms, band=band)
+            line["variants"] = other_variants(g, p, d, out, cells=cells, terms=terms, band=band,
+                                              peak_terms=peak_terms)
             line["rle_vs_cells"] = rle_crossover_leg(dev)
             if not args.no_surrogate:
                 line["surrogate_rerank"] = surrogate_leg(dev)
