@@ -359,11 +359,14 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
 SURR_FLOPS_PER_BEAM = 2 * (128 * 32 * 6 + 64 * 32 * 96 + 32 * 32 * 96 + 1024 * 256 + 256)  # conv1-3, fc1, fc2
 
 
+PRESCREEN_MIN_RANGE = 96.0  # shorter beams are cheap to evaluate exactly; the network's cost is per beam
+
+
 def surrogate_leg(dev, steps: int = 2500):
     """Config 4: train the surrogate on 10.3 M beams that exact FSMI labels (7 office maps x 4096
     poses x 360 beams), then select the best 10 of 4096 candidate poses on a held-out map by
     surrogate prescreen + exact rerank of the top 64, against exact FSMI of every beam. Both
-    selections run as CUDA-graph replays."""
+    selections run as CUDA-graph replays. Returns (result, network)."""
     import numpy as np
     import torch
 
@@ -420,19 +423,77 @@ def surrogate_leg(dev, steps: int = 2500):
                          "note": "mma.sync BF16 (conv stack + fc1), against the measured cuBLAS BF16 peak"},
         "training": {"label_s": t_label, "train_s": t_train, "steps": steps, "batch": 4096,
                      "loss_first_last": [losses[0], losses[-1]]},
-    }
+    }, net
 
 
-def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512), len_range=(8, 512, 8, 256)):
-    """Config 5: a stream of candidate sets on a 4096x4096 office map and two 256x256x64 voxel
-    submaps, evaluated exactly (2D FSMI, sigma 2; 3D FSMI-RLE, sigma 2, run cap 64) in one
-    persistent launch (fsmi_eval_mixed), against the same sets launched one after the other.
-    Sets (default): 3 in 4 are 2D (16-8192 poses, log-uniform; 360 beams; range 8-512 cells), the
-    rest 3D (16-512 poses; 64x64 rays; 8-256 virtual cells); pose_range and len_range give other
-    streams. All sets are queued at time 0; a set's latency is the time until its last beam or ray
-    is done."""
+def surrogate_stream_leg(dev, net, k: int = 64, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512),
+                         len_range=(8, 512, 8, 256)):
+    """Config 5 with the surrogate: each 2D set of the stream whose range the network covers
+    (R <= 256) and that has more than k poses selects its best 10 poses by surrogate prescreen
+    (profiles cut at the set's range, which the network reads as the map ending there; it is
+    trained at R = 256 only) + exact rerank of the top k, against exact FSMI of all its beams, and
+    by a per-set choice of the two (prescreen from PRESCREEN_MIN_RANGE up). The sets run one after
+    the other in stream order, all queued at time 0, so a set's latency is the sum of the service
+    times up to it."""
     import numpy as np
     import torch
+
+    from paper_1905_02238_gb300 import fsmi
+    from paper_1905_02238_gb300 import surrogate as sg
+
+    grid, poses2, dirs2, _, _, _, sets = stream_sets(nsets, seed, pose_range, len_range)
+    g, p2, d2 = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (grid, poses2, dirs2))
+    rows = []
+    for s_ in sets:
+        kind, po, npose, do, ndir, r = s_[:6]
+        if kind != fsmi.SET_2D or r > fsmi.SURR_L or npose <= k:
+            continue
+        prm = fsmi.Params(variant=fsmi.EXACT, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=r)
+        pg = p2[po:po + npose]
+        ex = sg.ExactAll(g, pg, d2, prm)
+        pre = sg.Prescreen(net, g, pg, d2, prm, k=k)
+        ex.run()
+        found = pre.run()
+        scores = ex.score.clone()
+        rows.append({"poses": npose, "range": r, "exact_ms": _time_ms(ex.run, reps=3),
+                     "prescreen_ms": _time_ms(pre.run, reps=3),
+                     "recall_at_10_ties_1e-4": sg.recall_with_ties(found, scores, 10, 1e-4),
+                     "regret": sg.regret(found, scores)})
+        del ex, pre
+    if not rows:
+        return {"sets": 0}
+    poses = sum(r_["poses"] for r_ in rows)
+
+    for r_ in rows:
+        use = r_["range"] >= PRESCREEN_MIN_RANGE
+        r_["chosen_ms"] = r_["prescreen_ms"] if use else r_["exact_ms"]
+        r_["chosen_recall"] = r_["recall_at_10_ties_1e-4"] if use else 1.0
+
+    def summary(key):
+        ms = np.array([r_[key] for r_ in rows])
+        lat = np.cumsum(ms)
+        return {"ms": float(ms.sum()), "poses_per_s": poses / (ms.sum() * 1e-3),
+                "set_latency_ms_p50": float(np.percentile(lat, 50)), "set_latency_ms_p99": float(np.percentile(lat, 99))}
+
+    rec = [r_["recall_at_10_ties_1e-4"] for r_ in rows]
+    return {"workload": f"the 2D sets of the {nsets}-set stream (4096x4096 office map, 360 beams) with R <= "
+                        f"{fsmi.SURR_L} and more than {k} poses; sets in stream order, all queued at t = 0",
+            "sets": len(rows), "poses": poses, "exact_all": summary("exact_ms"),
+            "prescreen_rerank": summary("prescreen_ms"),
+            "speedup": sum(r_["exact_ms"] for r_ in rows) / sum(r_["prescreen_ms"] for r_ in rows),
+            "recall_at_10_ties_1e-4": {"min": min(rec), "mean": float(np.mean(rec))},
+            "per_set_choice": {**summary("chosen_ms"), "rule": f"prescreen when R >= {PRESCREEN_MIN_RANGE:g}, else exact",
+                               "speedup": sum(r_["exact_ms"] for r_ in rows) / sum(r_["chosen_ms"] for r_ in rows),
+                               "recall_at_10_min": min(r_["chosen_recall"] for r_ in rows)},
+            "regret_max": max(r_["regret"] for r_ in rows), "rows": rows}
+
+
+def stream_sets(nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512), len_range=(8, 512, 8, 256)):
+    """The config-5 stream: a 4096x4096 office map with 16384 free-cell poses and 360 beams, two
+    256x256x64 voxel submaps with 512 poses each and 64x64 rays, and nsets candidate sets: 3 in 4
+    are 2D (pose_range[0]-[1] poses, log-uniform; range len_range[0]-[1] cells), the rest 3D
+    (pose_range[2]-[3] poses; len_range[2]-[3] virtual cells), as fsmi.make_sets tuples."""
+    import numpy as np
 
     from paper_1905_02238_gb300 import fsmi, synth
 
@@ -454,6 +515,23 @@ def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512
             npose = int(np.exp(rng.uniform(np.log(pose_range[2]), np.log(pose_range[3]))))
             k = int(rng.integers(0, 2))
             sets.append((fsmi.SET_3D, 512 * k, npose, 0, 4096, float(rng.integers(len_range[2], len_range[3] + 1)), k))
+    return grid, poses2, dirs2, vols, poses3, dirs3, sets
+
+
+def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512), len_range=(8, 512, 8, 256)):
+    """Config 5: a stream of candidate sets on a 4096x4096 office map and two 256x256x64 voxel
+    submaps, evaluated exactly (2D FSMI, sigma 2; 3D FSMI-RLE, sigma 2, run cap 64) in one
+    persistent launch (fsmi_eval_mixed), against the same sets launched one after the other.
+    Sets (default): 3 in 4 are 2D (16-8192 poses, log-uniform; 360 beams; range 8-512 cells), the
+    rest 3D (16-512 poses; 64x64 rays; 8-256 virtual cells); pose_range and len_range give other
+    streams. All sets are queued at time 0; a set's latency is the time until its last beam or ray
+    is done."""
+    import numpy as np
+    import torch
+
+    from paper_1905_02238_gb300 import fsmi, synth
+
+    grid, poses2, dirs2, vols, poses3, dirs3, sets = stream_sets(nsets, seed, pose_range, len_range)
     g, p2, d2, p3, d3 = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (grid, poses2, dirs2, poses3, dirs3))
     vt = [torch.from_numpy(v).to(dev) for v in vols]
     vd = fsmi.make_volumes(vt, dev)
@@ -689,12 +767,15 @@ def run_fsmi(args):
             line["variants"] = other_variants(g, p, d, out, cells=cells, terms=terms, band=band,
                                               peak_terms=peak_terms)
             line["rle_vs_cells"] = rle_crossover_leg(dev)
+            net = None
             if not args.no_surrogate:
-                line["surrogate_rerank"] = surrogate_leg(dev)
+                line["surrogate_rerank"], net = surrogate_leg(dev)
             if not args.no_mixed:
                 line["mixed_stream"] = mixed_leg(dev)
                 line["mixed_stream_small_sets"] = mixed_leg(dev, nsets=256, seed=6, pose_range=(16, 128, 4, 16),
                                                             len_range=(8, 64, 8, 64))
+                if net is not None:
+                    line["mixed_stream_surrogate"] = surrogate_stream_leg(dev, net)
             line["cpu_baseline"] = cpu_baseline(grid, poses, dirs, gpu_out=exact_out)
         print(json.dumps(line), flush=True)
     if ws > 1:

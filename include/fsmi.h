@@ -420,10 +420,12 @@ fsmi_status fsmi_update_map_2d(float *map, int W, int H, const int32_t *poses, i
 
 /* fsmi_profiles_2d - BF16 profiles out [N][256][2] of beams `beam_ids` (flat p * B + b; NULL = all
  * N = P * B beams in order). An id outside [0, P * B) gives an all-zero profile and sets
- * FSMI_STATUS_BAD_BEAM. */
+ * FSMI_STATUS_BAD_BEAM. max_range (cells): a sample at distance i + 1/2 >= max_range reads as
+ * outside the map, (0, 0), as if the map ended there (a beam cut at range R crosses the same cells
+ * as one whose map ends at R); max_range <= 0 keeps all 256 samples. NaN is an argument error. */
 fsmi_status fsmi_profiles_2d(const float *map, int W, int H, const int32_t *poses, int P,
-                             const int32_t *dirs, int B, const int32_t *beam_ids, long long N,
-                             uint16_t *out, fsmi_stream_t stream);
+                             const int32_t *dirs, int B, float max_range, const int32_t *beam_ids,
+                             long long N, uint16_t *out, fsmi_stream_t stream);
 
 /* Workspace of fsmi_surrogate_loss_grad for a batch of N (mode 0) or of fsmi_surrogate_predict
  * for N beams (mode 1). */
@@ -446,14 +448,15 @@ fsmi_status fsmi_surrogate_adam(float *params, float *m, float *v, const float *
 fsmi_status fsmi_surrogate_cast(const float *params, uint16_t *wbf16, fsmi_stream_t stream);
 
 /* fsmi_surrogate_predict - predictions pred [P*B] for every beam of every pose on the map (the
- * profiles are sampled inside the kernel), or, with map == NULL, for N given profiles x. The conv
- * layers (mma.sync) and fc1 (tcgen05, accumulators in TMEM) run on the tensor cores with BF16
- * activations between layers and FP32 accumulation; fc2 reads the fc1 activations in FP32.
+ * profiles are sampled inside the kernel, cut at max_range as in fsmi_profiles_2d), or, with
+ * map == NULL, for N given profiles x (max_range unused). The conv layers (mma.sync) and fc1
+ * (tcgen05, accumulators in TMEM) run on the tensor cores with BF16 activations between layers and
+ * FP32 accumulation; fc2 reads the fc1 activations in FP32.
  * ws: fsmi_surrogate_workspace_size(1, N) bytes, 16-byte aligned. */
 fsmi_status fsmi_surrogate_predict(const float *params, const uint16_t *wbf16, const float *map,
                                    int W, int H, const int32_t *poses, int P, const int32_t *dirs,
-                                   int B, const uint16_t *x, long long N, float *pred, void *ws,
-                                   size_t ws_bytes, fsmi_stream_t stream);
+                                   int B, float max_range, const uint16_t *x, long long N, float *pred,
+                                   void *ws, size_t ws_bytes, fsmi_stream_t stream);
 
 /* fsmi_topk - idx [k] = indices of the k largest of v [n] in descending order, lower index first
  * among equal values, NaN last. 1 <= k <= n <= 16384. */

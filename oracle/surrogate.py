@@ -74,10 +74,12 @@ def init_params(seed: int) -> np.ndarray:
 
 # ---- profile -------------------------------------------------------------------------------------
 
-def profile_2d(grid, pose, u, L: int = L_IN) -> np.ndarray:
+def profile_2d(grid, pose, u, L: int = L_IN, max_range: float = 0.0) -> np.ndarray:
     """Samples of one beam: sample i is the cell holding o + (i + 1/2) d (d the Q30 beam
     direction), i.e. the floor of the Q31 position (o << 15) + (2i + 1) d; x[i] = (o, 1) inside the
-    map, (0, 0) outside. Exact integer arithmetic."""
+    map, (0, 0) outside, and (0, 0) too when the sample lies at or beyond max_range (i + 1/2 >=
+    max_range, max_range > 0): a beam cut at range R sees the cells of a map that ends at R. Exact
+    integer arithmetic."""
     H, W = grid.shape
     c, s = int(pose[2]), int(pose[3])
     ux, uy = int(u[0]), int(u[1])
@@ -85,6 +87,8 @@ def profile_2d(grid, pose, u, L: int = L_IN) -> np.ndarray:
     dy = (s * ux + c * uy + (1 << 29)) >> 30
     x = np.zeros((L, 2), np.float64)
     for i in range(L):
+        if max_range > 0 and i + 0.5 >= max_range:
+            continue
         px = ((int(pose[0]) << 15) + (2 * i + 1) * dx) >> 31
         py = ((int(pose[1]) << 15) + (2 * i + 1) * dy) >> 31
         if 0 <= px < W and 0 <= py < H:
@@ -93,11 +97,11 @@ def profile_2d(grid, pose, u, L: int = L_IN) -> np.ndarray:
     return x
 
 
-def profiles_2d(grid, poses, dirs, L: int = L_IN) -> np.ndarray:
+def profiles_2d(grid, poses, dirs, L: int = L_IN, max_range: float = 0.0) -> np.ndarray:
     out = np.zeros((poses.shape[0] * dirs.shape[0], L, 2))
     for p in range(poses.shape[0]):
         for b in range(dirs.shape[0]):
-            out[p * dirs.shape[0] + b] = profile_2d(grid, poses[p], dirs[b], L)
+            out[p * dirs.shape[0] + b] = profile_2d(grid, poses[p], dirs[b], L, max_range)
     return out
 
 

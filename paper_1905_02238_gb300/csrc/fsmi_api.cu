@@ -323,16 +323,26 @@ fsmi_status fsmi_update_map_2d(float *map, int W, int H, const int32_t *poses, i
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
-fsmi_status fsmi_profiles_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
-                             const int32_t *beam_ids, long long N, uint16_t *out, fsmi_stream_t stream)
+// samples kept by a profile cut at max_range: i with i + 1/2 < max_range (all 256 if max_range <= 0)
+static int profile_keep(float max_range)
 {
-    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || N < 0) return FSMI_ERR_ARG;
+    if (!(max_range > 0.0f)) return 256;
+    const double k = ceil((double)max_range - 0.5);
+    return k < 0.0 ? 0 : (k > 256.0 ? 256 : (int)k);
+}
+
+fsmi_status fsmi_profiles_2d(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
+                             float max_range, const int32_t *beam_ids, long long N, uint16_t *out,
+                             fsmi_stream_t stream)
+{
+    if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || N < 0 || max_range != max_range) return FSMI_ERR_ARG;
     if (!beam_ids && N != (long long)P * B) return FSMI_ERR_ARG;
     if (N == 0) return FSMI_OK;
     if (!map || !poses || !dirs || !out || B == 0) return FSMI_ERR_ARG;
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
-    cudaError_t e = launch_profiles(map, W, H, poses, P, dirs, B, beam_ids, N, out, sp, (cudaStream_t)stream);
+    cudaError_t e = launch_profiles(map, W, H, poses, P, dirs, B, profile_keep(max_range), beam_ids, N, out, sp,
+                                    (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 
@@ -379,10 +389,11 @@ fsmi_status fsmi_surrogate_cast(const float *params, uint16_t *wbf16, fsmi_strea
 }
 
 fsmi_status fsmi_surrogate_predict(const float *params, const uint16_t *wbf16, const float *map, int W, int H,
-                                   const int32_t *poses, int P, const int32_t *dirs, int B, const uint16_t *x,
-                                   long long N, float *pred, void *ws, size_t ws_bytes, fsmi_stream_t stream)
+                                   const int32_t *poses, int P, const int32_t *dirs, int B, float max_range,
+                                   const uint16_t *x, long long N, float *pred, void *ws, size_t ws_bytes,
+                                   fsmi_stream_t stream)
 {
-    if (!params || !wbf16 || !pred) return FSMI_ERR_ARG;
+    if (!params || !wbf16 || !pred || max_range != max_range) return FSMI_ERR_ARG;
     if (map) {
         if (!grid_ok(W) || !grid_ok(H) || P < 0 || B < 0 || (P > 0 && B > 0 && (!poses || !dirs))) return FSMI_ERR_ARG;
         N = (long long)P * B;
@@ -393,8 +404,8 @@ fsmi_status fsmi_surrogate_predict(const float *params, const uint16_t *wbf16, c
     if (!ws || !aligned16(ws) || ws_bytes < surrogate_infer_bytes(N)) return FSMI_ERR_WORKSPACE;
     int *sp = status_ptr();
     if (!sp) return cuda_fail(cudaGetLastError());
-    cudaError_t e = launch_surrogate_infer(map, W, H, poses, dirs, B, x, N, wbf16, params, pred, ws, sp,
-                                           (cudaStream_t)stream);
+    cudaError_t e = launch_surrogate_infer(map, W, H, poses, dirs, B, profile_keep(max_range), x, N, wbf16, params,
+                                           pred, ws, sp, (cudaStream_t)stream);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
 }
 

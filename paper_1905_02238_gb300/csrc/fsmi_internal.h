@@ -119,16 +119,17 @@ cudaError_t prepare_mixed();
 // learned surrogate (fsmi_surrogate.cu)
 size_t surrogate_train_floats(int N);
 size_t surrogate_infer_bytes(long long N);
+// profiles keep samples i < keep (the rest read as outside the map)
 cudaError_t launch_profiles(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
-                            const int32_t *beam_ids, long long N, void *out, int *status, cudaStream_t s);
+                            int keep, const int32_t *beam_ids, long long N, void *out, int *status, cudaStream_t s);
 cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, const void *x, const float *y, int N,
                                        float *grad, float *loss, float *pred_out, float *ws, cudaStream_t s);
 cudaError_t launch_surrogate_adam(float *p, float *m, float *v, const float *g, float lr, float b1, float b2, float eps,
                                   int t, void *wbf16, cudaStream_t s);
 cudaError_t launch_surrogate_cast(const float *p, void *wbf16, cudaStream_t s);
 cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t *poses, const int32_t *dirs, int B,
-                                   const void *x, long long N, const void *wbf16, const float *params, float *pred,
-                                   void *ws, int *status, cudaStream_t s);
+                                   int keep, const void *x, long long N, const void *wbf16, const float *params,
+                                   float *pred, void *ws, int *status, cudaStream_t s);
 cudaError_t launch_topk(const float *v, int n, int k, int32_t *idx, cudaStream_t s);
 cudaError_t launch_gather_rows(const int32_t *src, long long nrows, int width, const int32_t *idx, int k,
                                int32_t *dst, int *status, cudaStream_t s);

@@ -65,8 +65,8 @@ __device__ __forceinline__ void beam_dir_2d(const int32_t *pose, const int32_t *
 // one warp per beam: out[n][i] = (o, inside) as BF16 pairs
 __global__ void __launch_bounds__(256)
     k_profiles(const float *__restrict__ map, int W, int H, const int32_t *__restrict__ poses,
-               const int32_t *__restrict__ dirs, int B, long long nbeams, const int32_t *__restrict__ beam_ids,
-               long long N, __nv_bfloat162 *__restrict__ out, int *status)
+               const int32_t *__restrict__ dirs, int B, int keep, long long nbeams,
+               const int32_t *__restrict__ beam_ids, long long N, __nv_bfloat162 *__restrict__ out, int *status)
 {
     const int lane = lane_id();
     const long long wpb = blockDim.x >> 5;
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(256)
         int dx, dy;
         beam_dir_2d(pose, dirs + 2 * (id % B), dx, dy);
         for (int i = lane; i < kL; i += 32) {
-            float o, in;
-            sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, o, in);
+            float o = 0.0f, in = 0.0f;  // beyond the range: outside
+            if (i < keep) sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, o, in);
             out[n * kL + i] = __floats2bfloat162_rn(o, in);
         }
     }
@@ -576,7 +576,7 @@ __device__ void conv_stack(uint4 *act1, uint4 *reg, const uint4 *zero, const bf1
 // n % B) or given (x [N][256] bf16 pairs). h0 [N][1024] bf16.
 __global__ void __launch_bounds__(kConvWarps * 32)
     k_conv_infer(const float *__restrict__ map, int W, int H, const int32_t *__restrict__ poses,
-                 const int32_t *__restrict__ dirs, int B, const __nv_bfloat162 *__restrict__ xg, long long N,
+                 const int32_t *__restrict__ dirs, int B, int keep, const __nv_bfloat162 *__restrict__ xg, long long N,
                  const bf16 *__restrict__ w, const float *__restrict__ params, bf16 *__restrict__ h0,
                  unsigned long long *queue)
 {
@@ -612,8 +612,8 @@ __global__ void __launch_bounds__(kConvWarps * 32)
             int dx, dy;
             beam_dir_2d(pose, dirs + 2 * (n % B), dx, dy);
             for (int i = lane; i < kL; i += 32) {
-                float o, in;
-                sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, o, in);
+                float o = 0.0f, in = 0.0f;  // beyond the range: outside
+                if (i < keep) sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, o, in);
                 xs[i] = __floats2bfloat162_rn(o, in);
             }
         } else {
@@ -947,10 +947,10 @@ size_t surrogate_train_floats(int N)
 }
 
 cudaError_t launch_profiles(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
-                            const int32_t *beam_ids, long long N, void *out, int *status, cudaStream_t s)
+                            int keep, const int32_t *beam_ids, long long N, void *out, int *status, cudaStream_t s)
 {
     if (N <= 0) return cudaSuccess;
-    k_profiles<<<grid_cap((N + 7) / 8), 256, 0, s>>>(map, W, H, poses, dirs, B, (long long)P * B, beam_ids, N,
+    k_profiles<<<grid_cap((N + 7) / 8), 256, 0, s>>>(map, W, H, poses, dirs, B, keep, (long long)P * B, beam_ids, N,
                                                      (__nv_bfloat162 *)out, status);
     return cudaGetLastError();
 }
@@ -1088,8 +1088,8 @@ cudaError_t encode_bf16_2d(CUtensorMap *map, const void *ptr, unsigned long long
 }  // namespace
 
 cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t *poses, const int32_t *dirs, int B,
-                                   const void *x, long long N, const void *wbf16, const float *params, float *pred,
-                                   void *ws, int *status, cudaStream_t s)
+                                   int keep, const void *x, long long N, const void *wbf16, const float *params,
+                                   float *pred, void *ws, int *status, cudaStream_t s)
 {
     if (N <= 0) return cudaSuccess;
     const bf16 *w = (const bf16 *)wbf16;
@@ -1106,7 +1106,7 @@ cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t
     if (e != cudaSuccess) return e;
     long long grid = (long long)sm_count() * occ;
     if (grid > (N + kConvWarps - 1) / kConvWarps) grid = (N + kConvWarps - 1) / kConvWarps;
-    k_conv_infer<<<(unsigned)grid, kConvWarps * 32, smem_conv, s>>>(map, W, H, poses, dirs, B,
+    k_conv_infer<<<(unsigned)grid, kConvWarps * 32, smem_conv, s>>>(map, W, H, poses, dirs, B, keep,
                                                                      (const __nv_bfloat162 *)x, N, w, params, h0, queue);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

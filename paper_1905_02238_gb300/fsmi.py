@@ -162,14 +162,14 @@ def load():
             "fsmi_best_trajectory": [p, p, i, p, i, p, p, p],
             "fsmi_scan_sums": [p, ll, i, p, p],
             "fsmi_update_map_2d": [p, i, i, p, i, p, i, p, P, p, sz, p],
-            "fsmi_profiles_2d": [p, i, i, p, i, p, i, p, ll, p, p],
+            "fsmi_profiles_2d": [p, i, i, p, i, p, i, ctypes.c_float, p, ll, p, p],
             "fsmi_eval_mixed": [p, i, i, p, i, p, i, P, p, i, p, i, p, i, P, p, i, ll, p, p, p, sz, p],
             "fsmi_surrogate_workspace_size": [i, ll, ctypes.POINTER(ctypes.c_size_t)],
             "fsmi_surrogate_loss_grad": [p, p, p, p, i, p, p, p, p, sz, p],
             "fsmi_surrogate_adam": [p, p, p, p, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i, p,
                                     p],
             "fsmi_surrogate_cast": [p, p, p],
-            "fsmi_surrogate_predict": [p, p, p, i, i, p, i, p, i, p, ll, p, p, sz, p],
+            "fsmi_surrogate_predict": [p, p, p, i, i, p, i, p, i, ctypes.c_float, p, ll, p, p, sz, p],
             "fsmi_topk": [p, i, i, p, p],
             "fsmi_gather_rows": [p, ll, i, p, i, p, p],
             "fsmi_device_status": [p, ctypes.POINTER(ctypes.c_int)],
@@ -643,8 +643,9 @@ class Graph:
 
 # ---- learned surrogate ------------------------------------------------------------------------------
 
-def profiles_2d(grid, poses, dirs, beam_ids=None, out=None) -> torch.Tensor:
-    """fsmi_profiles_2d -> bfloat16 [N][256][2] beam profiles (all P*B beams, or beam_ids)."""
+def profiles_2d(grid, poses, dirs, beam_ids=None, out=None, max_range: float = 0.0) -> torch.Tensor:
+    """fsmi_profiles_2d -> bfloat16 [N][256][2] beam profiles (all P*B beams, or beam_ids); samples
+    at distance i + 1/2 >= max_range read as outside the map (max_range <= 0: all 256)."""
     lib = load()
     m = _Marshal(grid, poses, dirs, beam_ids)
     g = m.arg(grid, torch.float32, "grid", 2)
@@ -655,7 +656,7 @@ def profiles_2d(grid, poses, dirs, beam_ids=None, out=None) -> torch.Tensor:
     if out is None or m.host:
         out = torch.empty((N, SURR_L, 2), dtype=torch.bfloat16, device=m.dev)
     _raise(lib.fsmi_profiles_2d(_ptr(g), g.shape[1], g.shape[0], _ptr(ps), ps.shape[0], _ptr(ds), ds.shape[0],
-                                _ptr(ids), N, _ptr(out), _stream()), "fsmi_profiles_2d")
+                                float(max_range), _ptr(ids), N, _ptr(out), _stream()), "fsmi_profiles_2d")
     return m.out(out)
 
 
@@ -711,9 +712,10 @@ def surrogate_cast(params, wbf16):
     _raise(lib.fsmi_surrogate_cast(_ptr(params), _ptr(wbf16), _stream()), "fsmi_surrogate_cast")
 
 
-def surrogate_predict(params, wbf16, grid=None, poses=None, dirs=None, x=None, out=None, ws=None) -> torch.Tensor:
+def surrogate_predict(params, wbf16, grid=None, poses=None, dirs=None, x=None, out=None, ws=None,
+                      max_range: float = 0.0) -> torch.Tensor:
     """fsmi_surrogate_predict on the tensor cores: every beam of every pose on `grid` (profiles sampled
-    in the kernel) -> float32 [P*B], or given profiles x [N][256][2] -> [N]."""
+    in the kernel, cut at max_range) -> float32 [P*B], or given profiles x [N][256][2] -> [N]."""
     lib = load()
     _dev_tensor(params, torch.float32, "params", SURR_NPARAMS)
     _dev_tensor(wbf16, torch.bfloat16, "wbf16", SURR_NPARAMS)
@@ -723,11 +725,11 @@ def surrogate_predict(params, wbf16, grid=None, poses=None, dirs=None, x=None, o
         ps = _dev_tensor(poses, torch.int32, "poses")
         ds = _dev_tensor(dirs, torch.int32, "dirs")
         N = ps.shape[0] * ds.shape[0]
-        args = (_ptr(g), g.shape[1], g.shape[0], _ptr(ps), ps.shape[0], _ptr(ds), ds.shape[0], None, 0)
+        args = (_ptr(g), g.shape[1], g.shape[0], _ptr(ps), ps.shape[0], _ptr(ds), ds.shape[0], float(max_range), None, 0)
     else:
         xx = _dev_tensor(x, torch.bfloat16, "x")
         N = xx.shape[0]
-        args = (None, 0, 0, None, 0, None, 0, _ptr(xx), N)
+        args = (None, 0, 0, None, 0, None, 0, 0.0, _ptr(xx), N)
     if out is None:
         if _capturing():
             raise FsmiError("inside a graph capture pass a preallocated `out`")

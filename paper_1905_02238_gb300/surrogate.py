@@ -9,6 +9,7 @@ draws the training batches' beam indices (numpy, seeded) and keeps the parameter
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass
 
@@ -43,20 +44,24 @@ def init_params(seed: int) -> np.ndarray:
 class TrainingMap:
     grid: torch.Tensor    # float32 [H][W]
     poses: torch.Tensor   # int32 [P][4]
-    labels: torch.Tensor  # float32 [P * B], exact FSMI of every beam
+    labels: torch.Tensor  # float32 [P * B], exact FSMI of every beam at max_range
+    max_range: float = 0.0  # the labels' beam range; the profiles are cut there (0: all 256 samples)
 
 
-def label_maps(n_maps: int, poses_per_map: int, dirs, prm: fsmi.Params, seed: int = 100, size: int = 2048):
+def label_maps(n_maps: int, poses_per_map: int, dirs, prm: fsmi.Params, seed: int = 100, size: int = 2048,
+               ranges=None):
     """Config-2 style maps (office generator, seeds seed, seed+1, ...) with every beam of every pose
-    labelled by exact FSMI on the GPU."""
+    labelled by exact FSMI on the GPU, at prm.max_range or, with `ranges`, map k at ranges[k % len]
+    (ranges up to 256, the samples of a profile)."""
     out = []
     d = dirs if isinstance(dirs, torch.Tensor) else torch.from_numpy(dirs).cuda()
     for k in range(n_maps):
         grid, poses, _ = synth.config2(n_poses=poses_per_map, size=size, seed=seed + k, pose_seed=seed + 1000 + k)
         g = torch.from_numpy(grid).cuda()
         p = torch.from_numpy(poses).cuda()
-        lab = fsmi.eval_2d(g, p, d, prm).reshape(-1)
-        out.append(TrainingMap(g, p, lab))
+        r = float(ranges[k % len(ranges)]) if ranges else float(prm.max_range)
+        lab = fsmi.eval_2d(g, p, d, dataclasses.replace(prm, max_range=r)).reshape(-1)
+        out.append(TrainingMap(g, p, lab, r))
     return out
 
 
@@ -126,7 +131,7 @@ class Surrogate:
             k = int(which[i])
             mp = maps[k]
             ids = ids_dev[i]
-            fsmi.profiles_2d(mp.grid, mp.poses, d, beam_ids=ids, out=x)
+            fsmi.profiles_2d(mp.grid, mp.poses, d, beam_ids=ids, out=x, max_range=mp.max_range)
             fsmi.gather_rows(scaled[k].view(torch.int32).reshape(-1, 1), ids, out=y.view(torch.int32).reshape(-1, 1))
             fsmi.surrogate_loss_grad(self.params, self.wbf16, x, y, self.grad, self.loss, ws=ws)
             self.step += 1
@@ -138,13 +143,14 @@ class Surrogate:
         return losses
 
     # ---- inference ------------------------------------------------------------------------------
-    def predict(self, grid, poses, dirs, out=None, ws=None) -> torch.Tensor:
+    def predict(self, grid, poses, dirs, out=None, ws=None, max_range: float = 0.0) -> torch.Tensor:
         """Network outputs ((predicted MI - shift) / scale) of every beam of every pose, [P * B]
-        (tensor cores)."""
+        (tensor cores), for beams cut at max_range (0: all 256 samples)."""
         n = poses.shape[0] * dirs.shape[0]
         if ws is None:
             ws = self._workspace(1, n)
-        pred = fsmi.surrogate_predict(self.params, self.wbf16, grid=grid, poses=poses, dirs=dirs, out=out, ws=ws)
+        pred = fsmi.surrogate_predict(self.params, self.wbf16, grid=grid, poses=poses, dirs=dirs, out=out, ws=ws,
+                                      max_range=max_range)
         return pred
 
 
@@ -170,7 +176,7 @@ class Prescreen:
 
     def run(self) -> torch.Tensor:
         """Pose indices [top] (int32, device): the best by exact FSMI among the surrogate's top k."""
-        self.net.predict(self.grid, self.poses, self.dirs, out=self.pred, ws=self.ws_pred)
+        self.net.predict(self.grid, self.poses, self.dirs, out=self.pred, ws=self.ws_pred, max_range=self.prm.max_range)
         fsmi.scan_sums_into(self.pred.view(self.poses.shape[0], self.dirs.shape[0]), self.score)
         fsmi.topk(self.score, self.k, out=self.cand)
         fsmi.gather_rows(self.poses, self.cand, out=self.sel)

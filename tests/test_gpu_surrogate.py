@@ -53,6 +53,9 @@ def test_profiles_bit_exact():
     ids = np.array([5, 0, 77, 239, 3], np.int32)
     xs = fsmi.profiles_2d(_cuda(grid), _cuda(poses), _cuda(dirs), beam_ids=_cuda(ids)).float().cpu().numpy()
     np.testing.assert_array_equal(xs, x[ids])
+    for R in (0.5, 0.51, 17.0, 63.5, 100.25, 255.5, 300.0):  # profiles cut at a range
+        xr = fsmi.profiles_2d(_cuda(grid), _cuda(poses), _cuda(dirs), max_range=R).float().cpu().numpy()
+        np.testing.assert_array_equal(xr, S.bf16_round(S.profiles_2d(grid, poses, dirs, max_range=R)))
 
 
 def _profiles(grid, poses, dirs):
@@ -142,6 +145,11 @@ def test_tensor_core_inference_matches_oracle():
     # profiles sampled inside the kernel give the same floats
     got_map = fsmi.surrogate_predict(params, wb, grid=_cuda(grid), poses=_cuda(poses), dirs=_cuda(dirs))
     np.testing.assert_array_equal(got_map.cpu().numpy(), got.astype(np.float32))
+    # ... and cut at a range, the same floats as the cut profiles given as input
+    xr = fsmi.profiles_2d(_cuda(grid), _cuda(poses), _cuda(dirs), max_range=37.5)
+    got_r = fsmi.surrogate_predict(params, wb, grid=_cuda(grid), poses=_cuda(poses), dirs=_cuda(dirs), max_range=37.5)
+    np.testing.assert_array_equal(got_r.cpu().numpy(), fsmi.surrogate_predict(params, wb, x=xr).cpu().numpy())
+    assert not torch.equal(got_r, got_map)
     # many row tiles per persistent block and a ragged last tile: every row equals its own value
     # from the small launch (rows are independent and each row's sums run in a fixed order)
     idx = np.random.default_rng(11).integers(0, x.shape[0], 152 * 128 * 3 + 77)

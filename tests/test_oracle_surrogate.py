@@ -87,6 +87,22 @@ def test_profile_is_exact_geometry():
     assert np.all(prof[16:] == 0)
 
 
+def test_profile_range_cut_is_a_map_that_ends_there():
+    # a beam cut at range R sees the cells of a map cropped just past R: along +x from (3.5, 7.5)
+    # sample i lies at x = 4 + i, inside the range when i + 1/2 < R
+    g = np.arange(30 * 30, dtype=np.float32).reshape(30, 30) / 900.0 + 0.01
+    pose, u = synth.pose_2d(3.5, 7.5, 0.0), synth.q30(np.array([1.0, 0.0]))
+    for R in (0.4, 0.5, 0.6, 7.0, 7.5, 7.51, 12.25, 25.5):
+        cut = S.profile_2d(g, pose, u, 40, max_range=R)
+        keep = int(np.ceil(R - 0.5))  # samples i with i + 1/2 < R
+        cropped = S.profile_2d(g[:, :4 + keep], pose, u, 40)
+        np.testing.assert_array_equal(cut, cropped)
+        full = S.profile_2d(g, pose, u, 40)
+        np.testing.assert_array_equal(cut[:keep], full[:keep])
+        assert np.all(cut[keep:] == 0)
+    np.testing.assert_array_equal(S.profile_2d(g, pose, u, 40, max_range=0.0), S.profile_2d(g, pose, u, 40))
+
+
 def test_bf16_round_matches_torch():
     rng = np.random.default_rng(6)
     a = np.concatenate([rng.normal(0, 10, 1000), rng.normal(0, 1e-3, 1000), [0.0, -0.0, 1.0, 3.0e38, -3.4e38]])
