@@ -244,10 +244,37 @@ __device__ __forceinline__ float exact_window_sum(const float *sl, const float *
     return r;
 }
 
+// Boundary terms m in [a, b) on one side of a first-hit cell's centre, added to acc: before the
+// centre (NEG) -dC_m T(mu - l_m), after it +dC_m T(l_m - mu). Pairs at even m go through the
+// packed tail; an odd first or last boundary is evaluated alone.
+template <bool NEG>
+__device__ __forceinline__ float side_terms(const float *sl, const float *sdc, int a, int b, float mu, float acc)
+{
+    int m = a;
+    if (m < b && (m & 1)) {
+        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(NEG ? mu - sl[m] : sl[m] - mu), acc);
+        ++m;
+    }
+    const f32x2 mu2 = pack2(mu, mu);
+    f32x2 acc2 = pack2(0.0f, 0.0f);
+#pragma unroll 2
+    for (; m + 1 < b; m += 2) {
+        const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
+        const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
+        acc2 = fma2(dc, gauss_tail2p<NEG>(NEG ? sub2(mu2, L) : sub2(L, mu2)), acc2);
+    }
+    float a0, a1;
+    unpack2(acc2, a0, a1);
+    acc += a0 + a1;
+    if (m < b) acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(NEG ? mu - sl[m] : sl[m] - mu), acc);
+    return acc;
+}
+
 // Approx-FSMI: for slot j the band k in [klo, khi] = [j - Delta, j + Delta] n [0, n-1] (0-based),
-// i.e. boundaries m in [klo, khi + 1] with C' = C on the band and 0 outside it.
-__device__ __forceinline__ float approx_sum(const float *sl, const float *sc, const float *sp, int n, bool e0,
-                                            float pe0, float mu0, int D)
+// i.e. boundaries m in [klo, khi + 1] with C' = C on the band and 0 outside it: the band edges
+// weigh C_klo and -C_khi, the interior C_m - C_{m-1} (sdc).
+__device__ __forceinline__ float approx_sum(const float *sl, const float *sc, const float *sdc, const float *sp,
+                                            int n, bool e0, float pe0, float mu0, int D)
 {
     const int nslots = n + (e0 ? 1 : 0);
     float r = 0.0f;
@@ -269,11 +296,13 @@ __device__ __forceinline__ float approx_sum(const float *sl, const float *sc, co
         }
         const int mid = (j < n) ? j + 1 : 0;  // boundaries m < mid lie before the centre
         float acc = 0.0f;
-        for (int m = klo; m <= khi + 1; ++m) {
-            const float cm = (m <= khi) ? sc[m] : 0.0f;
-            const float cm1 = (m > klo) ? sc[m - 1] : 0.0f;
-            const float dc = cm - cm1;
-            acc = fmaf(m < mid ? -dc : dc, gauss_tail(sl[m] - mu), acc);
+        if (klo <= khi) {  // an empty band (e_0 with Delta = 0) adds nothing
+            const float clo = sc[klo], chi = sc[khi];
+            acc = fmaf(klo < mid ? -clo : clo, gauss_tail(sl[klo] - mu), acc);
+            const int split = min(max(mid, klo + 1), khi + 1);
+            acc = side_terms<true>(sl, sdc, klo + 1, split, mu, acc);
+            acc = side_terms<false>(sl, sdc, split, khi + 1, mu, acc);
+            acc = fmaf(khi + 1 < mid ? chi : -chi, gauss_tail(sl[khi + 1] - mu), acc);
         }
         r = fmaf(Pj, Cj + acc, r);
     }
@@ -406,7 +435,11 @@ __device__ __forceinline__ float beam_sum(const DevParams &p, int n, float *sl, 
             I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0,
                                  (p.flags & FSMI_FLAG_FULL_WINDOW) ? kTailCut : kTailCutDefault);
         }
-        if (VAR == FSMI_APPROX) I = approx_sum(sl, sc, sp, n, e0, pe0, mu0, p.trunc);
+        if (VAR == FSMI_APPROX) {
+            for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
+            __syncwarp();
+            I = approx_sum(sl, sc, sx, sp, n, e0, pe0, mu0, p.trunc);
+        }
         if (VAR == FSMI_UNIFORM) I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
         I = warp_sum(I);
     }

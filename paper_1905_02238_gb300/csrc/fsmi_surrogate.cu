@@ -45,12 +45,13 @@ __device__ __forceinline__ float bf(const bf16 *p, long long i) { return __bfloa
 
 // Sample i of a beam: the cell holding o + (i + 1/2) d, the floor of the Q31 position
 // (o << 15) + (2i + 1) d (d the Q30 beam direction).
+// sample i (of the first `keep`; later ones read as outside the map)
 __device__ __forceinline__ void sample_2d(const float *map, int W, int H, long long ox, long long oy, int dx, int dy,
-                                          int i, float &o, float &in)
+                                          int i, int keep, float &o, float &in)
 {
     const long long px = ((ox << 15) + (long long)(2 * i + 1) * dx) >> 31;
     const long long py = ((oy << 15) + (long long)(2 * i + 1) * dy) >> 31;
-    const bool inside = px >= 0 && px < W && py >= 0 && py < H;
+    const bool inside = i < keep && px >= 0 && px < W && py >= 0 && py < H;
     o = inside ? __ldg(map + py * W + px) : 0.0f;
     in = inside ? 1.0f : 0.0f;
 }
@@ -81,8 +82,8 @@ __global__ void __launch_bounds__(256)
         int dx, dy;
         beam_dir_2d(pose, dirs + 2 * (id % B), dx, dy);
         for (int i = lane; i < kL; i += 32) {
-            float o = 0.0f, in = 0.0f;  // beyond the range: outside
-            if (i < keep) sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, o, in);
+            float o, in;
+            sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, keep, o, in);
             out[n * kL + i] = __floats2bfloat162_rn(o, in);
         }
     }
@@ -612,8 +613,8 @@ __global__ void __launch_bounds__(kConvWarps * 32)
             int dx, dy;
             beam_dir_2d(pose, dirs + 2 * (n % B), dx, dy);
             for (int i = lane; i < kL; i += 32) {
-                float o = 0.0f, in = 0.0f;  // beyond the range: outside
-                if (i < keep) sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, o, in);
+                float o, in;
+                sample_2d(map, W, H, pose[0], pose[1], dx, dy, i, keep, o, in);
                 xs[i] = __floats2bfloat162_rn(o, in);
             }
         } else {
