@@ -56,6 +56,23 @@ def test_host_only_entry_points(lib_path):
     assert lib.fsmi_workspace_size(9, 100, None, ctypes.byref(b)) == 1
 
 
+def test_range_argument_is_checked_before_any_launch(lib_path):
+    # a NaN range is an argument error, found on the host (no pointer is touched, nothing launched)
+    lib = ctypes.CDLL(lib_path)
+    p, i, f, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong
+    lib.fsmi_profiles_2d.argtypes = [p, i, i, p, i, p, i, f, p, ll, p, p]
+    lib.fsmi_surrogate_predict.argtypes = [p, p, p, i, i, p, i, p, i, f, p, ll, p, p, ctypes.c_size_t, p]
+    nan = float("nan")
+    # with nothing to do these return ok for a finite range, so only the range check can fail them
+    assert lib.fsmi_profiles_2d(None, 16, 16, None, 0, None, 1, 5.0, None, 0, None, None) == 0
+    assert lib.fsmi_profiles_2d(None, 16, 16, None, 0, None, 1, nan, None, 0, None, None) == 1
+    dummy = ctypes.c_void_p(16)  # never dereferenced: no beams
+    assert lib.fsmi_surrogate_predict(dummy, dummy, None, 0, 0, None, 0, None, 0, 5.0, None, 0, dummy, None, 0,
+                                      None) == 0
+    assert lib.fsmi_surrogate_predict(dummy, dummy, None, 0, 0, None, 0, None, 0, nan, None, 0, dummy, None, 0,
+                                      None) == 1
+
+
 class _Sched(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("warps_per_block", "blocks_per_sm", "queue_chunk", "cell_runlen")]
 
