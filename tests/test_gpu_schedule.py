@@ -237,6 +237,51 @@ def test_graph_replay_of_sets_and_3d():
     assert fsmi.device_status() == 0
 
 
+def test_benchmark_launch_configuration_against_oracle():
+    # exactly what the benchmark times: config 2 at full size with the per-cell gains workspace,
+    # the autotuned 2D schedule and one CUDA-graph replay per step; config 3 likewise for the 3D
+    # batch. The replayed results equal a plain call bit for bit and match the oracle on samples.
+    grid, poses, dirs = synth.config2()
+    g, p, d = _cuda(grid), _cuda(poses), _cuda(dirs)
+    gp = fsmi.Params(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0)
+    op = oracle.Params(variant=oracle.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0)
+    out = torch.empty((1024, 360), dtype=torch.float32, device="cuda")
+    ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device="cuda")
+    saved2, saved3 = fsmi.get_schedule(K2), fsmi.get_schedule(KR)
+    try:
+        fsmi.autotune(K2, lambda: fsmi.eval_2d(g, p, d, gp, out=out, ws=ws), reps=1)
+        graph = fsmi.Graph(lambda: fsmi.eval_2d(g, p, d, gp, out=out, ws=ws))
+        out.fill_(-1.0)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        graph.close()
+        plain = fsmi.eval_2d(g, p, d, gp)
+        np.testing.assert_array_equal(_bits(out), _bits(plain))
+        rows = [5, 517, 1000]
+        assert_mi_close(out.cpu().numpy()[rows], oracle.eval_2d(grid, poses[rows], dirs, op), "config2 graph")
+
+        vox, vposes, vdirs = synth.config3()
+        v, vp, vd = _cuda(vox), _cuda(vposes), _cuda(vdirs)
+        gp3 = fsmi.Params(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=384.0, run_cap=64)
+        op3 = oracle.Params(variant=oracle.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=384.0, run_cap=64)
+        out3 = torch.empty((64, vd.shape[0]), dtype=torch.float32, device="cuda")
+        ws3 = torch.empty(fsmi.QUEUE_BYTES, dtype=torch.uint8, device="cuda")
+        fsmi.autotune(KR, lambda: fsmi.eval_3d(v, vp, vd, gp3, out=out3, ws=ws3), reps=1)
+        graph3 = fsmi.Graph(lambda: fsmi.eval_3d(v, vp, vd, gp3, out=out3, ws=ws3))
+        graph3.replay()
+        torch.cuda.synchronize()
+        graph3.close()
+        np.testing.assert_array_equal(_bits(out3), _bits(fsmi.eval_3d(v, vp, vd, gp3)))
+        sel_r = np.arange(0, vd.shape[0], 257)
+        ref3, _ = oracle.eval_3d(vox, vposes[[3, 40]], vdirs[sel_r], op3)
+        assert_mi_close(out3.cpu().numpy()[np.ix_([3, 40], sel_r)], ref3, "config3 graph")
+    finally:
+        fsmi.set_schedule(K2, saved2)
+        fsmi.set_schedule(KR, saved3)
+    assert fsmi.device_status() == 0
+
+
 def test_autotune_picks_a_candidate_and_sets_it():
     grid, poses = _office(256, 32, seed=21)
     g, p, d = _cuda(grid), _cuda(poses), _cuda(synth.beam_dirs_2d(180))
