@@ -236,6 +236,12 @@ def rle_crossover_leg(dev):
     l = torch.arange(n, dtype=torch.float32, device=dev).repeat(nb)
     lend = torch.full((nb,), float(n), dtype=torch.float32, device=dev)
     ws = torch.empty(fsmi.QUEUE_BYTES, dtype=torch.uint8, device=dev)
+    # the paper's pairing (Table 2): Approx-FSMI (Delta = 3) on the cells vs Approx-FSMI-RLE on the runs
+    prm_ac = fsmi.Params(variant=fsmi.APPROX, trunc_delta=3, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP,
+                         max_range=float(n))
+    prm_ar = fsmi.Params(variant=fsmi.APPROX, trunc_delta=3, sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP,
+                         max_range=float(n), run_cap=64, g_kernel=fsmi.G_ERF)
+    paper_ratio = {1: 0.2, 2: 0.7, 4: 1.8, 8: 4.6, 16: 7.4, 32: 11.2, 64: 16.5, 128: 24.4}  # Table 2, one CPU core
     rows = []
     for L in (1, 2, 4, 8, 16, 32, 64, 128):
         ng = -(-n // L)
@@ -258,13 +264,19 @@ def rle_crossover_leg(dev):
         finally:
             fsmi.set_schedule(fsmi.KIND_RLE, saved)
         diff = float(((orr - oc).abs() / oc.abs().clamp_min(1e-30)).max().item())
+        ms_ac = _time_ms(lambda: fsmi.eval_beams(off, o, l, lend, prm_ac, out=oc, ws=ws), reps=10)
+        ms_ar = _time_ms(lambda: fsmi.eval_rle(roff, ro, rl, prm_ar, out=orr, ws=ws), reps=10)
         rows.append({"L": L, "runs_per_beam": len(split), "cells_ms": ms_c, "rle_run_pairs_ms": ms_r,
-                     "rle_default_ms": ms_auto, "run_pairs_speedup": ms_c / ms_r, "max_rel_diff": diff})
+                     "rle_default_ms": ms_auto, "run_pairs_speedup": ms_c / ms_r, "max_rel_diff": diff,
+                     "approx_cells_ms": ms_ac, "approx_rle_ms": ms_ar, "approx_rle_speedup": ms_ac / ms_ar,
+                     "paper_approx_rle_speedup": paper_ratio[L]})
     faster = [r["L"] for r in rows if r["rle_run_pairs_ms"] < r["cells_ms"]]
     return {"workload": "100,000 beams x 256 unit cells in groups of L cells of equal U(0,1) occupancy; exact FSMI "
                         "per cell (fsmi_eval_beams) vs FSMI-RLE on the runs (fsmi_eval_rle, unit-cell Gaussian "
                         "mass; run pairs always, and with the default schedule that takes the cell form for "
-                        "mean run lengths below 32)",
+                        "mean run lengths below 32); and the paper's pairing, Approx-FSMI (Delta = 3) per cell "
+                        "vs Approx-FSMI-RLE (Theorem 5) on the runs, beside the paper's ratios (Table 2: "
+                        "Xeon E5-2695, one core, 1000 beams)",
             "rows": rows, "run_pairs_faster_from_L": faster[0] if faster else None}
 
 
