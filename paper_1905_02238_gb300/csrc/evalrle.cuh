@@ -338,18 +338,23 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
     }
     int nrun = 0, carried = 0, n = 0;
     unsigned prev_bits = 0u;
+    // Q31 position o + (2i + 1) d of this lane's sample, advanced by 64 d per chunk of 32
+    long long q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = o[a] + (2LL * lane + 1) * d[a];
+    const float inv_cap = 1.0f / (float)cap;
     for (int base = 0; base < nsamp; base += 32) {
         const int i = base + lane;
         bool inb = false;
         float val = 0.0f;
         if (i < nsamp) {
-            const long long k = 2LL * i + 1;
-            const long long px = (o[0] + k * d[0]) >> 31;
-            const long long py = (o[1] + k * d[1]) >> 31;
-            const long long pz = (o[2] + k * d[2]) >> 31;
-            inb = px >= 0 && px < X && py >= 0 && py < Y && pz >= 0 && pz < Z;
+            const long long px = q[0] >> 31, py = q[1] >> 31, pz = q[2] >> 31;
+            inb = (unsigned long long)px < (unsigned long long)X && (unsigned long long)py < (unsigned long long)Y &&
+                  (unsigned long long)pz < (unsigned long long)Z;
             if (inb) val = __ldg(vox + ((pz * Y + py) * X + px));
         }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[a] += 64 * d[a];
         const unsigned m_in = __ballot_sync(kFull, inb);
         const int nvalid = (m_in == kFull) ? 32 : (__ffs(~m_in) - 1);
         const bool valid = lane < nvalid;
@@ -359,7 +364,10 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         const bool newval = valid && (i == 0 || bits != pbits);
         int st = warp_incl_max_int(newval ? i : -1);
         st = max(st, carried);
-        const bool brk = valid && ((i - st) % cap == 0);
+        // a run of equal values splits every cap samples: (i - st) a multiple of cap, found with a
+        // rounded quotient (exact: i - st < 2^20 and cap <= 255) instead of an integer remainder
+        const int rel = i - st;
+        const bool brk = valid && rel - __float2int_rn((float)rel * inv_cap) * cap == 0;
         const unsigned mb = __ballot_sync(kFull, brk);
         if (brk) {
             const int k = nrun + __popc(mb & ((1u << lane) - 1u));
