@@ -41,12 +41,12 @@ RCP_PER_SM_CLK = 16  # SFU rcp.approx results per SM per clock (measured 15.1)
 SFU_CLK_PER_TERM = 1.0 / EX2_PER_SM_CLK + 1.0 / RCP_PER_SM_CLK  # one ex2 and one rcp per tail term
 OPS_PER_TERM = 11  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh): distance,
 #                    square, 1 + p|d|, 5 Horner FMAs, two products, accumulate
-TAIL_CUT = 5.75  # scaled half-width of the exact kernel's default window (csrc/eval2d.cuh)
+TAIL_CUT = 4.81  # scaled half-width of the exact kernel's default window (csrc/eval2d.cuh)
 
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
 # ncu capture (profiles/k_eval_2d_exact_office2048.md), valid only for the kernel sources whose
 # hash is recorded with it; reported as null once those sources change.
-TRAFFIC = {"sources_sha1": "9a82121f527bd7a7abb698a36e2d20e282d38e79", "bytes_per_launch": 110.83e6}
+TRAFFIC = {"sources_sha1": "2addcdbe6381f85814c8bb6d71a4bc8b6b358ddc", "bytes_per_launch": 110.94e6}
 KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb300/csrc/eval2d.cuh",
                   "paper_1905_02238_gb300/csrc/dda2d.cuh", "paper_1905_02238_gb300/csrc/gauss_tail.cuh",
                   "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]

@@ -86,9 +86,9 @@ typedef struct {
 } fsmi_params;
 
 /* Exact 2D FSMI evaluates, for each first-hit cell j, the boundary terms of Theorem 1's pair sum
- * within about 6.8 sigma of the cell's centre: every term beyond weighs less than 2^-37 of its
- * factor |C_m - C_{m-1}|, so the MI differs from the full n(n+1) sweep by far less than FP32
- * resolution (but not bit for bit).
+ * within about 5.7 sigma of the cell's centre: every term beyond weighs less than 2^-27 of its
+ * factor |C_m - C_{m-1}|, so the MI differs from the full n(n+1) sweep by about one FP32 rounding
+ * at most (not bit for bit).
  * FSMI_FLAG_FULL_WINDOW widens the window to every term whose Gaussian tail is non-zero in FP32
  * (about 13.3 sigma; the tail underflows to exactly 0 beyond), which gives the full sweep's result
  * bit for bit; FSMI_FLAG_FULL_SWEEP evaluates all n(n+1) terms (both for verification and timing

@@ -29,6 +29,23 @@ namespace fsmi {
 
 // per-warp shared arrays, in units of `stride` floats: l, C, P, scratch (ids / f_emp / D / dC)
 constexpr int kArrays2D = 4;
+// Padding boundaries before index 0 and after index n + 1 of l and dC (l = -+3e30, dC = 0: their
+// terms are exactly zero), so that the exact window loops can run past a beam's ends.
+constexpr int kPad2D = 32;
+
+// Floats between consecutive arrays for beams of up to nmax cells (n + 2 boundaries + padding).
+__host__ __device__ constexpr int stride_2d(int nmax) { return ((nmax + 2 + kPad2D) + 3) & ~3; }
+// Floats of one warp's arrays: kArrays2D strides and the front padding of l and dC.
+__host__ __device__ constexpr int warp_floats_2d(int stride) { return kArrays2D * stride + 2 * kPad2D; }
+
+// One warp's arrays in its region `base` (16-byte aligned): [pad | l | C | P | pad | scratch].
+__device__ __forceinline__ void carve_2d(float *base, int stride, float *&sl, float *&sc, float *&sp, float *&sx)
+{
+    sl = base + kPad2D;
+    sc = sl + stride;
+    sp = sc + stride;
+    sx = sp + stride + kPad2D;
+}
 // internal variant id of the full n(n+1) exact sweep (FSMI_FLAG_FULL_SWEEP)
 constexpr int kExactFullSweep = 3;
 
@@ -128,11 +145,11 @@ __device__ __forceinline__ float exact_sum(const float *sl, const float *sc, con
 // Largest scaled distance whose tail is not flushed to zero: beyond |d| = 11.3 the factor
 // 2^(-d^2) <= 2^(-127.69) is subnormal and ex2.approx.ftz returns exactly 0, so the term is +-0.
 constexpr float kTailCut = 11.3f;
-// Default window of the exact sum: T(5.75) = 6.4e-12 < 2^-37. Boundaries come at most two per
+// Default window of the exact sum: T(4.81) = 7.4e-9 < 2^-27. Boundaries come at most two per
 // major-axis crossing interval (scaled length >= cs = sqrt(log2 e) / (sigma sqrt 2)), so the terms
-// skipped on one side weigh at most 2 T(5.75) / (1 - 2^(-11.5 cs)) times max |C_m - C_{m-1}|:
-// below 2^-34 of it for sigma <= 20 cells, far under the FP32 rounding of the sums.
-constexpr float kTailCutDefault = 5.75f;
+// skipped on one side weigh at most 2 T(4.81) / (1 - 2^(-9.62 cs)) times max |C_m - C_{m-1}|:
+// below 2^-24 of it (one FP32 ulp) for sigma <= 20 cells, and below 2^-26 for sigma <= 2.
+constexpr float kTailCutDefault = 4.81f;
 
 __device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
 {
@@ -172,15 +189,12 @@ __device__ __forceinline__ int lower_bound_from(const float *a, int N, float x, 
 #endif
 constexpr int kPairUnroll = FSMI_PAIR_UNROLL;  // boundary pairs in flight per lane, exact window loop
 
-__device__ __forceinline__ f32x2 window_terms(const float *sl, const float *sdc, int lo, int hi, int mid, float mu)
+__device__ __forceinline__ f32x2 window_terms(const float *sl, const float *sdc, int m, int nb, int end, int mid, float mu)
 {
-    int m = lo & ~1;
-    const int end = (hi + 1) & ~1;
     const f32x2 mu2 = pack2(mu, mu);
     f32x2 acc = pack2(0.0f, 0.0f);
-    const int nb = min(max(mid & ~1, m), end);  // pairs (m, m + 1) with m + 1 < mid
 #pragma unroll kPairUnroll
-    for (; m < nb; m += 2) {
+    for (; m < nb; m += 2) {  // pairs (m, m + 1) with m + 1 < mid
         const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
         const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
         acc = fma2(dc, gauss_tail2p<true>(sub2(mu2, L)), acc);
@@ -203,11 +217,15 @@ __device__ __forceinline__ f32x2 window_terms(const float *sl, const float *sdc,
     return acc;
 }
 
-// Exact pair sum over the boundaries within the window: for slot j only m with
+// Exact pair sum over the boundaries within the window: for slot j at least the m with
 // |l_m - mu_j| < cut (scaled) are visited, in increasing m. With cut = kTailCut every non-zero
 // term of the full sweep is added in the same order and the FP32 result is the same bit for bit;
-// with kTailCutDefault the terms skipped are below 2^-37 of their weights.
-// sdc[m] = C_m - C_{m-1} for m = 0..n.
+// with kTailCutDefault the terms skipped are below 2^-27 of their weights.
+// The 32 slots of a round run the same number of pairs below and above their centres (the
+// round's longest window on each side): a lane with a shorter window adds the next boundaries
+// beyond it, which are terms of the full sum too (or padding with weight 0), so that no lane
+// leaves the unrolled loops at a different point than the others.
+// sdc[m] = C_m - C_{m-1} for m = 0..n; sl and sdc padded by kPad2D entries on both sides.
 __device__ __forceinline__ float exact_window_sum(const float *sl, const float *sdc, const float *sc,
                                                   const float *sp, int n, bool e0, float pe0, float mu0, float cut)
 {
@@ -218,27 +236,38 @@ __device__ __forceinline__ float exact_window_sum(const float *sl, const float *
     const float span = sl[n] - sl[0];
     const float per = span > 0.0f ? (float)n / span : 0.0f;
     const int half = (int)fminf(cut * per, (float)(n + 1));
+    const int mtop = (n + 1 + kPad2D) & ~1;  // pairs (m, m + 1) stay below n + 2 + kPad2D
     float r = 0.0f;
-    for (int j = lane_id(); j < nslots; j += 32) {
-        float mu, Cj, Pj;
-        int mid;
-        if (j < n) {
-            mu = 0.5f * (sl[j] + sl[j + 1]);
-            Cj = sc[j];
-            Pj = sp[j];
-            mid = j + 1;
-        } else {
-            mu = mu0;
-            Cj = 0.0f;
-            Pj = pe0;
-            mid = 0;
+    for (int jb = 0; jb < nslots; jb += 32) {
+        const int j = jb + lane_id();
+        float mu = 0.0f, Cj = 0.0f, Pj = 0.0f;
+        int mid = 0, m0 = 0, nb = 0, end = 0;
+        if (j < nslots) {
+            if (j < n) {
+                mu = 0.5f * (sl[j] + sl[j + 1]);
+                Cj = sc[j];
+                Pj = sp[j];
+                mid = j + 1;
+            } else {
+                mu = mu0;
+                Pj = pe0;
+            }
+            const int anchor = mid;  // j + 1, or 0 for the no-return slot (centre before l_0)
+            // sl[n + 1] is the first padding boundary (3e30), above every target
+            const int lo = lower_bound_from(sl, n + 1, mu - cut, anchor - half - 2);
+            const int hi = lower_bound_from(sl, n + 1, mu + cut, anchor + half - 1);
+            m0 = lo & ~1;
+            end = (hi + 1) & ~1;
+            nb = min(max(mid & ~1, m0), end);  // pairs (m, m + 1) with m + 1 < mid end here
         }
-        const int anchor = mid;  // j + 1, or 0 for the no-return slot (centre before l_0)
-        // sl[n + 1] is the padding boundary (3e30), above every target
-        const int lo = lower_bound_from(sl, n + 1, mu - cut, anchor - half - 2);
-        const int hi = lower_bound_from(sl, n + 1, mu + cut, anchor + half - 1);
+        const int tn = (nb - m0) >> 1, tp = nb < end ? (end - nb - 2) >> 1 : 0;
+        const int TN = __reduce_max_sync(kFull, tn), TP = __reduce_max_sync(kFull, tp);
+        if (j < nslots) {
+            m0 = max(nb - 2 * TN, -kPad2D);
+            if (nb < end) end = min(nb + 2 + 2 * TP, mtop);
+        }
         float a0, a1;
-        unpack2(window_terms(sl, sdc, lo, hi, mid, mu), a0, a1);
+        unpack2(window_terms(sl, sdc, m0, nb, end, mid, mu), a0, a1);
         r = fmaf(Pj, Cj + (a0 + a1), r);
     }
     return r;
@@ -427,9 +456,11 @@ __device__ __forceinline__ float beam_sum(const DevParams &p, int n, float *sl, 
         if (VAR == kExactFullSweep) I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
         if (VAR == FSMI_EXACT) {
             for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
-            if (lane == 0) {  // padding boundary n + 1 for the even-aligned window pairs
-                sl[n + 1] = 3.0e30f;
-                sx[n + 1] = 0.0f;
+            for (int i = lane; i < kPad2D; i += 32) {  // padding boundaries on both sides, weight 0
+                sl[-1 - i] = -3.0e30f;
+                sx[-1 - i] = 0.0f;
+                sl[n + 1 + i] = 3.0e30f;
+                sx[n + 1 + i] = 0.0f;
             }
             __syncwarp();
             I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0,

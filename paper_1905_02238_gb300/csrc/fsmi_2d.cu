@@ -15,10 +15,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, VAR == kExactFullSweep ? 1 : F
 {
     extern __shared__ float smem[];
     const int lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    float *sl = smem + (size_t)warp * kArrays2D * stride;
-    float *sc = sl + stride;
-    float *sp = sc + stride;
-    float *sx = sp + stride;
+    float *sl, *sc, *sp, *sx;
+    carve_2d(smem + (size_t)warp * warp_floats_2d(stride), stride, sl, sc, sp, sx);
     for_each_item(nbeams, queue, chunk,
                   [&](long long beam) { eval_beam<VAR, SRC>(src, p, beam, sl, sc, sp, sx, out, status); });
 }
@@ -64,8 +62,8 @@ static cudaError_t launch_variant(const Src2D &src, const DevParams &p, long lon
                                   unsigned long long *queue, cudaStream_t s)
 {
     const Schedule &sc = current_schedule(FSMI_KIND_2D);
-    const int stride = ((p.nmax + 2) + 3) & ~3;
-    const size_t per_warp = (size_t)kArrays2D * stride * sizeof(float);
+    const int stride = stride_2d(p.nmax);
+    const size_t per_warp = (size_t)warp_floats_2d(stride) * sizeof(float);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, 0);
     const size_t smem = (size_t)wpb * per_warp;
     auto kern = k_eval_2d<VAR, SRC>;

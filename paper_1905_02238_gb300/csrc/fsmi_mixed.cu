@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     double *gs = (double *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
     rb.gtab = (float *)(gs + rb.ts.K + 1);
     if (src.has3d) build_table(rb.tab, gs, rb.gtab, rb.ts.K, rb.ts.kind, rb.ts.sigma, rb.ts.H, rb.ts.band);
-    const int per_warp = max(kArrays2D * stride2, ray3d_warp_floats(p3));
+    const int per_warp = max(warp_floats_2d(stride2), ray3d_warp_floats(p3));
     float *base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * per_warp;
     rb.base = base;
     if (times && threadIdx.x == 0) atomicMin(times, global_ns());
@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
             st.max_range <= p2.rmax) {
             const long long rfix = __double2ll_rn((double)st.max_range * 65536.0);
             const float rend = (float)((double)rfix * (1.0 / 65536.0));
-            float *sl = base, *sc = sl + stride2, *sp = sc + stride2, *sx = sp + stride2;
+            float *sl, *sc, *sp, *sx;
+            carve_2d(base, stride2, sl, sc, sp, sx);
             const int n = beam_cells<false>(src.map, src.W, src.H, src.gains, src.poses2 + 4 * pi,
                                             src.dirs2[2 * di], src.dirs2[2 * di + 1], rfix, rend, p2.nmax, p2, 0,
                                             nullptr, sl, sc, sp, sx, status);
@@ -122,9 +123,9 @@ cudaError_t launch_mixed_variant(const MixedSrc &src, const DevParams &p2, const
                                  cudaStream_t s)
 {
     const Schedule &sc = current_schedule(FSMI_KIND_2D);
-    const int stride2 = ((p2.nmax + 2) + 3) & ~3;
+    const int stride2 = stride_2d(p2.nmax);
     const int stride3 = ((p3.nmax + 2 * p3.K + 4) + 3) & ~3;
-    const size_t per_warp = (size_t)max(kArrays2D * stride2, ray3d_warp_floats(p3)) * sizeof(float);
+    const size_t per_warp = (size_t)max(warp_floats_2d(stride2), ray3d_warp_floats(p3)) * sizeof(float);
     const size_t table = rle_table_bytes(table_spec(p3).K);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, table);
     const size_t smem = table + (size_t)wpb * per_warp;
