@@ -36,8 +36,8 @@ N_POSES = 1024
 L2_FLUSH_BYTES = 512 << 20  # > the 126 MB L2
 SM_COUNT_NOMINAL = 152
 FMA_LANES_PER_SM_CLK = 128  # FP32 FMA-pipe lane operations per SM per clock (4 x 32)
-EX2_PER_SM_CLK = 32  # SFU ex2.approx results per SM per clock (a throughput probe measured 30.2)
-RCP_PER_SM_CLK = 16  # SFU rcp.approx results per SM per clock (measured 15.1)
+EX2_PER_SM_CLK = 32  # SFU ex2.approx results per SM per clock (csrc/pipe_probe.cu measured 31.8)
+RCP_PER_SM_CLK = 16  # SFU rcp.approx results per SM per clock (measured 15.95)
 SFU_CLK_PER_TERM = 1.0 / EX2_PER_SM_CLK + 1.0 / RCP_PER_SM_CLK  # one ex2 and one rcp per tail term
 OPS_PER_TERM = 11  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh): distance,
 #                    square, 1 + p|d|, 5 Horner FMAs, two products, accumulate
