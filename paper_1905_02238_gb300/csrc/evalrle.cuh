@@ -251,6 +251,41 @@ __device__ __forceinline__ int run_of(const int *S, int nr, int i)
     return lo - 1;
 }
 
+// sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d} over j in this lane's cells (P in CP, C at CC[K + k],
+// zero-padded by K on both sides), the taps added in increasing d. A compile-time radius KK keeps
+// the 2 KK + 1 kernel values in registers for the whole ray (one shared load per tap instead of
+// two); both forms add the same products in the same order. Only kernels without Theorem 5's
+// run-pair path take the register form (FIXED): in a kernel that has both, the extra registers
+// slow the run pairs down.
+template <int KK>
+__device__ __forceinline__ float band_conv_k(const float *CP, const float *CC, const float *gtab, int n)
+{
+    float g[2 * KK + 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * KK; ++d) g[d] = gtab[d];
+    float v = 0.0f;
+    for (int j = lane_id(); j < n; j += 32) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int d = 0; d <= 2 * KK; ++d) acc = fmaf(g[d], CC[j + d], acc);
+        v = fmaf(CP[j], acc, v);
+    }
+    return v;
+}
+
+template <bool FIXED>
+__device__ __forceinline__ float band_conv(const float *CP, const float *CC, const float *gtab, int K, int n)
+{
+    if (FIXED && K == 15) return band_conv_k<15>(CP, CC, gtab, n);  // Gaussian kernels at sigma = 2 cells
+    float v = 0.0f;
+    for (int j = lane_id(); j < n; j += 32) {
+        float acc = 0.0f;
+        for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
+        v = fmaf(CP[j], acc, v);
+    }
+    return v;
+}
+
 // Cell-level evaluation (eq. eqn_from_fsmi) of one ray: decompress the runs into the n virtual
 // cells, form P(e_j) and C_k by warp scans (Algorithms 2 and 3), then
 // I = sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d} (FSMI-RLE, Uniform-FSMI-RLE, strict-band
@@ -281,13 +316,7 @@ static __device__ float ray_mi_cells(float *base, int stride, int nr, int n, con
     }
     __syncwarp();
     cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
-    float tot = 0.0f;
-    for (int j = lane; j < n; j += 32) {
-        float acc = 0.0f;
-        for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
-        tot = fmaf(CP[j], acc, tot);
-    }
-    return tot;
+    return band_conv<false>(CP, CC, gtab, K, n);
 }
 
 __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const DevParams &p, const float2 *tab,
@@ -433,14 +462,19 @@ __host__ __device__ inline int ray3d_warp_floats(const DevParams &p)
     return (thm5_of(p) ? 0 : 3 * ray3d_cell_stride(p)) + 6 * ray3d_run_stride(p);
 }
 
+// Which evaluation paths a fused-ray kernel is compiled with: both (the variant read at run time),
+// Theorem 5's sub-blocks only, or the others (cell-level convolution and all run pairs) only.
+enum { kRay3dAny = 0, kRay3dThm5 = 1, kRay3dOther = 2 };
+
 // Samples, encodes and evaluates one ray into the warp's region `w` (ray3d_warp_floats floats);
-// returns the MI (warp-reduced) and the run count in *nr_out.
+// returns the MI (warp-reduced) and the run count in *nr_out. MODE must agree with thm5_of(p).
+template <int MODE>
 __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, int Z, const int32_t *pose,
                                               const int32_t *u, int nsamp, const DevParams &p, const float2 *tab,
                                               const float *gtab, int K, float *w, int *nr_out)
 {
     const int lane = lane_id();
-    const bool thm5 = thm5_of(p);
+    const bool thm5 = MODE == kRay3dAny ? thm5_of(p) : MODE == kRay3dThm5;
     const int cst = ray3d_cell_stride(p);
     float *CP = thm5 ? nullptr : w, *CF = w + cst, *CC = w + 2 * cst;
     const RunSmem r = run_smem(w + (thm5 ? 0 : 3 * cst), ray3d_run_stride(p));
@@ -458,12 +492,7 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
         }
         __syncwarp();
         cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
-        v = 0.0f;
-        for (int j = lane; j < n; j += 32) {
-            float acc = 0.0f;
-            for (int d = -K; d <= K; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
-            v = fmaf(CP[j], acc, v);
-        }
+        v = band_conv<MODE == kRay3dOther>(CP, CC, gtab, K, n);
     } else {  // here n_r <= nrcap, so every run was stored
         run_starts(r, nr, true);
         run_prefixes(r, nr, p.docc, p.demp);
@@ -532,12 +561,13 @@ __device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const Dev
 }
 
 // sampling, encoding and evaluation of one 3D ray (= pose * R + r), fused layout
+template <int MODE>
 __device__ __forceinline__ void eval_ray_3d(const Vox3D &vx, const DevParams &p, const RleBlock &rb,
                                             long long ray, float *__restrict__ out, int32_t *__restrict__ nruns)
 {
     const int pi = (int)(ray / vx.R), ri = (int)(ray % vx.R);
     int nr = 0;
-    const float I = ray_mi_fused(vx.vox, vx.X, vx.Y, vx.Z, vx.poses + 12 * (size_t)pi, vx.dirs + 3 * (size_t)ri, p.nmax,
+    const float I = ray_mi_fused<MODE>(vx.vox, vx.X, vx.Y, vx.Z, vx.poses + 12 * (size_t)pi, vx.dirs + 3 * (size_t)ri, p.nmax,
                                  p, rb.tab, rb.gtab, rb.ts.K, rb.base, &nr);
     if (lane_id() == 0) {
         out[ray] = I;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
                    st.volume < src.nvol && st.max_range >= 1.0f && st.max_range <= (float)p3.nmax) {
             const fsmi_volume v = src.vols[st.volume];
             int nr = 0;
-            I = ray_mi_fused(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range, p3,
+            I = ray_mi_fused<kRay3dAny>(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range, p3,
                              rb.tab, rb.gtab, rb.ts.K, base, &nr);
         } else {
             bad = FSMI_STATUS_BAD_BEAM;  // a malformed descriptor is never used to index

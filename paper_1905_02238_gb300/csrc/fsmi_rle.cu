@@ -5,13 +5,16 @@
 
 namespace fsmi {
 
+// MODE: kRay3dThm5 for Theorem 5's sub-blocks, kRay3dOther for every other variant (the launcher
+// picks by thm5_of(p)), so that each kernel holds only the paths it can take.
+template <int MODE>
 __global__ void __launch_bounds__(kMaxWarps * 32)
     k_eval_3d(Vox3D vx, DevParams p, long long nrays, int warp_floats, float *__restrict__ out,
               int32_t *__restrict__ nruns, unsigned long long *queue, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RleBlock rb = rle_block(smem_raw, p, warp_floats);
-    for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d(vx, p, rb, ray, out, nruns); });
+    for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d<MODE>(vx, p, rb, ray, out, nruns); });
 }
 
 __global__ void __launch_bounds__(kMaxWarps * 32)
@@ -167,11 +170,12 @@ cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32
     const int wpb = fit_warps(sc.warps_per_block, per_warp, rle_table_bytes(p.K));
     const size_t smem = rle_table_bytes(p.K) + (size_t)wpb * per_warp;
     long long grid;
-    cudaError_t e = grid_for(k_eval_3d, smem, nrays, wpb, sc.blocks_per_sm, grid);
+    auto kern = thm5_of(p) ? k_eval_3d<kRay3dThm5> : k_eval_3d<kRay3dOther>;
+    cudaError_t e = grid_for(kern, smem, nrays, wpb, sc.blocks_per_sm, grid);
     if (e == cudaSuccess) e = reset_queue(queue, s);
     if (e != cudaSuccess) return e;
-    k_eval_3d<<<(unsigned)grid, wpb * 32, smem, s>>>(v, p, nrays, wf, out, nruns, queue,
-                                                     sc.queue_chunk > 0 ? sc.queue_chunk : 1);
+    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(v, p, nrays, wf, out, nruns, queue,
+                                                sc.queue_chunk > 0 ? sc.queue_chunk : 1);
     return cudaGetLastError();
 }
 
@@ -243,7 +247,8 @@ cudaError_t encode_scratch_ptr(int32_t **ptr);
 cudaError_t prepare_rle()
 {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_3d);
+    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dThm5>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dOther>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_rle);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_rle_count);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_rle_write);
