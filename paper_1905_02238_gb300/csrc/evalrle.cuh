@@ -277,6 +277,8 @@ template <bool FIXED>
 __device__ __forceinline__ float band_conv(const float *CP, const float *CC, const float *gtab, int K, int n)
 {
     if (FIXED && K == 15) return band_conv_k<15>(CP, CC, gtab, n);  // Gaussian kernels at sigma = 2 cells
+    if (FIXED && K == 6) return band_conv_k<6>(CP, CC, gtab, n);    // strict band, Delta = 6
+    if (FIXED && K == 4) return band_conv_k<4>(CP, CC, gtab, n);    // box kernel, H = 4
     float v = 0.0f;
     for (int j = lane_id(); j < n; j += 32) {
         float acc = 0.0f;
