@@ -118,6 +118,21 @@ def test_eval_beams_all_variants(sigma, e0):
         assert_mi_close(got, ref, f"beams {kw} sigma={sigma} e0={e0}")
 
 
+@pytest.mark.parametrize("e0", [0, 1])
+def test_exact_windows_wider_than_padding_and_longer_than_cells(e0):
+    # sigma = 20 cells: a slot's window holds ~100 boundaries on each side, more than the 32 padding
+    # boundaries beyond a beam's ends, so lanes near the ends run shorter loops than the round;
+    # cells of 30-60 at sigma = 0.5: windows that end inside the slot's own cell
+    for sigma, (wlo, whi), seed in ((20.0, (0.05, 1.4142), 91), (0.5, (30.0, 60.0), 92)):
+        off, o, l, lend = synth.random_beams(120, 1, 400, seed=seed + e0, w_lo=wlo, w_hi=whi)
+        gp, op = _prms(sigma, 4096.0, e0)
+        got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
+        assert_mi_close(got, oracle.eval_beams(off, o, l, lend, op), f"wide windows sigma={sigma} e0={e0}")
+        gp.flags = fsmi.FLAG_FULL_SWEEP
+        full = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
+        assert np.all(np.abs(got.astype(np.float64) - full) <= 2.0 ** -20 * np.abs(full) + 1e-9)
+
+
 def test_eval_beams_edge_cases():
     # empty beams, single cells, known cells (o in {0, 1}), tiny and wide cells, long beams
     rng = np.random.default_rng(41)

@@ -42,6 +42,7 @@ def _rle_variants():
         dict(variant=fsmi.UNIFORM, uniform_h=0),
         dict(variant=fsmi.UNIFORM, uniform_h=2),
         dict(variant=fsmi.UNIFORM, uniform_h=4),
+        dict(variant=fsmi.APPROX, approx_reading=1, trunc_delta=6),  # kernel radius 6 (register taps)
     ]
 
 
@@ -180,7 +181,8 @@ def test_eval_3d_config3_full_size_sampled():
     rng = np.random.default_rng(51)
     sel_p = rng.choice(64, 3, replace=False)
     sel_r = np.sort(rng.choice(dirs.shape[0], 96, replace=False))
-    for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
+    for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6),
+               dict(variant=fsmi.APPROX, trunc_delta=6, approx_reading=1), dict(variant=fsmi.UNIFORM, uniform_h=4)):
         gp, op = _prms(**kw)
         got, nr = fsmi.eval_3d(_cuda(vox), _cuda(poses), _cuda(dirs), gp, with_runs=True)
         got, nr = got.cpu().numpy(), nr.cpu().numpy()
