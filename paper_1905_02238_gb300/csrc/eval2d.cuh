@@ -151,39 +151,12 @@ constexpr float kTailCut = 11.3f;
 // below 2^-24 of it (one FP32 ulp) for sigma <= 20 cells, and below 2^-26 for sigma <= 2.
 constexpr float kTailCutDefault = 4.81f;
 
-__device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
-{
-    int lo = 0, len = n;
-    while (len > 0) {
-        const int half = len >> 1;
-        if (a[lo + half] < x) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return lo;
-}
-
-// The same index (first g in [0, N] with a[g] >= x, a ascending, N >= 2, a[N] readable and
-// >= x) when it lies in [g0, g0 + 3]: three independent loads count the entries below x from g0;
-// two checks confirm the range, else bisection decides. Along a traversed beam boundaries are
-// nearly evenly spaced, so a guess from the mean spacing lands in that range.
-__device__ __forceinline__ int lower_bound_from(const float *a, int N, float x, int g0)
-{
-    g0 = min(max(g0, 0), N - 2);
-    const int c = (a[g0] < x ? 1 : 0) + (a[g0 + 1] < x ? 1 : 0) + (a[g0 + 2] < x ? 1 : 0);
-    const int g = g0 + c;
-    if ((c == 3 && a[g] < x) || (g0 > 0 && a[g0 - 1] >= x)) return lower_bound_f(a, N, x);
-    return g;
-}
-
-// Boundary terms m in [lo, hi) of one first-hit cell with centre mu, the range widened to even
-// bounds so that every term goes through the packed tail (a term added that way lies outside the
-// window: zero in FP32 or below the window's cut; index n + 1 is padding with l = 3e30, dC = 0).
+// Boundary terms of one first-hit cell with centre mu over the pairs (m, m + 1), m = m0, m0 + 2,
+// ... < end (m0, nb and end even, m0 <= nb <= end), so that every term goes through the packed
+// tail; the pairs below nb lie before the centre, the pair at nb straddles it when mid is odd.
 // A boundary m < mid lies before the centre: -dC_m T(mu - l_m); above it +dC_m T(l_m - mu).
-// Returns the packed sums over even and odd m, each added in increasing m.
+// Padding boundaries (l = -+3e30, dC = 0) give exact zeros. Returns the packed sums over even and
+// odd m, each added in increasing m.
 #ifndef FSMI_PAIR_UNROLL
 #define FSMI_PAIR_UNROLL 4
 #endif
@@ -221,51 +194,66 @@ __device__ __forceinline__ f32x2 window_terms(const float *sl, const float *sdc,
 // |l_m - mu_j| < cut (scaled) are visited, in increasing m. With cut = kTailCut every non-zero
 // term of the full sweep is added in the same order and the FP32 result is the same bit for bit;
 // with kTailCutDefault the terms skipped are below 2^-27 of their weights.
-// The 32 slots of a round run the same number of pairs below and above their centres (the
-// round's longest window on each side): a lane with a shorter window adds the next boundaries
-// beyond it, which are terms of the full sum too (or padding with weight 0), so that no lane
-// leaves the unrolled loops at a different point than the others.
+// The 32 slots of a round run the same number of pairs below and above their centres: the
+// fewest pairs G that cover every slot's window on that side. A slot whose window is shorter adds
+// the next boundaries beyond it, which are terms of the full sum too (or padding with weight 0),
+// so that no lane leaves the unrolled loops at a different point than the others. No window end is
+// searched for: with the pairs below the centre starting at nb - 2G, a slot is covered when the
+// boundary before that start lies below mu - cut (one shared load per lane and trial G), and the
+// trials start from the previous round's G, which changes little along a beam.
 // sdc[m] = C_m - C_{m-1} for m = 0..n; sl and sdc padded by kPad2D entries on both sides.
 __device__ __forceinline__ float exact_window_sum(const float *sl, const float *sdc, const float *sc,
                                                   const float *sp, int n, bool e0, float pe0, float mu0, float cut)
 {
     const int nslots = n + (e0 ? 1 : 0);
-    // search guesses: the window of slot j reaches about `half` boundaries to either side of
-    // boundary j + 1 (boundaries per unit of scaled distance from the beam's mean spacing); the
-    // guesses err by -1 .. +2 (lower end) and -2 .. +1 (upper end) along traversed beams
+    // first trial: about cut x (boundaries per unit of scaled distance) boundaries on each side
     const float span = sl[n] - sl[0];
     const float per = span > 0.0f ? (float)n / span : 0.0f;
-    const int half = (int)fminf(cut * per, (float)(n + 1));
+    int GN = (int)fminf(cut * per, (float)(n + 1)) >> 1, GP = GN;
     const int mtop = (n + 1 + kPad2D) & ~1;  // pairs (m, m + 1) stay below n + 2 + kPad2D
     float r = 0.0f;
     for (int jb = 0; jb < nslots; jb += 32) {
         const int j = jb + lane_id();
+        const bool act = j < nslots;
         float mu = 0.0f, Cj = 0.0f, Pj = 0.0f;
-        int mid = 0, m0 = 0, nb = 0, end = 0;
-        if (j < nslots) {
-            if (j < n) {
-                mu = 0.5f * (sl[j] + sl[j + 1]);
-                Cj = sc[j];
-                Pj = sp[j];
-                mid = j + 1;
-            } else {
-                mu = mu0;
-                Pj = pe0;
-            }
-            const int anchor = mid;  // j + 1, or 0 for the no-return slot (centre before l_0)
-            // sl[n + 1] is the first padding boundary (3e30), above every target
-            const int lo = lower_bound_from(sl, n + 1, mu - cut, anchor - half - 2);
-            const int hi = lower_bound_from(sl, n + 1, mu + cut, anchor + half - 1);
-            m0 = lo & ~1;
-            end = (hi + 1) & ~1;
-            nb = min(max(mid & ~1, m0), end);  // pairs (m, m + 1) with m + 1 < mid end here
+        int mid = 0;
+        if (act && j < n) {
+            mu = 0.5f * (sl[j] + sl[j + 1]);
+            Cj = sc[j];
+            Pj = sp[j];
+            mid = j + 1;
+        } else if (act) {  // the no-return slot: centre before l_0, every boundary above it
+            mu = mu0;
+            Pj = pe0;
         }
-        const int tn = (nb - m0) >> 1, tp = nb < end ? (end - nb - 2) >> 1 : 0;
-        const int TN = __reduce_max_sync(kFull, tn), TP = __reduce_max_sync(kFull, tp);
-        if (j < nslots) {
-            m0 = max(nb - 2 * TN, -kPad2D);
-            if (nb < end) end = min(nb + 2 + 2 * TP, mtop);
+        const int nb = mid & ~1;  // pairs (m, m + 1) with m + 1 < mid end here
+        const float below = mu - cut, above = mu + cut;
+        // below the centre: covered at G when every boundary before nb - 2G lies below mu - cut
+        // (true for every G once nb - 2G <= 0, so both loops end)
+        auto neg_ok = [&](int G) {
+            const int m = nb - 2 * G;
+            return !act || m <= 0 || sl[m - 1] < below;
+        };
+        // above it: covered when every boundary from nb + 2 + 2G on lies at or beyond mu + cut
+        // (true once that index passes n)
+        auto pos_ok = [&](int G) {
+            const int e = nb + 2 + 2 * G;
+            return !act || e > n || sl[e] >= above;
+        };
+        if (__all_sync(kFull, neg_ok(GN))) {
+            while (GN > 0 && __all_sync(kFull, neg_ok(GN - 1))) --GN;
+        } else {
+            do ++GN;
+            while (!__all_sync(kFull, neg_ok(GN)));
         }
+        if (__all_sync(kFull, pos_ok(GP))) {
+            while (GP > 0 && __all_sync(kFull, pos_ok(GP - 1))) --GP;
+        } else {
+            do ++GP;
+            while (!__all_sync(kFull, pos_ok(GP)));
+        }
+        const int m0 = act ? max(nb - 2 * GN, -kPad2D) : 0;
+        const int end = act ? min(nb + 2 + 2 * GP, mtop) : 0;
         float a0, a1;
         unpack2(window_terms(sl, sdc, m0, nb, end, mid, mu), a0, a1);
         r = fmaf(Pj, Cj + (a0 + a1), r);
