@@ -44,8 +44,8 @@ OPS_PER_TERM = 11  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss
 TAIL_CUT = 4.81  # scaled half-width of the exact kernel's default window (csrc/eval2d.cuh)
 
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
-# ncu capture (profiles/k_eval_2d_exact_office2048.md), valid only for the kernel sources whose
-# hash is recorded with it; reported as null once those sources change.
+# ncu capture of one full-size launch (dram__bytes_read.sum + dram__bytes_write.sum), valid only
+# for the kernel sources whose hash is recorded with it; reported as null once those sources change.
 TRAFFIC = {"sources_sha1": "9098bd92c1f20676a055853ef5123c829b2be5a0", "bytes_per_launch": 110.64e6}
 KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb300/csrc/eval2d.cuh",
                   "paper_1905_02238_gb300/csrc/dda2d.cuh", "paper_1905_02238_gb300/csrc/gauss_tail.cuh",

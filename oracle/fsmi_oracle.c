@@ -11,7 +11,7 @@
  * paper's order; library primitives (erfc, exp, log, log1p, pow) are the only building blocks.
  * No blocking, fusion, telescoping or reordering beyond what the cited equation states.
  *
- * Conventions (the readings of ambiguous passages are listed in the design doc):
+ * Conventions (readings of passages the paper leaves open or states ambiguously):
  *   - natural logarithms: mutual information is in nats;
  *   - cells are 0-based here: paper cell i (1..n) is index i-1; boundaries l[0..n] with l[0] = l_1 = 0;
  *   - the no-return event e_0 is dropped by default (e0_mode = 0); e0_mode = 1 places it at the
