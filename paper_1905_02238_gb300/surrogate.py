@@ -1,6 +1,6 @@
 """Learned surrogate of the beam FSMI: training on FSMI-labelled beams, prescreening of candidate
 poses, and the exact rerank (not part of the paper; exact FSMI stays the labeller, the fallback
-and the judge).
+and the final arbiter of the ranking).
 
 Every numerical step runs in the library's kernels (``fsmi.py``): profile sampling, the network's
 forward and backward passes, Adam, the tensor-core inference, per-pose sums, top-k selection,
