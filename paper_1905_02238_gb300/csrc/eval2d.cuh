@@ -148,7 +148,8 @@ constexpr float kTailCut = 11.3f;
 // Default window of the exact sum: T(4.81) = 7.4e-9 < 2^-27. Boundaries come at most two per
 // major-axis crossing interval (scaled length >= cs = sqrt(log2 e) / (sigma sqrt 2)), so the terms
 // skipped on one side weigh at most 2 T(4.81) / (1 - 2^(-9.62 cs)) times max |C_m - C_{m-1}|:
-// below 2^-24 of it (one FP32 ulp) for sigma <= 20 cells, and below 2^-26 for sigma <= 2.
+// at most 2^-24 of it (one FP32 ulp) for sigma up to 19 cells (1.01 x 2^-24 at 20), below 2^-25
+// for sigma <= 2.
 constexpr float kTailCutDefault = 4.81f;
 
 // Boundary terms of one first-hit cell with centre mu over the pairs (m, m + 1), m = m0, m0 + 2,

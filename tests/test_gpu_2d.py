@@ -282,7 +282,7 @@ def test_exact_full_window_is_bit_identical_to_full_sweep(e0):
 @pytest.mark.parametrize("e0", [0, 1])
 def test_exact_default_window_against_full_sweep(e0):
     # the default window skips terms below 2^-27 of their weights (together below one FP32 ulp of
-    # the largest weight for sigma <= 20 cells): the MI moves by a few FP32 roundings of the
+    # the largest weight for sigma up to 19 cells): the MI moves by a few FP32 roundings of the
     # running sums at most, far inside the parity tolerance
     for R, sigma, npo in WINDOW_CASES:
         grid, poses, dirs = _window_case(R, sigma, npo)
