@@ -227,6 +227,30 @@ def test_invalid_arguments_launch_nothing():
     assert fsmi.eval_2d(_cuda(grid), _cuda(poses[:0]), _cuda(dirs), gp).shape == (0, 360)
 
 
+@pytest.mark.parametrize("e0", [0, 1])
+def test_eval_beams_at_the_cell_limit(e0):
+    # beams of exactly FSMI_MAX_CELLS cells: the per-warp arrays and their padding at full extent
+    rng = np.random.default_rng(60 + e0)
+    nb, n = 4, 2048
+    w = rng.uniform(0.05, 1.4142, (nb, n))
+    w[:, rng.random(n) < 0.02] = 0.0  # a few zero-length cells
+    edges = np.concatenate([np.zeros((nb, 1)), np.cumsum(w, axis=1)], axis=1).astype(np.float32)
+    off = (np.arange(nb + 1) * n).astype(np.int32)
+    o = rng.uniform(0.0, 1.0, nb * n).astype(np.float32)
+    l = edges[:, :n].reshape(-1).copy()
+    lend = edges[:, n].copy()
+    for kw in _variants():
+        gp, op = _prms(2.0, 64.0, e0, **kw)
+        got = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp).cpu().numpy()
+        assert_mi_close(got, oracle.eval_beams(off, o, l, lend, op), f"limit {kw} e0={e0}")
+    gp, _ = _prms(2.0, 64.0, e0)
+    gp.flags = fsmi.FLAG_FULL_WINDOW
+    win = fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp)
+    gp.flags = fsmi.FLAG_FULL_SWEEP
+    assert torch.equal(win, fsmi.eval_beams(_cuda(off), _cuda(o), _cuda(l), _cuda(lend), gp))
+    assert fsmi.device_status() == 0
+
+
 def test_bad_explicit_beam_sets_status():
     off = np.array([0, 3000], np.int32)  # longer than FSMI_MAX_CELLS
     o = np.full(3000, 0.5, np.float32)
