@@ -52,11 +52,19 @@ KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb
                   "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]
 
 
-def kernel_sources_sha1() -> str:
+# DRAM bytes per launch of the fused 3D kernel on the 512x512x128 batch, per variant, from one
+# ncu capture each (valid for the sources hashed with them, like TRAFFIC)
+KERNEL_SOURCES_3D = ["paper_1905_02238_gb300/csrc/fsmi_rle.cu", "paper_1905_02238_gb300/csrc/evalrle.cuh",
+                     "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]
+TRAFFIC_3D = {"sources_sha1": "765520f473e66df7e45bad953e9fb96522a3511d", "fsmi_rle_3d": 561.87e6, "approx_fsmi_rle_3d_delta6": 569.76e6,
+              "approx_fsmi_rle_3d_delta6_band": 563.57e6, "uniform_fsmi_rle_3d_h4": 562.45e6}
+
+
+def kernel_sources_sha1(files=None) -> str:
     import hashlib
 
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in files or KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -217,6 +225,75 @@ def work_counts(fsmi, grid, p, d, chunk=32768):
     return cells, pairs, terms, band
 
 
+def rle_work_counts(fsmi, v, vp, vd, prm, cell_runlen, K, poses_per_chunk=8):
+    """Algorithmic work of one fused 3D launch, from the (bit-exact) encoder: virtual-cell samples
+    (a 4-byte gather each), runs, and the FP32 work of the path each ray takes. Cell-level form
+    (rays with n < cell_runlen * n_r, not Theorem 5): 2K + 2 FMAs per cell (the 2K + 1 taps of
+    the banded convolution and the product with P(e_j)). Run pairs (the other rays, and every ray
+    under Theorem 5): the A/B terms of pair_AB (csrc/evalrle.cuh), 6 FP32 operations each
+    (window difference, weighted window, two accumulations, the power of x)."""
+    import torch
+
+    thm5 = prm.variant == fsmi.APPROX and prm.approx_reading == 0
+    D = prm.trunc_delta
+    tot = {"rays": 0, "samples": 0, "runs": 0, "cell_rays": 0, "cell_cells": 0, "pair_rays": 0, "pair_terms": 0}
+
+    def terms(Lu, Lv, t):  # pair_AB iterations: j in [max(0, -K - t), min(Lu - 1, Lv - 1 + K - t)]
+        lo = torch.clamp(-K - t, min=0)
+        hi = torch.minimum(Lu - 1, Lv - 1 + K - t)
+        return torch.clamp(hi - lo + 1, min=0)
+
+    for a in range(0, vp.shape[0], poses_per_chunk):
+        pp = vp[a:a + poses_per_chunk]
+        nrays = pp.shape[0] * vd.shape[0]
+        off, _, rl = fsmi.rle_encode_3d(v, pp, vd, prm, capacity=nrays * int(prm.max_range))
+        off = off.to(torch.int64)
+        L = rl.to(torch.int64)[:int(off[-1])]
+        cum = torch.cat([torch.zeros(1, dtype=torch.int64, device=L.device), torch.cumsum(L, 0)])
+        n = cum[off[1:]] - cum[off[:-1]]
+        nr = off[1:] - off[:-1]
+        tot["rays"] += nrays
+        tot["samples"] += int(n.sum())
+        tot["runs"] += int(nr.sum())
+        cell = torch.zeros_like(n, dtype=torch.bool) if thm5 else (n < cell_runlen * nr)
+        tot["cell_rays"] += int(cell.sum())
+        tot["cell_cells"] += int(n[cell].sum())
+        pair = (~cell) & (nr > 0)
+        tot["pair_rays"] += int(pair.sum())
+        ray = torch.repeat_interleave(torch.arange(nrays, device=L.device), nr)
+        S = cum[:-1] - cum[off[:-1]][ray]  # run start within its ray
+        keep = pair[ray]
+        if thm5:
+            tot["pair_terms"] += int(L[keep].sum())  # the diagonal blocks (theta, gamma): L_u terms
+            for k in range(1, D + 2):  # runs within Delta of run u lie at most Delta + 1 runs away
+                u, w = torch.arange(0, L.numel() - k, device=L.device), torch.arange(k, L.numel(), device=L.device)
+                ok = keep[u] & (ray[u] == ray[w])
+                su, Lu, sv, Lv = S[u], L[u], S[w], L[w]
+                up = ok & (sv < su + Lu + D)  # u < v
+                su2 = torch.maximum(su, sv - D)
+                tot["pair_terms"] += int(torch.where(up, terms(su + Lu - su2, torch.minimum(Lv, su + Lu + D - sv),
+                                                               su2 - sv), 0).sum())
+                dn = ok & (su + Lu + D > sv)  # the same pair seen from v (v > u): sub-block below v
+                # v as the first-hit run, u below it: Lu' = min(L_v, s_u + L_u + D - s_v), Lv' from s_v - D
+                sv2 = torch.maximum(su, sv - D)
+                tot["pair_terms"] += int(torch.where(dn, terms(torch.minimum(Lv, su + Lu + D - sv), su + Lu - sv2,
+                                                               sv - sv2), 0).sum())
+        elif bool(pair.any()):
+            rid = torch.nonzero(pair).squeeze(1)
+            m = int(nr[rid].max())
+            idx = off[:-1][rid][:, None] + torch.arange(m, device=L.device)[None, :]
+            valid = torch.arange(m, device=L.device)[None, :] < nr[rid][:, None]
+            idx = torch.where(valid, idx, torch.zeros_like(idx))
+            Sr, Lr = S[idx], L[idx]
+            t = Sr[:, :, None] - Sr[:, None, :]
+            c = terms(Lr[:, :, None], Lr[:, None, :], t)
+            c = torch.where(valid[:, :, None] & valid[:, None, :], c, torch.zeros_like(c))
+            tot["pair_terms"] += int(c.sum())
+        del off, rl, L, cum
+    tot["fp32_ops"] = tot["cell_cells"] * (2 * K + 2) + 6 * tot["pair_terms"]
+    return tot
+
+
 def rle_crossover_leg(dev):
     """The paper's run-length experiment (beams of 256 unit cells made of groups of L cells of equal
     occupancy; 100,000 beams rather than the paper's 1000, so that the GPU times throughput and not
@@ -295,20 +372,70 @@ def _time_ms(fn, reps=5):
     return s.elapsed_time(e) / reps
 
 
+def pipe_rates_leg(dev):
+    """Measured denominators of the rooflines (fsmi_probe): SM clock, SFU ex2 / rcp and FP32 /
+    packed-FP32 FMA issue rates per SM per clock, L2 read bandwidth (a 32 MB buffer, well inside
+    the 126 MB L2, read 32 times per launch) and HBM read bandwidth (a 2 GB buffer read once)."""
+    import torch
+
+    from paper_1905_02238_gb300 import fsmi
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cyc = torch.zeros(1, dtype=torch.int64, device=dev)
+    sink = torch.zeros(4, dtype=torch.float32, device=dev)
+
+    def mhz():
+        ms = _time_ms(lambda: fsmi.probe(fsmi.PROBE_SPIN, 1 << 24, cyc), reps=1)
+        return float(cyc.item()) / (ms * 1e3)
+
+    f0 = mhz()
+    rates = {}
+    iters = 4096
+    for name, kind in (("ex2", fsmi.PROBE_EX2), ("rcp", fsmi.PROBE_RCP), ("fma", fsmi.PROBE_FMA),
+                       ("fma_f32x2_instructions", fsmi.PROBE_FMA2)):
+        ms = _time_ms(lambda: fsmi.probe(kind, iters, sink), reps=2)
+        rates[name] = fsmi.probe_threads(kind) * iters * 8 / (ms * 1e-3)  # lane operations per second
+    f1 = mhz()
+    f = 0.5 * (f0 + f1)
+    per_clk = {k: v / sms / (f * 1e6) for k, v in rates.items()}
+    l2buf = torch.ones((32 << 20) // 4, dtype=torch.float32, device=dev)
+    ms_l2 = _time_ms(lambda: fsmi.probe(fsmi.PROBE_READ, 32, l2buf), reps=3)
+    del l2buf
+    hbuf = torch.ones((2 << 30) // 4, dtype=torch.float32, device=dev)
+    ms_hbm = _time_ms(lambda: fsmi.probe(fsmi.PROBE_READ, 1, hbuf), reps=3)
+    del hbuf
+    return {"sm_mhz_before_after": [f0, f1], "per_sm_per_clock": per_clk,
+            "l2_read_gbs": 32 * (32 << 20) / (ms_l2 * 1e-3) / 1e9, "hbm_read_gbs": (2 << 30) / (ms_hbm * 1e-3) / 1e9,
+            "nominal_per_sm_per_clock": {"ex2": 32, "rcp": 16, "fma": 128, "fma_f32x2_instructions": 64},
+            "how": "fsmi_probe kernels, CUDA events: 152 SMs x 8 blocks x 256 threads, 8 chains of 4096 dependent "
+                   "operations per thread (rcp chains add one add.f32 each); reads cached in L2 only (ld.global.cg)"}
+
+
 def _sched(s):
     return {"warps_per_block": s.warps_per_block, "blocks_per_sm": s.blocks_per_sm, "queue_chunk": s.queue_chunk,
             "cell_runlen": s.cell_runlen}
 
 
-def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=None):  # noqa: C901
-    """Throughput of the other variants on the same devices (context; not the headline). The 3D
-    variants run as the 512x512x128 depth-camera batch in one persistent launch with an autotuned
-    schedule, captured in a CUDA graph and timed by graph replays."""
+def roofline(bound, achieved, peak, unit, kernel, model, traffic=None, **extra):
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": traffic, "kernel": kernel, "model": model, **extra}
+
+
+def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=None, pipes=None,
+                   sm_mhz=None):  # noqa: C901
+    """Throughput of the other variants on the same devices (context; not the headline), each
+    with its roofline. The 3D variants run as the 512x512x128 depth-camera batch in one persistent
+    launch with an autotuned schedule, captured in a CUDA graph and timed by graph replays."""
+    import numpy as np
     import torch
 
     from paper_1905_02238_gb300 import fsmi, synth
 
     res = {}
+    sms = torch.cuda.get_device_properties(g.device).multi_processor_count
+    f_hz = (sm_mhz or 2070.0) * 1e6
+    l2_gbs = pipes["l2_read_gbs"] if pipes else None
+    fma_peak = sms * FMA_LANES_PER_SM_CLK * f_hz  # FP32 lane operations per second
     nb = p.shape[0] * d.shape[0]
     gains_ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=g.device)
     for name, kw, nterms in (("exact_fsmi_full_sweep", dict(variant=fsmi.EXACT, flags=fsmi.FLAG_FULL_SWEEP), None),
@@ -325,6 +452,19 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
             if peak_terms and cells:
                 # Approx evaluates band + 1 boundary tails per first-hit cell (one ex2, one rcp each)
                 res[name]["roofline_sfu_frac"] = (nterms + cells) / (ms * 1e-3) / peak_terms
+                res[name]["roofline"] = roofline(
+                    "alu", (nterms + cells) / (ms * 1e-3) / 1e12, peak_terms / 1e12, "T tail-terms/s (SFU)",
+                    "k_eval_2d<APPROX,map>",
+                    f"{nterms + cells:.4g} boundary tails per launch (sum over first-hit cells j of the band "
+                    f"[j - 6, j + 6] clipped to the beam, plus one: its boundaries), one ex2 and one rcp each")
+        if name == "uniform_fsmi_h4" and cells and l2_gbs:
+            # Algorithm 4 after the per-map-cell gains: per visited cell one 16-byte gather of
+            # (o, f_occ, f_emp) from the L2-resident gains array, prefix sums and O(1) arithmetic
+            res[name]["roofline"] = roofline(
+                "l2", 16 * cells / (ms * 1e-3) / 1e9, l2_gbs, "GB/s", "k_eval_2d<UNIFORM,map>",
+                f"{cells:.4g} visited cells per launch x 16 B gathered (per-map-cell gains, L2-resident) "
+                "against the measured L2 read bandwidth (pipe_rates); the kernel is bound by issue "
+                "(traversal, gathers, scans), not by either pipe")
     if terms:
         res["exact_fsmi_window_terms"] = terms
     # config 1 (correctness configuration, launch-latency bound): one pose x 360 beams, R = 64
@@ -364,6 +504,24 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
                      "schedule": _sched(best),
                      "workload": "512x512x128 voxels, 64 poses x 128x128 rays, 384 virtual cells, fused sample+RLE+MI, "
                                  "autotuned schedule, CUDA-graph replay"}
+        K = 4 if prm.variant == fsmi.UNIFORM else (6 if prm.approx_reading == 1 else int(np.ceil(7.45 * SIGMA)))
+        wc = rle_work_counts(fsmi, v, vp, vd, prm, best.cell_runlen or 32, K)
+        res[name]["work"] = wc
+        sec = ms * 1e-3
+        fr_fma = wc["fp32_ops"] / sec / fma_peak
+        l2_bytes = 4 * wc["samples"] + 4 * nr
+        if l2_gbs:
+            fr_l2 = l2_bytes / sec / 1e9 / l2_gbs
+            rl2 = roofline("l2", l2_bytes / sec / 1e9, l2_gbs, "GB/s", f"k_eval_3d ({name})",
+                           f"{wc['samples']:.4g} virtual-cell samples x 4 B gathered + 4 B out per ray, against the "
+                           "measured L2 read bandwidth (the 134 MB volume is mostly L2-served)",
+                           traffic=TRAFFIC_3D.get(name) if TRAFFIC_3D.get("sources_sha1") == kernel_sources_sha1(
+                               KERNEL_SOURCES_3D) else None)
+            rfma = roofline("alu", wc["fp32_ops"] / sec / 1e12, fma_peak / 1e12, "T FP32 ops/s", f"k_eval_3d ({name})",
+                            f"{wc['cell_cells']:.4g} cells of cell-form rays x {2 * K + 2} FMAs (banded convolution, "
+                            f"K = {K}) + {wc['pair_terms']:.4g} run-pair A/B terms x 6 FP32 ops")
+            res[name]["roofline"] = rl2 if fr_l2 >= fr_fma else rfma
+            res[name]["roofline_other"] = rfma if fr_l2 >= fr_fma else rl2
     fsmi.set_schedule(fsmi.KIND_RLE, saved)
     return res
 
@@ -774,10 +932,11 @@ def run_fsmi(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,  # per step: per-cell gains of the map, then the beams
         }
-        if ws == 1:
+        if ws == 1 and not args.no_context:
             exact_out = out.cpu().numpy()  # the timed steps' result, before the context runs reuse `out`
+            line["pipe_rates"] = pipe_rates_leg(dev)
             line["variants"] = other_variants(g, p, d, out, cells=cells, terms=terms, band=band,
-                                              peak_terms=peak_terms)
+                                              peak_terms=peak_terms, pipes=line["pipe_rates"], sm_mhz=sm_max)
             line["rle_vs_cells"] = rle_crossover_leg(dev)
             net = None
             if not args.no_surrogate:
@@ -795,6 +954,40 @@ def run_fsmi(args):
     return 0
 
 
+def relaunch_cmd(n: int, argv: list[str], port: int) -> list[str]:
+    """The torchrun command that runs this script as n local ranks (one per GPU) with argv."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+            "--master-addr", "127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+
+
+def free_port() -> int:
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def check_ranks() -> int:
+    """--check-ranks: every rank joins a gloo group (no GPU work, nothing timed) and rank 0 prints
+    how many joined: a self-check of the launcher, not a benchmark line."""
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        dist.init_process_group("gloo")
+        t = torch.ones(1)
+        dist.all_reduce(t)
+        joined = int(t.item())
+        dist.destroy_process_group()
+    else:
+        joined = 1
+    if rank == 0:
+        print(json.dumps({"check": "ranks", "world_size": ws, "ranks_joined": joined}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -804,9 +997,20 @@ def main():
     ap.add_argument("--poses", type=int, default=N_POSES, help="poses per GPU (smaller for profiling cases)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed candidate-set stream leg")
+    ap.add_argument("--no-context", action="store_true", help="only the timed steps (profiling runs)")
+    ap.add_argument("--check-ranks", action="store_true", help="launcher self-check: join the ranks, report, exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    ws = int(os.environ.get("WORLD_SIZE", "0"))
+    if args.gpus > 1 and ws == 0:
+        # --gpus N without a launcher: start N local ranks (one process per GPU) and wait for them
+        return subprocess.call(relaunch_cmd(args.gpus, sys.argv[1:], free_port()))
+    if ws and ws != args.gpus:
+        sys.stderr.write(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={ws}: the rank count must match\n")
+        return 2
+    if args.check_ranks:
+        return check_ranks()
     if args.impl == "reference":
         return run_reference(args)
     return run_fsmi(args)

@@ -277,7 +277,9 @@ fsmi_status fsmi_trace_2d(int W, int H, const int32_t *poses, int P, const int32
  *   run_o    float32 [run_capacity], run_len uint8 [run_capacity]: output runs.
  *   ws       device workspace of at least fsmi_workspace_size(FSMI_FN_RLE_ENCODE_3D, ...) bytes.
  * If the runs exceed run_capacity, the status bit FSMI_STATUS_RUN_OVERFLOW is set, run_off
- * still holds the full offsets and only runs below run_capacity are written.
+ * still holds the full offsets and only runs below run_capacity are written. The offsets are
+ * int32: where the runs of a batch pass INT32_MAX in total, the offsets beyond saturate at
+ * INT32_MAX (never wrap) and FSMI_STATUS_RUN_OVERFLOW is set.
  */
 fsmi_status fsmi_rle_encode_3d(const float *vox, int X, int Y, int Z, const int32_t *poses, int P,
                                const int32_t *dirs, int R, const fsmi_params *prm, int32_t *run_off,
@@ -338,6 +340,31 @@ fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *p
  * value plus 2e-8 everywhere.
  */
 fsmi_status fsmi_gauss_tail(const float *s, float *out, long long n, fsmi_stream_t stream);
+
+/*
+ * fsmi_probe - measurement kernels for the rooflines of the kernels above (not part of the
+ * method; the paper has no counterpart). One launch on `stream`; the caller times it with CUDA
+ * events and divides the work by the time:
+ *   FSMI_PROBE_EX2, _RCP, _FMA, _FMA2: fsmi_probe_threads(probe) threads each run iters x 8
+ *     dependent ex2.approx.ftz.f32 / rcp.approx.ftz.f32 (+ one add.f32 each) / fma.rn.f32 /
+ *     fma.rn.f32x2 instructions (eight independent chains). buf: >= 4 bytes, never written in
+ *     practice (a sink that keeps the work alive).
+ *   FSMI_PROBE_READ: iters passes over the bytes of buf (16-byte aligned, a multiple of 16), each
+ *     a grid-strided float4 read cached in L2 only: L2 read bandwidth for a buffer well inside L2,
+ *     HBM read bandwidth for one several times larger.
+ *   FSMI_PROBE_SPIN: one warp spins for iters SM clock cycles (<= 2^40) and stores the cycle
+ *     count in buf (int64, 8-byte aligned): the SM clock is iters / the launch's duration.
+ * Returns FSMI_ERR_ARG for an unknown probe or a buffer that does not fit.
+ */
+#define FSMI_PROBE_EX2 0
+#define FSMI_PROBE_RCP 1
+#define FSMI_PROBE_FMA 2
+#define FSMI_PROBE_FMA2 3
+#define FSMI_PROBE_READ 4
+#define FSMI_PROBE_SPIN 5
+fsmi_status fsmi_probe(int probe, long long iters, void *buf, size_t bytes, fsmi_stream_t stream);
+/* threads of one fsmi_probe launch of `probe` on the current device (0 if unknown) */
+int fsmi_probe_threads(int probe);
 
 /*
  * The exploration loop around the beam MI (Section 2.4; eq. (1) of Section 2.1).

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsmi.so")
-PROBE = os.path.join(BUILD, "pipe_probe")  # issue-rate probe of the SFU and FMA pipes (csrc/pipe_probe.cu)
-SOURCES = ["fsmi_api.cu", "fsmi_2d.cu", "fsmi_rle.cu", "fsmi_explore.cu", "fsmi_surrogate.cu", "fsmi_mixed.cu"]
+SOURCES = ["fsmi_api.cu", "fsmi_2d.cu", "fsmi_rle.cu", "fsmi_explore.cu", "fsmi_surrogate.cu", "fsmi_mixed.cu",
+           "fsmi_probe.cu"]
 HEADERS = ["fsmi_internal.h", "fsmi_device.cuh", "gauss_tail.cuh", "dda2d.cuh", "eval2d.cuh", "evalrle.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -37,28 +37,13 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_probe(force: bool = False) -> str:
-    """Compile (if stale) the standalone pipe-rate probe and return its path."""
-    src = os.path.join(CSRC, "pipe_probe.cu")
-    if not force and os.path.exists(PROBE) and os.path.getmtime(PROBE) >= os.path.getmtime(src):
-        return PROBE
-    os.makedirs(BUILD, exist_ok=True)
-    tmp = PROBE + f".{os.getpid()}.tmp"
-    r = subprocess.run([nvcc()] + ARCH + ["-O3", "-std=c++17", "-o", tmp, src], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed on pipe_probe.cu:\n{r.stderr}")
-    os.replace(tmp, PROBE)
-    return PROBE
-
-
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
-          out: str | None = None, src_dir: str | None = None) -> str:
-    """Compile (if stale) and return the path of libfsmi.so. `out`, `extra_flags` (e.g. -D
-    tunables) and `src_dir` (another copy of csrc/) build a separate library elsewhere."""
-    if out is None and not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
+    """Compile (if stale) and return the path of libfsmi.so. `extra_flags` (e.g. -D tunables)
+    force a rebuild with them."""
+    if not force and not extra_flags and not _stale():
         return LIB
-    target = out or LIB
-    bdir = BUILD if out is None else out + ".objs"
+    target = LIB
+    bdir = BUILD
     os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
@@ -68,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     def compile_one(src: str) -> str:
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [cc] + flags + ["-c", os.path.join(src_dir or CSRC, src), "-o", obj]
+        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -76,11 +61,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
-        probe = ex.submit(build_probe, force) if out is None else None
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-        if probe is not None:
-            probe.result()
     tmp = target + f".{os.getpid()}.tmp"
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", "-rpath,/usr/local/cuda/lib64"]

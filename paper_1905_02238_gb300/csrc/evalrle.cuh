@@ -587,7 +587,7 @@ __device__ __forceinline__ void eval_ray_rle(const int32_t *__restrict__ off, co
     const RunSmem r = run_smem(rb.base, stride);
     const int b = off[ray];
     const int nr = off[ray + 1] - b;
-    bool bad = nr < 0 || nr > p.nmax;
+    bool bad = b < 0 || nr < 0 || nr > p.nmax;
     int cells = 0;
     if (!bad) {
         for (int u = lane; u < nr; u += 32) {

@@ -170,6 +170,8 @@ fsmi_schedule to_public(const Schedule &s)
 }
 }  // namespace
 
+fsmi_status record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
 const Schedule &current_schedule(int kind) { return g_schedule[kind]; }
 
 int sm_count()

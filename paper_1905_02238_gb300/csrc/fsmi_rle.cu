@@ -53,11 +53,11 @@ __global__ void __launch_bounds__(kWarpsRLE * 32)
     int *S = (int *)(O + stride);
     for (long long ray = (long long)blockIdx.x * kWarpsRLE + warp; ray < nrays; ray += (long long)gridDim.x * kWarpsRLE) {
         const int nr = sample_encode(vx, ray, p.nmax, p.run_cap, O, S);
-        const long long b = run_off[ray];
+        const long long b = run_off[ray];  // saturated at INT32_MAX by the scan, never negative
         bool over = false;
         for (int u = lane; u < nr; u += 32) {
             const long long idx = b + u;
-            if (idx < capacity) {
+            if (idx >= 0 && idx < capacity) {
                 run_o[idx] = O[u];
                 run_len[idx] = (uint8_t)(S[u + 1] - S[u]);
             } else {
@@ -107,29 +107,67 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int32_t *a, long long n, in
     if (threadIdx.x == blockDim.x - 1) tot[blockIdx.x] = run;
 }
 
-// exclusive scan of the tile totals in place (one block, loops over chunks)
-__global__ void __launch_bounds__(1024) k_scan_totals(int32_t *tot, int ntiles)
+// 64-bit inclusive scan across the block (tile totals of up to 1024 tiles of 4096 rays can pass
+// 2^31 runs, so they are summed in 64 bits)
+__device__ __forceinline__ long long block_incl_scan_ll(long long v, long long *wsum)
 {
-    __shared__ int wsum[32];
-    __shared__ int carry;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) x += wsum[warp - 1];
+    __syncthreads();
+    return x;
+}
+
+// Exclusive scan of the tile totals in place (one block, loops over chunks of 1024 tiles), summed
+// in 64 bits. The offsets are int32: a tile whose runs start at or beyond INT32_MAX gets the
+// start INT32_MAX, and FSMI_STATUS_RUN_OVERFLOW is set (k_scan_add saturates the offsets inside a
+// tile the same way), so that no offset wraps to a negative value.
+__global__ void __launch_bounds__(1024) k_scan_totals(int32_t *tot, int ntiles, int *status)
+{
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
+    bool over = false;
     for (int b = 0; b < ntiles; b += 1024) {
         const int i = b + threadIdx.x;
-        const int v = i < ntiles ? tot[i] : 0;
-        const int inc = block_incl_scan(v, wsum);
-        const int c = carry;
-        if (i < ntiles) tot[i] = c + inc - v;
+        const long long v = i < ntiles ? (long long)tot[i] : 0;
+        const long long inc = block_incl_scan_ll(v, wsum);
+        const long long c = carry;
+        if (i < ntiles) {
+            const long long ex = c + inc - v;
+            over |= c + inc > 0x7fffffffLL;
+            tot[i] = (int32_t)min(ex, 0x7fffffffLL);
+        }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = c + inc;
         __syncthreads();
     }
+    if (over) set_status(status, FSMI_STATUS_RUN_OVERFLOW);
 }
 
+// offsets = tile-local inclusive sums + the tile's start, saturated at INT32_MAX
 __global__ void k_scan_add(int32_t *a, long long n, const int32_t *tot)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        a[i] += tot[i / kScanTile];
+        a[i] = (int32_t)min((long long)a[i] + (long long)tot[i / kScanTile], 0x7fffffffLL);
 }
 
 // ---- launchers ---------------------------------------------------------------------------------
@@ -214,7 +252,7 @@ cudaError_t launch_rle_encode_3d(const Vox3D &v, const DevParams &p, int32_t *ru
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan_tiles<<<ntiles, 1024, 0, s>>>(run_off + 1, nrays, ws_tiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_scan_totals<<<1, 1024, 0, s>>>(ws_tiles, ntiles);
+    k_scan_totals<<<1, 1024, 0, s>>>(ws_tiles, ntiles, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     long long ag = (nrays + 255) / 256;
     if (ag > (long long)sm_count() * 8) ag = (long long)sm_count() * 8;

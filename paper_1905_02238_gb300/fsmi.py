@@ -175,6 +175,8 @@ def load():
             "fsmi_device_status": [p, ctypes.POINTER(ctypes.c_int)],
             "fsmi_gauss_tail": [p, p, ll, p],
             "fsmi_rle_encode_3d_noalloc": [p, i, i, i, p, i, p, i, P, p, p, p, i, p],
+            "fsmi_probe": [i, ll, p, sz, p],
+            "fsmi_probe_threads": [i],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -542,6 +544,23 @@ def gauss_tail(s: torch.Tensor) -> torch.Tensor:
     out = torch.empty_like(s)
     _raise(lib.fsmi_gauss_tail(_ptr(s), _ptr(out), s.numel(), _stream()), "fsmi_gauss_tail")
     return m.out(out)
+
+
+PROBE_EX2, PROBE_RCP, PROBE_FMA, PROBE_FMA2, PROBE_READ, PROBE_SPIN = range(6)
+
+
+def probe(kind: int, iters: int, buf: torch.Tensor) -> None:
+    """fsmi_probe: one launch of a measurement kernel (PROBE_*) on the current stream; buf is the
+    sink (ALU probes), the buffer read (PROBE_READ) or the int64 cycle count (PROBE_SPIN)."""
+    lib = load()
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise FsmiError("probe: buf must be a contiguous CUDA tensor")
+    _raise(lib.fsmi_probe(kind, iters, _ptr(buf), buf.numel() * buf.element_size(), _stream()), "fsmi_probe")
+
+
+def probe_threads(kind: int) -> int:
+    """Threads of one fsmi_probe launch of `kind` on the current device."""
+    return int(load().fsmi_probe_threads(kind))
 
 
 def device_status() -> int:

@@ -48,3 +48,30 @@ def test_two_gloo_ranks_shard_poses_and_take_the_slowest_time():
     assert g0 == g1  # on the same (replicated) map
     assert w0 == w1 == 11.0  # the job's time is the slowest rank's
     assert r0 == r1 == 2 * 16 * 360 / 11.0e-3
+
+
+def test_gpus_flag_starts_that_many_ranks():
+    # python bench.py --gpus 2 without a launcher re-launches itself as two torchrun ranks; the
+    # launcher self-check joins them in a gloo group (no GPU work) and reports the count
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--check-ranks"],
+                       capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line == {"check": "ranks", "world_size": 2, "ranks_joined": 2}
+
+
+def test_rank_count_mismatch_fails_loudly():
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, WORLD_SIZE="3", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--check-ranks"],
+                       capture_output=True, text=True, timeout=120, env=env, cwd=root)
+    assert r.returncode == 2 and "WORLD_SIZE=3" in r.stderr

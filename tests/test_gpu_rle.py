@@ -92,6 +92,26 @@ def test_encode_capacity_overflow_is_flagged_and_bounded():
     np.testing.assert_array_equal(rl.cpu().numpy()[:cap], rl_ref[:cap])
 
 
+def test_encode_offsets_saturate_instead_of_wrapping_past_int32():
+    # 2,101,250 rays along +x through a 1024-voxel-long grid, 1024 virtual cells each, runs of one
+    # cell: 2.15e9 runs in all, more than an int32 offset holds. The offsets past INT32_MAX must
+    # saturate there (never wrap negative) and the overflow must be flagged.
+    X, P, R = 1024, 2050, 1025
+    vox = np.random.default_rng(3).uniform(0.2, 0.8, (4, 4, X)).astype(np.float32)
+    pose = np.zeros((P, 12), np.int32)
+    pose[:, 0] = 1 << 14  # x = 0.25 (Q16): samples at x = i + 0.75, i = 0 .. 1023
+    pose[:, 1] = pose[:, 2] = 5 << 15  # y = z = 2.5
+    pose[:, 3] = pose[:, 7] = pose[:, 11] = 1 << 30  # identity rotation (Q30)
+    dirs = np.zeros((R, 3), np.int32)
+    dirs[:, 0] = 1 << 30
+    gp, _ = _prms(max_range=1024.0, run_cap=1)
+    fsmi.device_status()
+    off, _, _ = fsmi.rle_encode_3d(_cuda(vox), _cuda(pose), _cuda(dirs), gp, capacity=0)
+    assert fsmi.device_status() & fsmi.STATUS_RUN_OVERFLOW
+    want = np.minimum(np.arange(P * R + 1, dtype=np.int64) * 1024, 2**31 - 1)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.int64), want)
+
+
 def test_encode_full_size_config3_sampled():
     vox, poses, dirs = synth.config3()
     gp, _ = _prms()

@@ -85,14 +85,42 @@ def test_noalloc_encoder_matches_workspace_encoder_on_consecutive_calls(lib):
         assert torch.equal(a_l[:n], b_l[:n])
 
 
+def test_noalloc_encoder_matches_workspace_encoder_past_one_scan_chunk(lib):
+    # More than 1024 scan tiles of 4096 rays, so that the scan of the tile totals carries between
+    # its chunks of 1024 entries; first the larger batch, then a smaller one, so that the second
+    # call reads only entries it wrote itself.
+    from paper_1905_02238_gb300 import synth
+
+    vox = synth.voxel_world(64, 64, 32, n_boxes=6, seed=9, noise_seed=10, noise_frac=0.1)
+    dirs = torch.from_numpy(synth.pinhole_dirs(64, 64, 90.0)).cuda()
+    v = torch.from_numpy(vox).cuda()
+    prm = _P(0, 2.0, 1.5, 0.67, 6, 4, 6.0, 2, 0, 0, 0, 0)  # 6 virtual cells per ray, runs of at most 2
+    for npose, seed in ((1100, 21), (1030, 22)):
+        poses = torch.from_numpy(synth.free_voxel_poses(vox, npose, seed=seed, zlo=4, zhi=28)).cuda()
+        nrays = npose * dirs.shape[0]
+        assert nrays > 1024 * 4096
+        cap = 6 * nrays
+        a_off, a_o, a_l = _encode(lib, True, v, poses, dirs, prm, cap)
+        b_off, b_o, b_l = _encode(lib, False, v, poses, dirs, prm, cap)
+        assert torch.equal(a_off, b_off)
+        n = int(b_off[-1])
+        assert nrays <= n <= cap
+        assert torch.equal(a_o[:n].view(torch.int32), b_o[:n].view(torch.int32))
+        assert torch.equal(a_l[:n], b_l[:n])
+        del a_o, b_o, a_l, b_l
+
+
 def test_noalloc_encoder_rejects_batches_beyond_its_array(lib):
     vox, poses, dirs = _world(1)
     prm = _P(0, 2.0, 1.5, 0.67, 6, 4, 96.0, 16, 0, 0, 0, 0)
     Z, Y, X = vox.shape
     big_P = (4096 * 4096) // dirs.shape[0] + 1  # P * R just above the limit
+    # a poses buffer that really holds big_P poses: were the host check ever lost, the kernels
+    # would still read only inside it
+    big_poses = poses[torch.arange(big_P, device="cuda") % poses.shape[0]].contiguous()
     out = torch.zeros(4, dtype=torch.int32, device="cuda")
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    st = lib.fsmi_rle_encode_3d_noalloc(ctypes.c_void_p(vox.data_ptr()), X, Y, Z, ctypes.c_void_p(poses.data_ptr()),
+    st = lib.fsmi_rle_encode_3d_noalloc(ctypes.c_void_p(vox.data_ptr()), X, Y, Z, ctypes.c_void_p(big_poses.data_ptr()),
                                         big_P, ctypes.c_void_p(dirs.data_ptr()), dirs.shape[0], ctypes.byref(prm),
                                         ctypes.c_void_p(out.data_ptr()), None, None, 0, s)
     assert st == 2  # FSMI_ERR_CAPACITY, checked on the host: nothing was launched
