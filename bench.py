@@ -39,8 +39,8 @@ FMA_LANES_PER_SM_CLK = 128  # FP32 FMA-pipe lane operations per SM per clock (4 
 EX2_PER_SM_CLK = 32  # SFU ex2.approx results per SM per clock (csrc/pipe_probe.cu measured 31.8)
 RCP_PER_SM_CLK = 16  # SFU rcp.approx results per SM per clock (measured 15.95)
 SFU_CLK_PER_TERM = 1.0 / EX2_PER_SM_CLK + 1.0 / RCP_PER_SM_CLK  # one ex2 and one rcp per tail term
-OPS_PER_TERM = 11  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh): distance,
-#                    square, 1 + p|d|, 5 Horner FMAs, two products, accumulate
+OPS_PER_TERM = 10  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss_tail.cuh): distance,
+#                    square, 1 + p|d|, 4 Horner FMAs, two products, accumulate
 TAIL_CUT = 4.81  # scaled half-width of the exact kernel's default window (csrc/eval2d.cuh)
 
 # DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an

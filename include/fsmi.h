@@ -336,8 +336,8 @@ fsmi_status fsmi_eval_3d(const float *vox, int X, int Y, int Z, const int32_t *p
  * fsmi_gauss_tail - the library's Gaussian tail, exposed so its accuracy can be tested:
  *   out[i] = 0.5 * erfc(s[i] / sqrt(log2 e)) for s[i] >= 0 (float32, device arrays of n).
  * The pair sums of the Gaussian variants (Theorem 1, eq. fsmi_approx) evaluate
- * G_{k,j} = Phi(x_{k+1}) - Phi(x_k) through this tail. Absolute error <= 2e-7; <= 1e-6 of the
- * value plus 2e-8 everywhere.
+ * G_{k,j} = Phi(x_{k+1}) - Phi(x_k) through this tail. Absolute error <= 3e-7; <= 4e-6 of the
+ * value plus 6e-8 everywhere.
  */
 fsmi_status fsmi_gauss_tail(const float *s, float *out, long long n, fsmi_stream_t stream);
 

@@ -92,11 +92,15 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int b
         }                                                                            \
         ++cnt;                                                                       \
     } while (0)
-    for (int k = k0; k <= k1; ++k) {
-        FSMI_EMIT(k < 0 ? 0.0f : (float)(g.nM0 + (unsigned)k * 65536u) * g.rM);
-        const unsigned nMn = g.nM0 + (unsigned)(k + 1) * 65536u;  // next major crossing
-        unsigned nmi = g.nm0 + (unsigned)i * 65536u;              // next minor crossing
-        if (g.am && mulw(nmi, g.aM) < mulw(nMn, g.am)) {         // minor crossing inside
+    // crossings are compared as nm(i) aM against nM(k + 1) am; both products advance by constant
+    // steps (aM 2^16 per minor crossing, am 2^16 per interval), so the loop multiplies nothing
+    unsigned nMn = g.nM0 + (unsigned)(k0 + 1) * 65536u;  // next major crossing
+    unsigned nmi = g.nm0 + (unsigned)i * 65536u;         // next minor crossing
+    unsigned long long pm = mulw(nmi, g.aM), pM = mulw(nMn, g.am);
+    const unsigned long long dm = (unsigned long long)g.aM << 16, dM = (unsigned long long)g.am << 16;
+    for (int k = k0; k <= k1; ++k, nMn += 65536u, pM += dM) {
+        FSMI_EMIT(k < 0 ? 0.0f : (float)(nMn - 65536u) * g.rM);
+        if (g.am && pm < pM) {  // minor crossing inside
             if (nmi >= g.Lm) {
                 ended = true;
                 endl = g.R;
@@ -112,6 +116,7 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int b
             FSMI_EMIT((float)nmi * g.rm);
             ++i;
             nmi += 65536u;
+            pm += dm;
         }
         if (nMn >= g.LM) {
             ended = true;
@@ -119,11 +124,13 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int b
             by_range = true;
             break;
         }
-        const bool tie = g.am && (mulw(nmi, g.aM) == mulw(nMn, g.am));
+        const bool tie = g.am && pm == pM;
         cM += g.sM;
         if (tie) {
             cm += g.sm;
             ++i;
+            nmi += 65536u;
+            pm += dm;
             ++ties;
         }
         if ((unsigned)cM >= (unsigned)g.dimM || (unsigned)cm >= (unsigned)g.dimm) {

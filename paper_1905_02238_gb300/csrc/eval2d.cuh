@@ -27,24 +27,26 @@ namespace fsmi {
 
 // ---- pair sums ------------------------------------------------------------------------------------
 
-// per-warp shared arrays, in units of `stride` floats: l, C, P, scratch (ids / f_emp / D / dC)
+// per-warp shared arrays, in units of `stride` floats: l, scratch (ids / f_emp / D / dC), C, P
 constexpr int kArrays2D = 4;
-// Padding boundaries before index 0 and after index n + 1 of l and dC (l = -+3e30, dC = 0: their
-// terms are exactly zero), so that the exact window loops can run past a beam's ends.
+// Padding boundaries before index 0 and after index n + 1 of the exact sum's boundary pairs
+// (l = -+3e30, dC = 0: their terms are exactly zero), so that its loops can run past a beam's ends.
 constexpr int kPad2D = 32;
+constexpr int kPadPairs = kPad2D / 2;
 
 // Floats between consecutive arrays for beams of up to nmax cells (n + 2 boundaries + padding).
 __host__ __device__ constexpr int stride_2d(int nmax) { return ((nmax + 2 + kPad2D) + 3) & ~3; }
-// Floats of one warp's arrays: kArrays2D strides and the front padding of l and dC.
+// Floats of one warp's arrays: kArrays2D strides and the front padding of the boundary pairs.
 __host__ __device__ constexpr int warp_floats_2d(int stride) { return kArrays2D * stride + 2 * kPad2D; }
 
-// One warp's arrays in its region `base` (16-byte aligned): [pad | l | C | P | pad | scratch].
+// One warp's arrays in its region `base` (16-byte aligned): [pad | l | scratch | C | P]. The pad,
+// l and scratch arrays are contiguous: the exact sum rebuilds them in place as boundary pairs.
 __device__ __forceinline__ void carve_2d(float *base, int stride, float *&sl, float *&sc, float *&sp, float *&sx)
 {
-    sl = base + kPad2D;
-    sc = sl + stride;
+    sl = base + 2 * kPad2D;
+    sx = sl + stride;
+    sc = sx + stride;
     sp = sc + stride;
-    sx = sp + stride + kPad2D;
 }
 // internal variant id of the full n(n+1) exact sweep (FSMI_FLAG_FULL_SWEEP)
 constexpr int kExactFullSweep = 3;
@@ -75,73 +77,6 @@ struct Src2D {
     const int32_t *stamp;
 };
 
-// One register-blocked pass of the exact pair sum over scaled distances: each lane owns J
-// first-hit slots j = jb + lane + 32 t and streams every boundary m = 0..n from shared memory.
-// Slot n is the no-return event when e0 is set (centre mu0, C_0 = 0). Terms of even and odd m
-// accumulate separately, each in increasing m, and are added at the end (the order the window
-// sum uses, so that the two agree bit for bit).
-template <int J>
-__device__ __forceinline__ float exact_pass(const float *sl, const float *sc, const float *sp, int n, int jb,
-                                            bool e0, float pe0, float mu0)
-{
-    const int lane = lane_id();
-    float mu[J], acc[J], acc1[J];
-    int mid[J];  // boundaries m < mid lie before the centre
-#pragma unroll
-    for (int t = 0; t < J; ++t) {
-        const int j = jb + lane + 32 * t;
-        mu[t] = (j < n) ? 0.5f * (sl[j] + sl[j + 1]) : ((j == n && e0) ? mu0 : 3.0e30f);
-        mid[t] = (j < n) ? j + 1 : 0;
-        acc[t] = 0.0f;
-        acc1[t] = 0.0f;
-    }
-    float cprev = 0.0f;
-    for (int m = 0; m <= n; ++m) {
-        const float lm = sl[m];
-        const float cm = sc[m];  // sc[n] = 0 (C_{n+1})
-        const float dc = cm - cprev;
-        cprev = cm;
-        if (m & 1) {
-#pragma unroll
-            for (int t = 0; t < J; ++t) acc1[t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc1[t]);
-        } else {
-#pragma unroll
-            for (int t = 0; t < J; ++t) acc[t] = fmaf(m < mid[t] ? -dc : dc, gauss_tail(lm - mu[t]), acc[t]);
-        }
-    }
-    float r = 0.0f;
-#pragma unroll
-    for (int t = 0; t < J; ++t) {
-        const int j = jb + lane + 32 * t;
-        const float a = acc[t] + acc1[t];
-        if (j < n)
-            r = fmaf(sp[j], sc[j] + a, r);
-        else if (j == n && e0)
-            r = fmaf(pe0, a, r);
-    }
-    return r;
-}
-
-__device__ __forceinline__ float exact_sum(const float *sl, const float *sc, const float *sp, int n, bool e0,
-                                           float pe0, float mu0)
-{
-    const int nslots = n + (e0 ? 1 : 0);
-    float r = 0.0f;
-    for (int jb = 0; jb < nslots; jb += 32 * 16) {
-        const int cnt = min(16, (nslots - jb + 31) >> 5);
-        switch (cnt) {
-#define FSMI_CASE(J) \
-    case J: r += exact_pass<J>(sl, sc, sp, n, jb, e0, pe0, mu0); break;
-            FSMI_CASE(1) FSMI_CASE(2) FSMI_CASE(3) FSMI_CASE(4) FSMI_CASE(5) FSMI_CASE(6) FSMI_CASE(7) FSMI_CASE(8)
-            FSMI_CASE(9) FSMI_CASE(10) FSMI_CASE(11) FSMI_CASE(12) FSMI_CASE(13) FSMI_CASE(14) FSMI_CASE(15)
-            FSMI_CASE(16)
-#undef FSMI_CASE
-            default: break;
-        }
-    }
-    return r;
-}
-
 // Largest scaled distance whose tail is not flushed to zero: beyond |d| = 11.3 the factor
 // 2^(-d^2) <= 2^(-127.69) is subnormal and ex2.approx.ftz returns exactly 0, so the term is +-0.
 constexpr float kTailCut = 11.3f;
@@ -152,94 +87,116 @@ constexpr float kTailCut = 11.3f;
 // for sigma <= 2.
 constexpr float kTailCutDefault = 4.81f;
 
-// Boundary terms of one first-hit cell with centre mu over the pairs (m, m + 1), m = m0, m0 + 2,
-// ... < end (m0, nb and end even, m0 <= nb <= end), so that every term goes through the packed
-// tail; the pairs below nb lie before the centre, the pair at nb straddles it when mid is odd.
-// A boundary m < mid lies before the centre: -dC_m T(mu - l_m); above it +dC_m T(l_m - mu).
-// Padding boundaries (l = -+3e30, dC = 0) give exact zeros. Returns the packed sums over even and
-// odd m, each added in increasing m.
+// ---- the exact pair sum over boundary pairs ------------------------------------------------------
+//
+// Boundary pairs: Q[P] = (l_{2P}, l_{2P+1}, dC_{2P}, dC_{2P+1}) with scaled distances l and
+// dC_m = C_m - C_{m-1} (C_{-1} = C_n = 0), for P in [-kPadPairs, n / 2 + 1 + kPadPairs); pairs
+// past either end of the beam are padding (l = -+3e30, dC = 0). One 16-byte shared load gives a
+// pair's two distances and two weights.
+//
+// Built in place over the traversal's distances sl and the scratch array after them (ids, then
+// f_emp, both dead by now), from the top pair down: writing Q[P] overwrites l_{4P} .. l_{4P+3},
+// which only Q[2P] and Q[2P+1] read, and those lie higher (P >= 1) or in the same step of 32 pairs,
+// whose reads all come before its writes.
+__device__ __forceinline__ void build_pairs(float *sl, const float *sc, int n, float cs)
+{
+    const int lane = lane_id();
+    float4 *Q = reinterpret_cast<float4 *>(sl);
+    const int pend = (n >> 1) + 1 + kPadPairs;  // pairs 0 .. pend - 1 (the last kPadPairs all padding)
+    for (int top = pend; top > 0; top -= 32) {
+        const int P = top - 32 + lane;
+        float4 v = make_float4(3.0e30f, 3.0e30f, 0.0f, 0.0f);
+        if (P >= 0) {
+            const int m = 2 * P;
+            if (m <= n) {
+                const float c0 = sc[m], cm = m > 0 ? sc[m - 1] : 0.0f;  // sc[n] = C_n = 0
+                v.x = sl[m] * cs;
+                v.z = c0 - cm;
+                if (m + 1 <= n) {
+                    v.y = sl[m + 1] * cs;
+                    v.w = sc[m + 1] - c0;
+                }
+            }
+        }
+        __syncwarp();
+        if (P >= 0) Q[P] = v;
+        __syncwarp();
+    }
+    if (lane < kPadPairs) Q[-1 - lane] = make_float4(-3.0e30f, -3.0e30f, 0.0f, 0.0f);
+    __syncwarp();
+}
+
+// Boundary terms of the pairs (m, m + 1), m even, for the first-hit centre mu: below it (NEG)
+// -dC_m T(mu - l_m), above it +dC_m T(l_m - mu), two terms per packed operation.
 #ifndef FSMI_PAIR_UNROLL
 #define FSMI_PAIR_UNROLL 4
 #endif
-constexpr int kPairUnroll = FSMI_PAIR_UNROLL;  // boundary pairs in flight per lane, exact window loop
+#ifndef FSMI_PAIR2_UNROLL
+#define FSMI_PAIR2_UNROLL 2
+#endif
+constexpr int kPairUnroll = FSMI_PAIR_UNROLL;    // boundary pairs in flight per lane, one slot per lane
+constexpr int kPair2Unroll = FSMI_PAIR2_UNROLL;  // the same, two slots per lane (twice the work per pair)
 
-__device__ __forceinline__ f32x2 window_terms(const float *sl, const float *sdc, int m, int nb, int end, int mid, float mu)
+template <bool NEG>
+__device__ __forceinline__ f32x2 pair_term(const float4 &q, f32x2 mu2, f32x2 acc)
 {
-    const f32x2 mu2 = pack2(mu, mu);
-    f32x2 acc = pack2(0.0f, 0.0f);
-#pragma unroll kPairUnroll
-    for (; m < nb; m += 2) {  // pairs (m, m + 1) with m + 1 < mid
-        const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
-        const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
-        acc = fma2(dc, gauss_tail2p<true>(sub2(mu2, L)), acc);
-    }
-    if (m < end) {  // first pair at or above the centre; m lies below it when m == mid - 1
-        const float2 L = *reinterpret_cast<const float2 *>(sl + m);
-        const float2 dc = *reinterpret_cast<const float2 *>(sdc + m);
-        const bool below = m == mid - 1;
-        const float d0 = below ? mu - L.x : L.x - mu;
-        const float c0 = below ? -dc.x : dc.x;
-        acc = fma2(pack2(c0, dc.y), gauss_tail2p<false>(pack2(d0, L.y - mu)), acc);
-        m += 2;
-    }
-#pragma unroll kPairUnroll
-    for (; m < end; m += 2) {
-        const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
-        const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
-        acc = fma2(dc, gauss_tail2p<false>(sub2(L, mu2)), acc);
-    }
-    return acc;
+    const f32x2 L = pack2(q.x, q.y), dc = pack2(q.z, q.w);
+    return fma2(dc, gauss_tail2p<NEG>(NEG ? sub2(mu2, L) : sub2(L, mu2)), acc);
 }
 
-// Exact pair sum over the boundaries within the window: for slot j at least the m with
-// |l_m - mu_j| < cut (scaled) are visited, in increasing m. With cut = kTailCut every non-zero
-// term of the full sweep is added in the same order and the FP32 result is the same bit for bit;
-// with kTailCutDefault the terms skipped are below 2^-27 of their weights.
-// The 32 slots of a round run the same number of pairs below and above their centres: the
-// fewest pairs G that cover every slot's window on that side. A slot whose window is shorter adds
-// the next boundaries beyond it, which are terms of the full sum too (or padding with weight 0),
-// so that no lane leaves the unrolled loops at a different point than the others. No window end is
-// searched for: with the pairs below the centre starting at nb - 2G, a slot is covered when the
-// boundary before that start lies below mu - cut (one shared load per lane and trial G), and the
-// trials start from the previous round's G, which changes little along a beam.
-// sdc[m] = C_m - C_{m-1} for m = 0..n; sl and sdc padded by kPad2D entries on both sides.
-__device__ __forceinline__ float exact_window_sum(const float *sl, const float *sdc, const float *sc,
-                                                  const float *sp, int n, bool e0, float pe0, float mu0, float cut)
+// the pair (m, m + 1) that straddles the centre: m below it, m + 1 above
+__device__ __forceinline__ f32x2 straddle_term(const float4 &q, float mu, f32x2 acc)
 {
+    return fma2(pack2(-q.z, q.w), gauss_tail2p<false>(pack2(mu - q.x, q.y - mu)), acc);
+}
+
+// Exact pair sum (Theorem 1) of one beam over the boundary pairs Q: for every first-hit slot j at
+// least the boundaries with |l_m - mu_j| < cut (scaled) are visited, in increasing m, even and odd
+// m in the two halves of a packed accumulator. With cut = kTailCut every non-zero term of the full
+// sweep is added, in the same order, so the FP32 result equals the full sweep (cut = +inf) bit for
+// bit; with kTailCutDefault the terms skipped are below 2^-27 of their weights.
+//
+// Slots go in rounds of 64 while more than 32 remain: lane i takes the adjacent slots A = jb + 2i
+// and B = A + 1 and evaluates both against each pair it loads. Pairs below A (m < A) lie below both
+// centres, the pair at m = A straddles A's centre and lies below B's, pairs from A + 2 on lie above
+// both. The last <= 32 slots (and the no-return slot n when e0 is set: centre mu0 before l_0, every
+// boundary above it) go one per lane. In every round all lanes run the same number of pairs below
+// and above (the fewest that cover every window of the round), so that no lane leaves the unrolled
+// loops early; a lane whose window is shorter adds boundaries beyond it, which are terms of the
+// full sum as well (or padding). The counts come from coverage trials that start from the previous
+// round's: below, a count G covers a slot when the boundary just before the loop's first pair lies
+// below mu - cut; above, when the boundary just after its last pair lies at or beyond mu + cut.
+__device__ __forceinline__ float exact_pairs_sum(const float4 *Q, const float *sc, const float *sp, int n, bool e0,
+                                                 float pe0, float mu0, float cut)
+{
+    const int lane = lane_id();
+    const float *Qf = reinterpret_cast<const float *>(Q);
+    auto lq = [&](int m) { return Qf[4 * (m >> 1) + (m & 1)]; };  // l_m (m >> 1 floors negative m)
     const int nslots = n + (e0 ? 1 : 0);
+    const int mtop = ((n >> 1) + 1 + kPadPairs) * 2;  // pairs (m, m + 1) stay below this m
     // first trial: about cut x (boundaries per unit of scaled distance) boundaries on each side
-    const float span = sl[n] - sl[0];
+    const float span = lq(n) - lq(0);
     const float per = span > 0.0f ? (float)n / span : 0.0f;
     int GN = (int)fminf(cut * per, (float)(n + 1)) >> 1, GP = GN;
-    const int mtop = (n + 1 + kPad2D) & ~1;  // pairs (m, m + 1) stay below n + 2 + kPad2D
     float r = 0.0f;
-    for (int jb = 0; jb < nslots; jb += 32) {
-        const int j = jb + lane_id();
-        const bool act = j < nslots;
-        float mu = 0.0f, Cj = 0.0f, Pj = 0.0f;
-        int mid = 0;
-        if (act && j < n) {
-            mu = 0.5f * (sl[j] + sl[j + 1]);
-            Cj = sc[j];
-            Pj = sp[j];
-            mid = j + 1;
-        } else if (act) {  // the no-return slot: centre before l_0, every boundary above it
-            mu = mu0;
-            Pj = pe0;
-        }
-        const int nb = mid & ~1;  // pairs (m, m + 1) with m + 1 < mid end here
-        const float below = mu - cut, above = mu + cut;
-        // below the centre: covered at G when every boundary before nb - 2G lies below mu - cut
-        // (true for every G once nb - 2G <= 0, so both loops end)
+    int jb = 0;
+    // ---- two adjacent slots per lane ----
+    for (; n - jb > 32; jb += 64) {
+        const int j = jb + 2 * lane;
+        const bool actA = j < n, actB = j + 1 < n;
+        const int a = actA ? j : jb;  // an idle lane shadows slot jb with zero weight
+        const float4 q0 = Q[a >> 1];  // l_a, l_{a+1}, dC_a, dC_{a+1}
+        const float muA = 0.5f * (q0.x + q0.y), muB = 0.5f * (q0.y + Qf[4 * ((a >> 1) + 1)]);
+        const float2 Cs = *reinterpret_cast<const float2 *>(sc + a);
+        const float2 Ps = *reinterpret_cast<const float2 *>(sp + a);
+        const float below = muA - cut, above = (actB ? muB : muA) + cut;
         auto neg_ok = [&](int G) {
-            const int m = nb - 2 * G;
-            return !act || m <= 0 || sl[m - 1] < below;
+            const int m = a - 2 * G;
+            return !actA || m <= 0 || lq(m - 1) < below;
         };
-        // above it: covered when every boundary from nb + 2 + 2G on lies at or beyond mu + cut
-        // (true once that index passes n)
         auto pos_ok = [&](int G) {
-            const int e = nb + 2 + 2 * G;
-            return !act || e > n || sl[e] >= above;
+            const int e = a + 2 + 2 * G;
+            return !actA || e > n || lq(e) >= above;
         };
         if (__all_sync(kFull, neg_ok(GN))) {
             while (GN > 0 && __all_sync(kFull, neg_ok(GN - 1))) --GN;
@@ -253,10 +210,83 @@ __device__ __forceinline__ float exact_window_sum(const float *sl, const float *
             do ++GP;
             while (!__all_sync(kFull, pos_ok(GP)));
         }
-        const int m0 = act ? max(nb - 2 * GN, -kPad2D) : 0;
+        const f32x2 muA2 = pack2(muA, muA), muB2 = pack2(muB, muB);
+        f32x2 accA = pack2(0.0f, 0.0f), accB = pack2(0.0f, 0.0f);
+        int m = max(a - 2 * GN, -kPad2D);
+#pragma unroll kPair2Unroll
+        for (; m < a; m += 2) {
+            const float4 q = Q[m >> 1];
+            accA = pair_term<true>(q, muA2, accA);
+            accB = pair_term<true>(q, muB2, accB);
+        }
+        accA = straddle_term(q0, muA, accA);
+        accB = pair_term<true>(q0, muB2, accB);
+        const int end = min(a + 2 + 2 * GP, mtop);
+#pragma unroll kPair2Unroll
+        for (m = a + 2; m < end; m += 2) {
+            const float4 q = Q[m >> 1];
+            accA = pair_term<false>(q, muA2, accA);
+            accB = pair_term<false>(q, muB2, accB);
+        }
+        float a0, a1, b0, b1;
+        unpack2(accA, a0, a1);
+        unpack2(accB, b0, b1);
+        r = fmaf(actA ? Ps.x : 0.0f, Cs.x + (a0 + a1), r);
+        r = fmaf(actB ? Ps.y : 0.0f, Cs.y + (b0 + b1), r);
+    }
+    // ---- one slot per lane ----
+    for (; jb < nslots; jb += 32) {
+        const int j = jb + lane;
+        const bool act = j < nslots;
+        float mu = 0.0f, Cj = 0.0f, Pj = 0.0f;
+        int mid = 0;
+        if (act && j < n) {
+            mu = 0.5f * (lq(j) + lq(j + 1));
+            Cj = sc[j];
+            Pj = sp[j];
+            mid = j + 1;
+        } else if (act) {  // the no-return slot: centre before l_0, every boundary above it
+            mu = mu0;
+            Pj = pe0;
+        }
+        const int nb = mid & ~1;  // pairs (m, m + 1) with m + 1 < mid end here
+        const float below = mu - cut, above = mu + cut;
+        auto neg_ok = [&](int G) {
+            const int m = nb - 2 * G;
+            return !act || m <= 0 || lq(m - 1) < below;
+        };
+        auto pos_ok = [&](int G) {
+            const int e = nb + 2 + 2 * G;
+            return !act || e > n || lq(e) >= above;
+        };
+        if (__all_sync(kFull, neg_ok(GN))) {
+            while (GN > 0 && __all_sync(kFull, neg_ok(GN - 1))) --GN;
+        } else {
+            do ++GN;
+            while (!__all_sync(kFull, neg_ok(GN)));
+        }
+        if (__all_sync(kFull, pos_ok(GP))) {
+            while (GP > 0 && __all_sync(kFull, pos_ok(GP - 1))) --GP;
+        } else {
+            do ++GP;
+            while (!__all_sync(kFull, pos_ok(GP)));
+        }
+        const f32x2 mu2 = pack2(mu, mu);
+        f32x2 acc = pack2(0.0f, 0.0f);
+        int m = act ? max(nb - 2 * GN, -kPad2D) : 0;
+        const int nbe = act ? nb : 0;
+#pragma unroll kPairUnroll
+        for (; m < nbe; m += 2) acc = pair_term<true>(Q[m >> 1], mu2, acc);
         const int end = act ? min(nb + 2 + 2 * GP, mtop) : 0;
+        if (m < end) {  // the pair at nb: it straddles the centre when mid is odd, else lies above it
+            const float4 q = Q[m >> 1];
+            acc = (m == mid - 1) ? straddle_term(q, mu, acc) : pair_term<false>(q, mu2, acc);
+            m += 2;
+        }
+#pragma unroll kPairUnroll
+        for (; m < end; m += 2) acc = pair_term<false>(Q[m >> 1], mu2, acc);
         float a0, a1;
-        unpack2(window_terms(sl, sdc, m0, nb, end, mid, mu), a0, a1);
+        unpack2(acc, a0, a1);
         r = fmaf(Pj, Cj + (a0 + a1), r);
     }
     return r;
@@ -400,14 +430,31 @@ __device__ __forceinline__ int beam_cells(const float *__restrict__ map, int W, 
     const unsigned ncell = (unsigned)W * (unsigned)H;
     bool bad = false;
     if (gains) {
-        for (int i = lane; i < n; i += 32) {
-            const unsigned id = (unsigned)((const int *)sx)[i];
-            bad |= id >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
-            float4 v = id < ncell ? __ldg(gains + id) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (TRAJ && id < ncell && __ldg(stamps + id) < state) v.y = v.z = 0.0f;
-            sp[i] = v.x;
-            sc[i] = v.y;
-            sx[i] = v.z;
+        // four cells per lane in flight: all ids, then all gathers, then all stores
+        constexpr int kG = 4;
+        for (int i0 = lane; i0 < n; i0 += 32 * kG) {
+            unsigned id[kG];
+            float4 v[kG];
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                const int i = i0 + 32 * k;
+                id[k] = i < n ? (unsigned)((const int *)sx)[i] : ncell;
+                bad |= i < n && id[k] >= ncell;  // cannot happen for a consistent traversal; never read out of bounds
+            }
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                v[k] = id[k] < ncell ? __ldg(gains + id[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (TRAJ && id[k] < ncell && __ldg(stamps + id[k]) < state) v[k].y = v[k].z = 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                const int i = i0 + 32 * k;
+                if (i < n) {
+                    sp[i] = v[k].x;
+                    sc[i] = v[k].y;
+                    sx[i] = v[k].z;
+                }
+            }
         }
     } else {
         for (int i = lane; i < n; i += 32) {
@@ -437,27 +484,19 @@ __device__ __forceinline__ float beam_sum(const DevParams &p, int n, float *sl, 
     const float cs = p.inv_s2 * (float)kSqrtLog2e;  // distance -> tail variable
     float I = 0.0f;
     if (n > 0) {
-        if (VAR != FSMI_UNIFORM) {
-            for (int i = lane; i <= n; i += 32) sl[i] *= cs;
-        }
         const float pe0 = cell_prefixes(sp, sc, sx, n, VAR == FSMI_UNIFORM);
-        const float mu0 = sl[0] - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
-        if (VAR == kExactFullSweep) I = exact_sum(sl, sc, sp, n, e0, pe0, mu0);
-        if (VAR == FSMI_EXACT) {
-            for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
-            for (int i = lane; i < kPad2D; i += 32) {  // padding boundaries on both sides, weight 0
-                sl[-1 - i] = -3.0e30f;
-                sx[-1 - i] = 0.0f;
-                sl[n + 1 + i] = 3.0e30f;
-                sx[n + 1 + i] = 0.0f;
-            }
-            __syncwarp();
-            I = exact_window_sum(sl, sx, sc, sp, n, e0, pe0, mu0,
-                                 (p.flags & FSMI_FLAG_FULL_WINDOW) ? kTailCut : kTailCutDefault);
+        if (VAR == FSMI_EXACT || VAR == kExactFullSweep) {
+            const float mu0 = sl[0] * cs - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
+            build_pairs(sl, sc, n, cs);
+            float cut = VAR == kExactFullSweep ? __int_as_float(0x7f800000) : kTailCutDefault;
+            if (VAR == FSMI_EXACT && (p.flags & FSMI_FLAG_FULL_WINDOW)) cut = kTailCut;
+            I = exact_pairs_sum(reinterpret_cast<const float4 *>(sl), sc, sp, n, e0, pe0, mu0, cut);
         }
         if (VAR == FSMI_APPROX) {
+            for (int i = lane; i <= n; i += 32) sl[i] *= cs;
             for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
             __syncwarp();
+            const float mu0 = sl[0] - 0.5f * cs;
             I = approx_sum(sl, sc, sx, sp, n, e0, pe0, mu0, p.trunc);
         }
         if (VAR == FSMI_UNIFORM) I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);

@@ -5,7 +5,7 @@
 The form is the classical rational-substitution approximation of erfc (Hastings; Abramowitz and
 Stegun 7.1.26 use erfc(z) ~= t (a1 + a2 t + ...) exp(-z^2), t = 1/(1 + p z)); the variable is
 scaled so that the exponential is a single base-2 exponential. The coefficients here are our own:
-a degree-5 P minimising the maximum ABSOLUTE error of T over s in [0, 80] (Lawson-weighted least
+a degree-4 P minimising the maximum ABSOLUTE error of T over s in [0, 80] (Lawson-weighted least
 squares in a Chebyshev basis, then converted to monomials for Horner's rule), with p scanned.
 Absolute error is the right measure for the pair sums: each term is a tail mass weighted by a
 bounded coefficient, so far-tail terms need only be tiny, not relatively accurate.
@@ -16,7 +16,7 @@ import numpy as np
 from scipy.special import erfc, erfcx
 
 K = np.sqrt(np.log2(np.e))
-DEGREE = 5
+DEGREE = 4
 
 
 def lawson(B, target, w, iters=300):
@@ -49,7 +49,7 @@ def fp32_check(p, coef):
     e = np.float32(2.0 ** (-(s * s)).astype(np.float64))
     T = (e * t) * q
     err = np.abs(T.astype(np.float64) - ref)
-    return err.max(), (err <= 1e-6 * ref + 2e-8).all()
+    return err.max(), (err <= 3e-6 * ref + 5e-8).all()
 
 
 def main():
@@ -61,7 +61,7 @@ def main():
     p, err, coef = best
     coef32 = [float(np.float32(c)) for c in coef]
     amax, ok = fp32_check(p, coef32)
-    print(f"// p = {p!r}, fit max |T error| = {err:.2e}, FP32 max |T error| = {amax:.2e}, within 1e-6 T + 2e-8: {ok}")
+    print(f"// p = {p!r}, fit max |T error| = {err:.2e}, FP32 max |T error| = {amax:.2e}, within 3e-6 T + 5e-8: {ok}")
     print(f"constexpr float kTailP = {p!r}f;")
     for i, c in enumerate(coef32):
         print(f"constexpr float kTailC{i} = {c!r}f;")

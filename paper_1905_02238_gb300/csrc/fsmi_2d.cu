@@ -6,10 +6,10 @@ namespace fsmi {
 // Persistent kernel: each warp evaluates beams one at a time, either in a static grid-stride
 // order or, with a work queue, taking `chunk` consecutive beams per atomic grab (balances beams
 // of very different lengths). The queue counter must be zero at launch.
-// The window, approx and uniform sums fit in 64 registers (8 resident blocks of 4 warps, the
-// shared-memory limit as well); the full sweep's register-blocked pass needs more.
+// Every variant fits in 64 registers (8 resident blocks of 4 warps, the shared-memory limit as
+// well); the full sweep is the exact window loop with an unbounded window.
 template <int VAR, int SRC>
-__global__ void __launch_bounds__(kMaxWarps * 32, VAR == kExactFullSweep ? 1 : FSMI_MIN_BLOCKS_2D)
+__global__ void __launch_bounds__(kMaxWarps * 32, FSMI_MIN_BLOCKS_2D)
     k_eval_2d(Src2D src, DevParams p, long long nbeams, int stride, float *__restrict__ out, int *status,
               unsigned long long *queue, int chunk)
 {

@@ -4,25 +4,27 @@
 //   T(s) = 0.5 * erfc(s / sqrt(log2 e)) ~= 2^(-s^2) * t * P(t),  t = 1 / (1 + p s),  s >= 0,
 //
 // the rational-substitution form of erfc (Hastings; Abramowitz and Stegun 7.1.26) with our own
-// degree-5 coefficients, fitted for minimum absolute error of T by csrc/fit_gauss_tail.py:
-// |T - exact| <= 4.0e-9 in exact arithmetic, <= 1.6e-7 (about 2 ulp of T(0) = 0.5) when
-// evaluated in FP32, and <= 1e-6 T + 2e-8 everywhere. A pair sum adds at most a few dozen such
-// terms per cell with bounded weights, so the tail contributes < 1e-6 relative error to an MI. The variable s is a distance scaled by
-// sqrt(log2 e) / (sigma sqrt 2), so that exp(-z^2) = 2^(-s^2).
+// degree-4 coefficients, fitted for minimum absolute error of T by csrc/fit_gauss_tail.py:
+// |T - exact| <= 6.4e-8 in exact arithmetic, <= 2.3e-7 (about 4 ulp of T(0) = 0.5) when
+// evaluated in FP32, and <= 3e-6 T + 5e-8 everywhere. A pair sum adds a few dozen such terms per
+// cell with weights bounded by the cell's C values, so the tail contributes a few 1e-6 relative
+// error to an MI at most, against the 1e-4 per-beam bar. (Degree 5 reaches 4e-9 in exact
+// arithmetic but not below FP32 rounding, 1.6e-7, and costs one more packed FMA per pair of
+// terms.) The variable s is a distance scaled by sqrt(log2 e) / (sigma sqrt 2), so that
+// exp(-z^2) = 2^(-s^2).
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace fsmi {
 
-// p = 0.325, fit max |T error| = 3.95e-09, FP32 max |T error| = 1.59e-07
-constexpr float kTailP = 0.32499998807907104f;
-constexpr float kTailC0 = 0.11761387437582016f;
-constexpr float kTailC1 = 0.046889495104551315f;
-constexpr float kTailC2 = 0.32172489166259766f;
-constexpr float kTailC3 = -0.31325554847717285f;
-constexpr float kTailC4 = 0.44042205810546875f;
-constexpr float kTailC5 = -0.11339477449655533f;
+// p = 0.39, fit max |T error| = 6.31e-08, FP32 max |T error| = 2.06e-07
+constexpr float kTailP = 0.38999998569488525f;
+constexpr float kTailC0 = 0.12250055372714996f;
+constexpr float kTailC1 = 0.2031688690185547f;
+constexpr float kTailC2 = -0.08829671889543533f;
+constexpr float kTailC3 = 0.3726899027824402f;
+constexpr float kTailC4 = -0.11006267368793488f;
 
 // sqrt(log2(e)): converts z = x / (sigma sqrt 2) into s = z sqrt(log2 e).
 constexpr double kSqrtLog2e = 1.2011224087864498;
@@ -46,8 +48,7 @@ __device__ __forceinline__ float gauss_tail(float d)
 {
     const float e = ex2_approx(-(d * d));
     const float t = rcp_approx(fmaf(kTailP, fabsf(d), 1.0f));
-    float q = kTailC5;
-    q = fmaf(q, t, kTailC4);
+    float q = kTailC4;
     q = fmaf(q, t, kTailC3);
     q = fmaf(q, t, kTailC2);
     q = fmaf(q, t, kTailC1);
@@ -106,8 +107,7 @@ __device__ __forceinline__ f32x2 gauss_tail2p(f32x2 d)
     const float e0 = ex2_approx(-dd0), e1 = ex2_approx(-dd1);
     unpack2(fma2(pack2(kTailP, kTailP), d, pack2(1.0f, 1.0f)), den0, den1);
     const f32x2 t = pack2(rcp_approx(den0), rcp_approx(den1));
-    f32x2 q = fma2(pack2(sg * kTailC5, sg * kTailC5), t, pack2(sg * kTailC4, sg * kTailC4));
-    q = fma2(q, t, pack2(sg * kTailC3, sg * kTailC3));
+    f32x2 q = fma2(pack2(sg * kTailC4, sg * kTailC4), t, pack2(sg * kTailC3, sg * kTailC3));
     q = fma2(q, t, pack2(sg * kTailC2, sg * kTailC2));
     q = fma2(q, t, pack2(sg * kTailC1, sg * kTailC1));
     q = fma2(q, t, pack2(sg * kTailC0, sg * kTailC0));
@@ -122,8 +122,7 @@ __device__ __forceinline__ void gauss_tail2(f32x2 d, float &T0, float &T1)
     const float e0 = ex2_approx(-dd0), e1 = ex2_approx(-dd1);
     unpack2(fma2(pack2(kTailP, kTailP), d, pack2(1.0f, 1.0f)), den0, den1);
     const f32x2 t = pack2(rcp_approx(den0), rcp_approx(den1));
-    f32x2 q = fma2(pack2(kTailC5, kTailC5), t, pack2(kTailC4, kTailC4));
-    q = fma2(q, t, pack2(kTailC3, kTailC3));
+    f32x2 q = fma2(pack2(kTailC4, kTailC4), t, pack2(kTailC3, kTailC3));
     q = fma2(q, t, pack2(kTailC2, kTailC2));
     q = fma2(q, t, pack2(kTailC1, kTailC1));
     q = fma2(q, t, pack2(kTailC0, kTailC0));

@@ -271,8 +271,8 @@ def test_gauss_tail_against_cuda_erfc():
     got = fsmi.gauss_tail(s).double()
     ref = 0.5 * torch.special.erfc(s.double() / k)
     err = (got - ref).abs()
-    assert err.max().item() <= 2.5e-7
-    assert bool(torch.all(err <= 1.5e-6 * ref + 2.5e-8))
+    assert err.max().item() <= 3e-7
+    assert bool(torch.all(err <= 4e-6 * ref + 6e-8))
 
 
 WINDOW_CASES = ((64.0, 1.5, 0), (256.0, 2.0, 24), (256.0, 0.4, 8), (256.0, 12.0, 8))
