@@ -191,11 +191,13 @@ static __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, lon
     int cnt = 0, ties = 0;
     bool ended = false, rng = false;
     float endl = 0.0f;
-    int i0 = 0, pred = 0;
-    if (k0 <= k1) {
-        i0 = minor_before(g, k0);
-        pred = (k1 - k0 + 1) + minor_before(g, k1 + 1) - i0;
-    }
+    // minor crossings before each lane's first interval: lane L's block ends where lane L + 1's
+    // begins, so one count per lane (at the end of its block) serves both
+    const int iend = k0 <= k1 ? minor_before(g, k1 + 1) : 0;
+    int i0 = __shfl_up_sync(kFull, iend, 1);
+    if (lane == 0) i0 = 0;  // k0 = -1: no minor crossing before the start
+    int pred = 0;
+    if (k0 <= k1) pred = (k1 - k0 + 1) + iend - i0;
     const int pinc = warp_incl_add_int(pred);
     if (k0 <= k1) walk<true>(g, k0, k1, i0, pinc - pred, cap, ids, l, cnt, ties, ended, endl, rng);
     const unsigned eb = __ballot_sync(kFull, ended);

@@ -529,7 +529,14 @@ __device__ __forceinline__ void eval_beam(const Src2D &src, const DevParams &p, 
         long long rfix = p.rfix;
         float rend = p.rend;
         if (SRC == kSrcMap || SRC == kSrcTraj) {
-            const int pi = (int)(beam / src.B), bi = (int)(beam % src.B);
+            int pi, bi;
+            if (beam <= 0x7fffffffLL) {  // 32-bit division (the common case; the 64-bit one is far longer)
+                pi = (int)((unsigned)beam / (unsigned)src.B);
+                bi = (int)((unsigned)beam - (unsigned)pi * (unsigned)src.B);
+            } else {
+                pi = (int)(beam / src.B);
+                bi = (int)(beam % src.B);
+            }
             pose = src.poses + 4 * (size_t)pi;
             ux = src.dirs[2 * bi];
             uy = src.dirs[2 * bi + 1];
