@@ -100,19 +100,15 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int b
     const unsigned long long dm = (unsigned long long)g.aM << 16, dM = (unsigned long long)g.am << 16;
     for (int k = k0; k <= k1; ++k, nMn += 65536u, pM += dM) {
         FSMI_EMIT(k < 0 ? 0.0f : (float)(nMn - 65536u) * g.rM);
-        if (g.am && pm < pM) {  // minor crossing inside
-            if (nmi >= g.Lm) {
-                ended = true;
-                endl = g.R;
-                by_range = true;
-                break;
-            }
+        const bool minor = g.am && pm < pM;  // a minor crossing inside the interval
+        if (minor && (nmi >= g.Lm || (unsigned)(cm + g.sm) >= (unsigned)g.dimm)) {  // the beam ends there
+            ended = true;
+            by_range = nmi >= g.Lm;
+            endl = by_range ? g.R : (float)nmi * g.rm;
+            break;
+        }
+        if (minor) {  // no branch inside: the lanes stay together whichever of them cross
             cm += g.sm;
-            if ((unsigned)cm >= (unsigned)g.dimm) {
-                ended = true;
-                endl = (float)nmi * g.rm;
-                break;
-            }
             FSMI_EMIT((float)nmi * g.rm);
             ++i;
             nmi += 65536u;
@@ -177,8 +173,8 @@ static __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, lon
     //   num * 2^30 < rfix * a  <=>  num < floor((rfix * a - 1) / 2^30) + 1
     g.LM = (unsigned)((((unsigned long long)rfix * g.aM - 1) >> 30) + 1);
     g.Lm = g.am ? (unsigned)((((unsigned long long)rfix * g.am - 1) >> 30) + 1) : 0u;
-    g.rM = 16384.0f / (float)g.aM;
-    g.rm = g.am ? 16384.0f / (float)g.am : 0.0f;
+    g.rM = __fdividef(16384.0f, (float)g.aM);  // distances need not be correctly rounded (< 2 ulp)
+    g.rm = g.am ? __fdividef(16384.0f, (float)g.am) : 0.0f;
     g.R = rend;
     // major crossings that stay in range and inside the grid along M
     const long long KR = g.LM > g.nM0 ? ((long long)g.LM - g.nM0 + 65535) >> 16 : 0;
@@ -202,17 +198,23 @@ static __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, lon
     if (k0 <= k1) walk<true>(g, k0, k1, i0, pinc - pred, cap, ids, l, cnt, ties, ended, endl, rng);
     const unsigned eb = __ballot_sync(kFull, ended);
     const int first = eb ? __ffs(eb) - 1 : 31;
-    const int c = lane <= first ? cnt : 0;
-    const int inc = warp_incl_add_int(c);
-    const int n = __shfl_sync(kFull, inc, 31);
     const float lend = __shfl_sync(kFull, endl, first);
     const unsigned rb = __ballot_sync(kFull, rng);
     if (end_by_range) *end_by_range = (rb >> first) & 1u;
-    if (n > cap) return -1;
-    // offsets of lanes after a diagonal step were too large: place the cells again
+    int n;
     if (__any_sync(kFull, lane < first && ties > 0)) {
+        // offsets of lanes after a diagonal step were too large: count exactly, place the cells again
+        const int c = lane <= first ? cnt : 0;
+        const int inc = warp_incl_add_int(c);
+        n = __shfl_sync(kFull, inc, 31);
+        if (n > cap) return -1;
         __syncwarp();
         if (lane <= first && k0 <= k1) walk<true>(g, k0, k1, i0, inc - c, cap, ids, l, cnt, ties, ended, endl, rng);
+    } else {
+        // every lane before the first that ended walked its whole block without a diagonal step,
+        // so its predicted count was exact: n = that lane's offset + its count
+        n = __shfl_sync(kFull, pinc - pred + cnt, first);
+        if (n > cap) return -1;
     }
     if (lane == 0) l[n] = lend;
     __syncwarp();

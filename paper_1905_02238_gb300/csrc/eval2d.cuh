@@ -176,7 +176,7 @@ __device__ __forceinline__ float exact_pairs_sum(const float4 *Q, const float *s
     const int mtop = ((n >> 1) + 1 + kPadPairs) * 2;  // pairs (m, m + 1) stay below this m
     // first trial: about cut x (boundaries per unit of scaled distance) boundaries on each side
     const float span = lq(n) - lq(0);
-    const float per = span > 0.0f ? (float)n / span : 0.0f;
+    const float per = span > 0.0f ? __fdividef((float)n, span) : 0.0f;
     int GN = (int)fminf(cut * per, (float)(n + 1)) >> 1, GP = GN;
     float r = 0.0f;
     int jb = 0;
@@ -292,67 +292,78 @@ __device__ __forceinline__ float exact_pairs_sum(const float4 *Q, const float *s
     return r;
 }
 
-// Boundary terms m in [a, b) on one side of a first-hit cell's centre, added to acc: before the
-// centre (NEG) -dC_m T(mu - l_m), after it +dC_m T(l_m - mu). Pairs at even m go through the
-// packed tail; an odd first or last boundary is evaluated alone.
-template <bool NEG>
-__device__ __forceinline__ float side_terms(const float *sl, const float *sdc, int a, int b, float mu, float acc)
+// ---- the Approx-FSMI pair sum over mirrored boundary pairs -------------------------------------
+//
+// Interleaved boundaries for Approx-FSMI: LW[m] = (l_m, dC_m) (scaled distance, C_m - C_{m-1})
+// for m in [-kPad2D, n + kPad2D], padding (l = -+3e30, dC = 0) beyond the beam. Built in place over
+// sl and the scratch array after it from the top down, as build_pairs does (writing LW[m]
+// overwrites l_{2m}, l_{2m+1}, which only LW[2m], LW[2m+1] read).
+__device__ __forceinline__ void build_lw(float *sl, const float *sc, int n, float cs)
 {
-    int m = a;
-    if (m < b && (m & 1)) {
-        acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(NEG ? mu - sl[m] : sl[m] - mu), acc);
-        ++m;
+    const int lane = lane_id();
+    float2 *LW = reinterpret_cast<float2 *>(sl);
+    const int mend = n + 1 + kPad2D;  // boundaries 0 .. mend - 1 (those above n padding)
+    for (int top = mend; top > 0; top -= 32) {
+        const int m = top - 32 + lane;
+        float2 v = make_float2(3.0e30f, 0.0f);
+        if (m >= 0 && m <= n) v = make_float2(sl[m] * cs, sc[m] - (m > 0 ? sc[m - 1] : 0.0f));  // sc[n] = 0
+        __syncwarp();
+        if (m >= 0) LW[m] = v;
+        __syncwarp();
     }
-    const f32x2 mu2 = pack2(mu, mu);
-    f32x2 acc2 = pack2(0.0f, 0.0f);
-#pragma unroll 2
-    for (; m + 1 < b; m += 2) {
-        const f32x2 L = *reinterpret_cast<const f32x2 *>(sl + m);
-        const f32x2 dc = *reinterpret_cast<const f32x2 *>(sdc + m);
-        acc2 = fma2(dc, gauss_tail2p<NEG>(NEG ? sub2(mu2, L) : sub2(L, mu2)), acc2);
-    }
-    float a0, a1;
-    unpack2(acc2, a0, a1);
-    acc += a0 + a1;
-    if (m < b) acc = fmaf(NEG ? -sdc[m] : sdc[m], gauss_tail(NEG ? mu - sl[m] : sl[m] - mu), acc);
-    return acc;
+    LW[-1 - lane] = make_float2(-3.0e30f, 0.0f);  // kPad2D = 32 padding boundaries below 0
+    __syncwarp();
 }
 
-// Approx-FSMI: for slot j the band k in [klo, khi] = [j - Delta, j + Delta] n [0, n-1] (0-based),
-// i.e. boundaries m in [klo, khi + 1] with C' = C on the band and 0 outside it: the band edges
-// weigh C_klo and -C_khi, the interior C_m - C_{m-1} (sdc).
-__device__ __forceinline__ float approx_sum(const float *sl, const float *sc, const float *sdc, const float *sp,
-                                            int n, bool e0, float pe0, float mu0, int D)
+// Approx-FSMI (eq. fsmi_approx): for first-hit slot j the band k in [klo, khi] = [j - Delta,
+// j + Delta] n [0, n - 1], i.e. boundaries m in [klo, khi + 1] with C' = C on the band and 0 outside
+// it. In boundary form the interior boundaries weigh dC_m, the band edges C_klo (at m = klo) and
+// -C_khi (at m = khi + 1). The boundaries below the centre, j - i, and above it, j + 1 + i, are
+// taken as mirrored pairs (j - i, j + 1 + i), i = 0 .. Delta, so that every pair has the signs
+// (-, +), which the tail's coefficients carry, and every lane runs exactly Delta + 1 pairs: an edge
+// clamped at the beam's end lands on a padding boundary (its term is 0, and dC_0 = C_0, dC_n =
+// -C_{n-1} are already the clamped edges' weights), and an unclamped edge is the last pair, whose
+// weights are C_{j-Delta} and -C_{j+Delta}. The no-return slot (e0) is j = -1 with centre mu0: the
+// paper's band k in [1, Delta], every boundary above it. Delta beyond n changes nothing (every band
+// is the whole beam), so it is capped at n; past the padding (Delta > kPad2D - 1) the indices are
+// clamped to it.
+template <bool CLAMP>
+__device__ __forceinline__ float approx_pairs_sum(const float2 *LW, const float *sc, const float *sp, int n, bool e0,
+                                                  float pe0, float mu0, int D)
 {
-    const int nslots = n + (e0 ? 1 : 0);
+    const int lane = lane_id();
     float r = 0.0f;
-    for (int j = lane_id(); j < nslots; j += 32) {
+    for (int jb = e0 ? -1 : 0; jb < n; jb += 32) {
+        const int j = jb + lane;
+        const bool act = j < n;
+        const int jj = act ? j : n - 1;  // an idle lane shadows the last slot with zero weight
         float mu, Cj, Pj;
-        int klo, khi;
-        if (j < n) {
-            mu = 0.5f * (sl[j] + sl[j + 1]);
-            Cj = sc[j];
-            Pj = sp[j];
-            klo = max(0, j - D);
-            khi = min(n - 1, j + D);
-        } else {  // e_0 at virtual index 0: paper band k in [1, Delta]
+        if (jj >= 0) {
+            mu = 0.5f * (LW[jj].x + LW[jj + 1].x);
+            Cj = sc[jj];
+            Pj = act ? sp[jj] : 0.0f;
+        } else {
             mu = mu0;
             Cj = 0.0f;
             Pj = pe0;
-            klo = 0;
-            khi = min(n - 1, D - 1);
         }
-        const int mid = (j < n) ? j + 1 : 0;  // boundaries m < mid lie before the centre
-        float acc = 0.0f;
-        if (klo <= khi) {  // an empty band (e_0 with Delta = 0) adds nothing
-            const float clo = sc[klo], chi = sc[khi];
-            acc = fmaf(klo < mid ? -clo : clo, gauss_tail(sl[klo] - mu), acc);
-            const int split = min(max(mid, klo + 1), khi + 1);
-            acc = side_terms<true>(sl, sdc, klo + 1, split, mu, acc);
-            acc = side_terms<false>(sl, sdc, split, khi + 1, mu, acc);
-            acc = fmaf(khi + 1 < mid ? chi : -chi, gauss_tail(sl[khi + 1] - mu), acc);
+        f32x2 acc = pack2(0.0f, 0.0f);
+        int i = 0;
+#pragma unroll 2
+        for (; i < D; ++i) {
+            const int mb = jj - i, ma = jj + 1 + i;
+            const float2 b = LW[CLAMP ? max(mb, -kPad2D) : mb], a = LW[CLAMP ? min(ma, n + kPad2D) : ma];
+            acc = fma2(pack2(b.y, a.y), gauss_tail2p<true, false>(pack2(mu - b.x, a.x - mu)), acc);
         }
-        r = fmaf(Pj, Cj + acc, r);
+        {  // i = D: the band edges
+            const int mb = jj - D, ma = jj + 1 + D;
+            const float2 b = LW[CLAMP ? max(mb, -kPad2D) : mb], a = LW[CLAMP ? min(ma, n + kPad2D) : ma];
+            const float wb = mb >= 0 ? sc[mb] : 0.0f, wa = (ma >= 1 && ma <= n) ? -sc[ma - 1] : 0.0f;
+            acc = fma2(pack2(wb, wa), gauss_tail2p<true, false>(pack2(mu - b.x, a.x - mu)), acc);
+        }
+        float a0, a1;
+        unpack2(acc, a0, a1);
+        r = fmaf(Pj, Cj + (a0 + a1), r);
     }
     return r;
 }
@@ -493,11 +504,12 @@ __device__ __forceinline__ float beam_sum(const DevParams &p, int n, float *sl, 
             I = exact_pairs_sum(reinterpret_cast<const float4 *>(sl), sc, sp, n, e0, pe0, mu0, cut);
         }
         if (VAR == FSMI_APPROX) {
-            for (int i = lane; i <= n; i += 32) sl[i] *= cs;
-            for (int m = lane; m <= n; m += 32) sx[m] = sc[m] - (m > 0 ? sc[m - 1] : 0.0f);
-            __syncwarp();
-            const float mu0 = sl[0] - 0.5f * cs;
-            I = approx_sum(sl, sc, sx, sp, n, e0, pe0, mu0, p.trunc);
+            const float mu0 = sl[0] * cs - 0.5f * cs;  // e_0 centre, l_1 - 1/2 (scaled)
+            build_lw(sl, sc, n, cs);
+            const int D = min(p.trunc, n);
+            const float2 *LW = reinterpret_cast<const float2 *>(sl);
+            I = D < kPad2D ? approx_pairs_sum<false>(LW, sc, sp, n, e0, pe0, mu0, D)
+                           : approx_pairs_sum<true>(LW, sc, sp, n, e0, pe0, mu0, D);
         }
         if (VAR == FSMI_UNIFORM) I = uniform_sum(sx, sp, n, e0, pe0, p.H, p.inv_2h1);
         I = warp_sum(I);

@@ -95,22 +95,22 @@ __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
     return d;
 }
 
-// sgn T(d0), sgn T(d1) packed, for two non-negative scaled distances packed in d; NEG gives the
-// negated tails exactly (the polynomial with negated coefficients is the negated polynomial in
+// sgn T(d0), sgn T(d1) packed, for two non-negative scaled distances packed in d; NEG (NEG1 for
+// the second half, NEG by default) gives the negated tails exactly (the polynomial with negated coefficients is the negated polynomial in
 // round-to-nearest arithmetic).
-template <bool NEG>
+template <bool NEG, bool NEG1 = NEG>
 __device__ __forceinline__ f32x2 gauss_tail2p(f32x2 d)
 {
-    constexpr float sg = NEG ? -1.0f : 1.0f;
+    constexpr float s0 = NEG ? -1.0f : 1.0f, s1 = NEG1 ? -1.0f : 1.0f;  // signs of the two halves
     float dd0, dd1, den0, den1;
     unpack2(mul2(d, d), dd0, dd1);
     const float e0 = ex2_approx(-dd0), e1 = ex2_approx(-dd1);
     unpack2(fma2(pack2(kTailP, kTailP), d, pack2(1.0f, 1.0f)), den0, den1);
     const f32x2 t = pack2(rcp_approx(den0), rcp_approx(den1));
-    f32x2 q = fma2(pack2(sg * kTailC4, sg * kTailC4), t, pack2(sg * kTailC3, sg * kTailC3));
-    q = fma2(q, t, pack2(sg * kTailC2, sg * kTailC2));
-    q = fma2(q, t, pack2(sg * kTailC1, sg * kTailC1));
-    q = fma2(q, t, pack2(sg * kTailC0, sg * kTailC0));
+    f32x2 q = fma2(pack2(s0 * kTailC4, s1 * kTailC4), t, pack2(s0 * kTailC3, s1 * kTailC3));
+    q = fma2(q, t, pack2(s0 * kTailC2, s1 * kTailC2));
+    q = fma2(q, t, pack2(s0 * kTailC1, s1 * kTailC1));
+    q = fma2(q, t, pack2(s0 * kTailC0, s1 * kTailC0));
     return mul2(mul2(pack2(e0, e1), t), q);
 }
 
