@@ -549,6 +549,16 @@ fsmi_status fsmi_capture_end(fsmi_stream_t stream, fsmi_graph *graph);
 fsmi_status fsmi_graph_launch(fsmi_graph graph, fsmi_stream_t stream);
 fsmi_status fsmi_graph_destroy(fsmi_graph graph);
 
+/* Poll limit, for the calling host thread, of the one device-side wait a caller can shorten: the
+ * surrogate inference kernel's epilogue waiting for its tensor-core accumulator
+ * (fsmi_surrogate_predict). polls >= 0 sets it, < 0 restores the default (2^22 polls, far longer
+ * than the tensor cores take). A limit too short for the MMAs makes that wait give up: the call
+ * then sets FSMI_STATUS_TIMEOUT, writes NaN predictions, and still returns only after its copies
+ * and MMAs in flight have completed (those waits keep the full limit), so the device stays usable.
+ * It exists so that the timeout path can be tested without faulting or hanging the GPU; the paper
+ * has no counterpart. */
+fsmi_status fsmi_set_wait_limit(long long polls);
+
 /* Waits for `stream`, then returns in *status the current device's status word (FSMI_STATUS_*
  * bits, 0 if clean) and clears it. *status is host memory. */
 fsmi_status fsmi_device_status(fsmi_stream_t stream, int *status);

@@ -595,6 +595,12 @@ fsmi_status fsmi_workspace_size(int fn, long long nitems, const fsmi_params *prm
     return FSMI_OK;
 }
 
+fsmi_status fsmi_set_wait_limit(long long polls)
+{
+    set_epilogue_polls(polls);
+    return FSMI_OK;
+}
+
 fsmi_status fsmi_device_status(fsmi_stream_t stream, int *status)
 {
     if (!status) return FSMI_ERR_ARG;

@@ -96,6 +96,8 @@ cudaError_t launch_rle_encode_3d_static(const Vox3D &v, const DevParams &p, int3
 int sm_count();
 // records e as the calling thread's last CUDA error and returns FSMI_ERR_CUDA
 fsmi_status record_cuda_error(cudaError_t e);
+// poll limit of the surrogate fc kernel's epilogue wait for this host thread (< 0: the default)
+void set_epilogue_polls(long long polls);
 
 // exploration loop (fsmi_explore.cu): trajectory visit stamps and sums, the Bayesian map update
 cudaError_t launch_traj_stamps(int W, int H, const int32_t *poses, int P, const int32_t *traj_off, int T,

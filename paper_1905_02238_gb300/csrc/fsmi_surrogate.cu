@@ -652,6 +652,8 @@ constexpr size_t kTcSmem = 1024 + (size_t)kTcStages * kTcStageBytes + 8 * kTcBar
 constexpr unsigned kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kHid >> 3) << 17) |
                               ((unsigned)(kTcRows >> 4) << 24);
 constexpr long long kWaitPolls = 1LL << 22;
+// poll limit of the epilogue's wait for its accumulator, per host thread (fsmi_set_wait_limit)
+thread_local long long g_epi_polls = kWaitPolls;
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ unsigned long long sdesc_sw128(unsigned saddr)
@@ -680,10 +682,10 @@ __device__ __forceinline__ bool mbar_test(unsigned addr, unsigned parity)
     return ok != 0;
 }
 
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity)
+// bounded wait for the phase with the given parity to complete (at most `polls` tests)
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, long long polls = kWaitPolls)
 {
-    for (long long i = 0; i < kWaitPolls; ++i)
+    for (long long i = 0; i < polls; ++i)
         if (mbar_test(addr, parity)) return true;
     return false;
 }
@@ -745,7 +747,8 @@ __device__ __forceinline__ int flag_of(const int *flag) { return *(const volatil
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_fc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, long long N,
-            const bf16 *__restrict__ w, const float *__restrict__ params, float *__restrict__ pred, int *status)
+            const bf16 *__restrict__ w, const float *__restrict__ params, float *__restrict__ pred, int *status,
+            long long epi_polls)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -851,7 +854,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int b = tl & 1, v = tl >> 1;
             const long long row = t * kTcRows + warp * 32 + lane;
             float acc = 0.0f;
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(tfull + b), (unsigned)(v & 1)));
+            // the one wait whose limit the caller sets (fsmi_set_wait_limit): the producer's and the
+            // MMA issuer's waits keep the full limit, so that every copy and MMA in flight has landed
+            // before TMEM is freed, whatever happens here
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(tfull + b), (unsigned)(v & 1), epi_polls));
             if (ok) {
                 tc_fence_after();
                 const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)b * kTcAcc;
@@ -1119,9 +1125,11 @@ cudaError_t launch_surrogate_infer(const float *map, int W, int H, const int32_t
     e = cudaFuncSetAttribute(k_fc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
     k_fc_tc<<<(unsigned)(tiles < (long long)sm_count() ? tiles : sm_count()), kTcThreads, kTcSmem, s>>>(
-        tmA, tmB, N, w, params, pred, status);
+        tmA, tmB, N, w, params, pred, status, g_epi_polls);
     return cudaGetLastError();
 }
+
+void set_epilogue_polls(long long polls) { g_epi_polls = polls < 0 ? kWaitPolls : polls; }
 
 cudaError_t launch_topk(const float *v, int n, int k, int32_t *idx, cudaStream_t s)
 {

@@ -177,6 +177,7 @@ def load():
             "fsmi_rle_encode_3d_noalloc": [p, i, i, i, p, i, p, i, P, p, p, p, i, p],
             "fsmi_probe": [i, ll, p, sz, p],
             "fsmi_probe_threads": [i],
+            "fsmi_set_wait_limit": [ll],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -561,6 +562,12 @@ def probe(kind: int, iters: int, buf: torch.Tensor) -> None:
 def probe_threads(kind: int) -> int:
     """Threads of one fsmi_probe launch of `kind` on the current device."""
     return int(load().fsmi_probe_threads(kind))
+
+
+def set_wait_limit(polls: int) -> None:
+    """fsmi_set_wait_limit: poll limit of the surrogate inference epilogue's wait for its
+    accumulator on this host thread (polls < 0 restores the default)."""
+    _raise(load().fsmi_set_wait_limit(polls), "fsmi_set_wait_limit")
 
 
 def device_status() -> int:

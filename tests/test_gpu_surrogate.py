@@ -84,11 +84,25 @@ def test_loss_and_gradient_match_oracle():
     np.testing.assert_allclose(pred.cpu().numpy(), rpred, rtol=2e-5, atol=2e-5 * np.abs(rpred).max())
     assert abs(float(loss.item()) - rloss) <= 5e-5 * rloss
     g = grad.cpu().numpy().astype(np.float64)
+    # Element by element: each gradient entry is a sum of products (over beams, positions and the
+    # layers above); the FP32 sums can cancel, so the bound scales with the sum of the absolute
+    # values of those products, which the oracle's backward pass gives when it runs on |weights|,
+    # |dpred| and the (non-negative) activations with the same ReLU masks. The bound, 2e-4 of that
+    # sum, covers FP32 accumulation and the FP32 forward values it multiplies (dpred = 2 (pred - y)
+    # / N cancels where pred is close to y, so its relative error can reach well above one ulp).
+    acache = dict(cache)
+    acache["p"] = {k: np.abs(v) for k, v in cache["p"].items()}
+    for k in ("a0", "a1", "a2", "a3", "a4", "h0"):
+        acache[k] = np.abs(cache[k])
+    bound = S.backward(acache, np.abs(dpred))
+    err = np.abs(g - rgrad)
+    worst = {}
     for name, (o, shape) in S.offsets().items():
         n = int(np.prod(shape))
-        a, b = g[o:o + n], rgrad[o:o + n]
-        # FP32 accumulation over up to N * positions terms against FP64
-        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-9, name
+        e, bnd = err[o:o + n], bound[o:o + n]
+        worst[name] = float(np.max(e / (bnd + 1e-30)))
+        assert np.all(e <= 2e-4 * bnd + 1e-12), (name, worst[name])
+    print('gradient error / abs-sum bound, worst per layer:', worst)
     # the same step twice gives the same floats
     g2 = torch.zeros_like(grad)
     fsmi.surrogate_loss_grad(params, wb, x, _cuda(y), g2, loss)
@@ -155,6 +169,32 @@ def test_tensor_core_inference_matches_oracle():
     idx = np.random.default_rng(11).integers(0, x.shape[0], 152 * 128 * 3 + 77)
     big = fsmi.surrogate_predict(params, wb, x=x[torch.from_numpy(idx).cuda()]).cpu().numpy()
     np.testing.assert_array_equal(big, got.astype(np.float32)[idx])
+
+
+def test_inference_wait_that_runs_out_sets_timeout_and_nan():
+    # The epilogue's bounded wait for its tensor-core accumulator, limited to zero polls, gives up
+    # before any MMA can finish: the call must flag FSMI_STATUS_TIMEOUT, write NaN for every row,
+    # still return (its copies and MMAs in flight land under the full limit), and leave the device
+    # usable: the next call with the default limit is clean and equals the one before.
+    grid, poses, dirs = _case(seed=8, n_poses=7, nb=48)
+    x, _ = _profiles(grid, poses, dirs)
+    th = _theta(9)
+    params = _cuda(th)
+    wb = torch.empty(fsmi.SURR_NPARAMS, dtype=torch.bfloat16, device="cuda")
+    fsmi.surrogate_cast(params, wb)
+    assert fsmi.device_status() == 0
+    before = fsmi.surrogate_predict(params, wb, x=x)
+    try:
+        fsmi.set_wait_limit(0)
+        bad = fsmi.surrogate_predict(params, wb, x=x)
+        torch.cuda.synchronize()
+    finally:
+        fsmi.set_wait_limit(-1)
+    assert fsmi.device_status() & fsmi.STATUS_TIMEOUT
+    assert bool(torch.isnan(bad).all())
+    after = fsmi.surrogate_predict(params, wb, x=x)
+    assert fsmi.device_status() == 0
+    assert torch.equal(after, before)
 
 
 def test_topk_and_gather():
