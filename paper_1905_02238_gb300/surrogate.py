@@ -227,6 +227,14 @@ def recall_with_ties(found, exact_scores, top: int = 10, rel_tol: float = 1e-4) 
     return float(min(hits.sum(), top)) / top
 
 
+def tie_band(exact_scores, top: int = 10, rel_tol: float = 1e-4) -> int:
+    """How many candidates score within rel_tol (relative) of the top-th best exact score: `top`
+    when the exact top set is separated at that level, more when the cut falls among ties."""
+    sc = _np(exact_scores).astype(np.float64)
+    kth = np.sort(sc)[::-1][top - 1]
+    return int((sc >= kth - rel_tol * abs(kth)).sum())
+
+
 def regret(found, exact_scores) -> float:
     """1 - (best exact score among `found`) / (best exact score overall)."""
     sc = _np(exact_scores).astype(np.float64)
