@@ -735,10 +735,12 @@ def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512
                        run_cap=64)
     out = torch.empty(n, dtype=torch.float32, device=dev)
     times = torch.zeros(n + 1, dtype=torch.int64, device=dev)
-    ws = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=dev)
+    # with room for the range-class plan: one launch per range class, in one call
+    ws = torch.empty(fsmi.mixed_workspace_size(g.numel(), len(sets)), dtype=torch.uint8, device=dev)
+    ws1 = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device=dev)
 
-    def mixed():
-        fsmi.eval_mixed(st, n, out=out, times=times, ws=ws, grid=g, poses2=p2, dirs2=d2, prm2=prm2, volumes=vd,
+    def mixed(w=ws):
+        fsmi.eval_mixed(st, n, out=out, times=times, ws=w, grid=g, poses2=p2, dirs2=d2, prm2=prm2, volumes=vd,
                         poses3=p3, dirs3=d3, prm3=prm3)
 
     # the same sets, one launch each, in order
@@ -766,10 +768,14 @@ def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512
             if record:
                 ev[i + 1].record()
 
+    mixed(ws1)  # the single launch (no plan): every warp sized for the stream's longest beam or ray
+    torch.cuda.synchronize()
+    single_out = out.clone()
+    ms_single = _time_ms(lambda: mixed(ws1), reps=3)
     mixed()
     sequential()
     torch.cuda.synchronize()
-    ok = bool(torch.equal(out, seq_out))
+    ok = bool(torch.equal(out, seq_out)) and bool(torch.equal(single_out, seq_out))
     graph = fsmi.Graph(mixed)
     ms_mixed = _time_ms(graph.replay, reps=3)
     graph.replay()
@@ -795,7 +801,10 @@ def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512
         "items": n, "beams_2d": n2, "rays_3d": n - n2, "poses": poses,
         "one_launch": {"ms": ms_mixed, "poses_per_s": poses / (ms_mixed * 1e-3), "items_per_s": n / (ms_mixed * 1e-3),
                        "set_latency_ms_p50": float(np.percentile(lat, 50)),
-                       "set_latency_ms_p99": float(np.percentile(lat, 99))},
+                       "set_latency_ms_p99": float(np.percentile(lat, 99)),
+                       "how": "one fsmi_eval_mixed call with the range-class plan (a launch per class), "
+                              "captured in a CUDA graph"},
+        "one_launch_without_plan_ms": ms_single,
         "launch_per_set": {"ms": ms_seq, "poses_per_s": poses / (ms_seq * 1e-3),
                            "set_latency_ms_p50": float(np.percentile(lat_seq, 50)),
                            "set_latency_ms_p99": float(np.percentile(lat_seq, 99))},

@@ -207,7 +207,13 @@ fsmi_status fsmi_eval_2d_sets(const float *map, int W, int H, const int32_t *pos
  *     %globaltimer value (ns) when item i finished; a set's latency is the largest of its items'
  *     times minus times[0].
  *   ws: 16-byte aligned; fsmi_workspace_size(FSMI_FN_EVAL_2D, W*H) bytes (queue counter and 2D
- *     per-cell gains), or FSMI_QUEUE_BYTES without 2D sets.
+ *     per-cell gains), or FSMI_QUEUE_BYTES without 2D sets. With fsmi_mixed_workspace_size(W*H
+ *     (0 without 2D sets), nsets) bytes the call also plans by range class: a one-warp pre-pass
+ *     lists the sets, in stream order, by kind and range class (16 classes per kind, bounds from
+ *     16 to 1024 cells about a factor 1.25 apart), and each class runs as its own persistent launch whose warps' shared arrays are sized
+ *     for that class rather than for the stream's longest beam; the classes run one after the
+ *     other, in that order. Results are the same floats either way. If any descriptor fails the
+ *     plan's checks (those below, and outputs contiguous in set order) the single launch runs.
  * Descriptors are checked per item in the kernel: an item of a malformed set (indices past the
  * pose or direction arrays, a range outside its bound, a kind without parameters, a volume index
  * outside [0, nvol)) gets NaN and sets FSMI_STATUS_BAD_BEAM. The work schedule is the 2D family's.
@@ -238,6 +244,10 @@ fsmi_status fsmi_eval_mixed(const float *map, int W, int H, const int32_t *poses
                             const int32_t *dirs3, int R3, const fsmi_params *prm3, const fsmi_set *sets,
                             int nsets, long long nitems, float *out, unsigned long long *times, void *ws,
                             size_t ws_bytes, fsmi_stream_t stream);
+
+/* Workspace bytes of fsmi_eval_mixed with the range-class plan: the queue counter, 16 bytes of
+ * gains per map cell (map_cells = W*H, or 0 without 2D sets) and the plan for nsets sets. */
+fsmi_status fsmi_mixed_workspace_size(long long map_cells, int nsets, size_t *bytes);
 
 /*
  * fsmi_eval_beams - the same pair sums on explicit beams (Theorem 1's inputs: o_i, l_i).

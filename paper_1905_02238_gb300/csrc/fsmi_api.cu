@@ -454,13 +454,25 @@ fsmi_status fsmi_eval_mixed(const float *map, int W, int H, const int32_t *poses
     if (!sp) return cuda_fail(cudaGetLastError());
     cudaStream_t s = (cudaStream_t)stream;
     float4 *gains = prm2 ? gains_of(ws, ws_bytes, (long long)W * H, nitems, d2.nmax) : nullptr;
+    // the range-class plan, when the workspace holds it (fsmi_mixed_workspace_size)
+    const size_t plan_at = kQueueBytes + (prm2 ? (size_t)W * H * sizeof(float4) : 0);
+    unsigned char *plan = (ws && aligned16(ws) && ws_bytes >= plan_at + mixed_plan_bytes(nsets))
+                              ? (unsigned char *)ws + plan_at
+                              : nullptr;
     cudaError_t e = cudaSuccess;
     if (gains) e = map_gains(map, W, H, d2, gains, s);
     if (e == cudaSuccess)
         e = launch_eval_mixed(map, W, H, gains, poses2, P2, dirs2, B2, prm2 ? &d2 : nullptr, vols, nvol, poses3, P3,
                               dirs3, R3, prm3 ? &d3 : nullptr, sets, nsets, nitems, out, times, sp,
-                              queue_of(FSMI_KIND_2D, ws, ws_bytes), s);
+                              queue_of(FSMI_KIND_2D, ws, ws_bytes), plan, s);
     return e == cudaSuccess ? FSMI_OK : cuda_fail(e);
+}
+
+fsmi_status fsmi_mixed_workspace_size(long long map_cells, int nsets, size_t *bytes)
+{
+    if (!bytes || map_cells < 0 || nsets < 0) return FSMI_ERR_ARG;
+    *bytes = kQueueBytes + (size_t)map_cells * sizeof(float4) + mixed_plan_bytes(nsets);
+    return FSMI_OK;
 }
 
 fsmi_status fsmi_eval_beams(const int32_t *off, const float *o, const float *l, const float *lend, int nbeams,

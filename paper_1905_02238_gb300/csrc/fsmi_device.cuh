@@ -67,14 +67,17 @@ __device__ __forceinline__ int warp_incl_max_int(int v)
 // Bernoulli KL divergence between posterior o' = o delta / (1 + a), a = o (delta - 1), and prior
 // o, which equals the printed f(delta, r) and stays accurate as o -> 0 or 1:
 //   f = o' log1p((delta - 1)(1 - o) / (1 + a)) - (1 - o) / (1 + a) log1p(a).
+// Every operation is rounded explicitly (no contraction left to the compiler), so that the kernels
+// that inline it all compute the same floats.
 __device__ __forceinline__ float cell_gain(float delta, float o)
 {
-    const float dm1 = delta - 1.0f;
-    const float a = o * dm1;
-    const float ria = 1.0f / (1.0f + a);
-    const float omo = 1.0f - o;
-    const float post = o * delta * ria;
-    return post * log1pf(dm1 * omo * ria) - omo * ria * log1pf(a);
+    const float dm1 = __fsub_rn(delta, 1.0f);
+    const float a = __fmul_rn(o, dm1);
+    const float ria = __fdiv_rn(1.0f, __fadd_rn(1.0f, a));
+    const float omo = __fsub_rn(1.0f, o);
+    const float post = __fmul_rn(__fmul_rn(o, delta), ria);
+    const float l1 = log1pf(__fmul_rn(__fmul_rn(dm1, omo), ria));
+    return __fsub_rn(__fmul_rn(post, l1), __fmul_rn(__fmul_rn(omo, ria), log1pf(a)));
 }
 
 // Upper Gaussian tail in the erfc variable: 0.5 * erfc(z) = 1 - Phi(z sqrt(2)), z >= 0.

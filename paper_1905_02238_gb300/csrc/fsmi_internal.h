@@ -117,7 +117,9 @@ cudaError_t launch_eval_mixed(const float *map, int W, int H, const float4 *gain
                               const int32_t *dirs2, int B2, const DevParams *p2, const fsmi_volume *vols, int nvol,
                               const int32_t *poses3, int P3, const int32_t *dirs3, int R3, const DevParams *p3,
                               const fsmi_set *sets, int nsets, long long nitems, float *out, unsigned long long *times,
-                              int *status, unsigned long long *queue, cudaStream_t s);
+                              int *status, unsigned long long *queue, unsigned char *plan, cudaStream_t s);
+// bytes of the range-class plan of fsmi_eval_mixed for nsets sets (8-byte aligned start)
+size_t mixed_plan_bytes(int nsets);
 cudaError_t prepare_mixed();
 
 // learned surrogate (fsmi_surrogate.cu)

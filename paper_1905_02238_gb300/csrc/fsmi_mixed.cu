@@ -10,6 +10,20 @@ namespace fsmi {
 
 namespace {
 
+// range classes per kind, by their upper bound in cells (about a factor 1.25 apart)
+constexpr int kMixClasses = 16;
+constexpr int kMixBuckets = 2 * kMixClasses;  // 2D classes 0..15, 3D classes 16..31 (one per lane of the plan warp)
+__host__ __device__ constexpr int mix_bound(int c)
+{
+    return c == 0 ? 16 : c == 1 ? 24 : c == 2 ? 32 : c == 3 ? 48 : c == 4 ? 64 : c == 5 ? 80 : c == 6 ? 96
+         : c == 7 ? 128 : c == 8 ? 160 : c == 9 ? 192 : c == 10 ? 256 : c == 11 ? 320 : c == 12 ? 384
+         : c == 13 ? 512 : c == 14 ? 768 : 1024;
+}
+static_assert(kMixBuckets <= 32, "the plan warp keeps one class per lane");
+// which kinds a launch of k_eval_mixed takes: both (the single launch), or one class's kind, 3D with
+// the evaluation path its variant uses (as fsmi_eval_3d compiles one kernel per path)
+enum { kMixAny = 0, kMix2D = 1, kMix3DOther = 2, kMix3DThm5 = 3 };
+
 // the set holding item i (sets sorted by out_offset), or -1
 __device__ __forceinline__ int mixed_set_of(const fsmi_set *sets, int nsets, long long i)
 {
@@ -56,13 +70,142 @@ struct MixedSrc {
     int nsets;
 };
 
+// ---- range classes -----------------------------------------------------------------------------
+//
+// A single launch must size every warp's shared arrays for the longest beam or ray of the whole
+// stream. When the caller's workspace holds a plan, a one-warp pre-pass sorts the sets, in stream
+// order, into range classes (2D and 3D separately, ranges up to 16, 24, 32, 48, 64, 80, 96, 128,
+// 160, 192, 256, 320, 384, 512, 768, 1024 cells), and each class runs as its own persistent launch
+// of a kernel that holds only its kind's path, sized for its bound; classes follow one another in
+// the stream. A set whose descriptor fails the plan's checks (kind, offsets, range, contiguous
+// outputs) makes the plan invalid: the class launches then return at once and the single launch
+// runs instead, with its per-item checks.
+
+struct MixedPlan {
+    int valid, pad;
+    int nsb[kMixBuckets];          // sets per class
+    long long count[kMixBuckets];  // items per class
+    // then int list[kMixBuckets][nsets] (set indices in stream order) and
+    // long long pref[kMixBuckets][nsets + 1] (first item of each listed set within its class)
+};
+
+__host__ __device__ inline size_t plan_list_bytes(int nsets) { return ((size_t)kMixBuckets * nsets * 4 + 7) & ~(size_t)7; }
+
+__device__ __forceinline__ long long warp_incl_add_ll(long long v)
+{
+    const int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// class of a set (2D: 0..15, 3D: 16..31) or -1 if its descriptor is not one a class launch takes
+__device__ __forceinline__ int mixed_class(const fsmi_set &st, const MixedSrc &src, const DevParams &p2,
+                                           const DevParams &p3)
+{
+    if (st.npose < 0 || st.ndir < 1 || st.pose_offset < 0 || st.dir_offset < 0) return -1;
+    if (st.kind == FSMI_SET_2D) {
+        if (!src.has2d || !(st.max_range > 0.0f && st.max_range <= p2.rmax)) return -1;
+        if ((long long)st.pose_offset + st.npose > src.P2 || (long long)st.dir_offset + st.ndir > src.B2) return -1;
+        int c = 0;
+        while (c < kMixClasses - 1 && st.max_range > (float)mix_bound(c)) ++c;
+        return c;
+    }
+    if (st.kind == FSMI_SET_3D) {
+        if (!src.has3d || !(st.max_range >= 1.0f && st.max_range <= (float)p3.nmax)) return -1;
+        if (st.volume < 0 || st.volume >= src.nvol) return -1;
+        if ((long long)st.pose_offset + st.npose > src.P3 || (long long)st.dir_offset + st.ndir > src.R3) return -1;
+        int c = 0;  // by the range itself: a class launch takes ranges up to its bound (and its nmax)
+        while (c < kMixClasses - 1 && st.max_range > (float)mix_bound(c)) ++c;
+        return kMixClasses + c;
+    }
+    return -1;
+}
+
+// One warp: the sets' classes, per class the listed sets in stream order with their first items.
+__global__ void __launch_bounds__(32) k_mixed_plan(MixedSrc src, DevParams p2, DevParams p3, long long nitems,
+                                                   unsigned char *plan_raw)
+{
+    const int lane = lane_id(), nsets = src.nsets;
+    MixedPlan *pl = reinterpret_cast<MixedPlan *>(plan_raw);
+    int *list = reinterpret_cast<int *>(plan_raw + sizeof(MixedPlan));
+    long long *pref = reinterpret_cast<long long *>(plan_raw + sizeof(MixedPlan) + plan_list_bytes(nsets));
+    int nsb = 0;          // lane b: sets of class b so far
+    long long cnt = 0;    // lane b: items of class b so far
+    long long total = 0;  // items of every set so far
+    bool valid = true;
+    for (int base = 0; base < nsets; base += 32) {
+        const int si = base + lane;
+        fsmi_set st{};
+        int cls = -2;  // -2: no set on this lane
+        long long n = 0;
+        if (si < nsets) {
+            st = src.sets[si];
+            cls = mixed_class(st, src, p2, p3);
+            n = cls >= 0 ? (long long)st.npose * st.ndir : 0;
+        }
+        const long long incl = warp_incl_add_ll(n);
+        // outputs must be contiguous, in set order, inside [0, nitems)
+        const bool ok = cls == -2 || (cls >= 0 && st.out_offset == total + incl - n);
+        valid = valid && __all_sync(kFull, ok);
+        total += __shfl_sync(kFull, incl, 31);
+        for (int b = 0; b < kMixBuckets; ++b) {
+            const bool in = cls == b;
+            const unsigned mask = __ballot_sync(kFull, in);
+            if (!mask) continue;
+            const long long ib = warp_incl_add_ll(in ? n : 0);
+            const int nb = __shfl_sync(kFull, nsb, b);
+            const long long cb = __shfl_sync(kFull, cnt, b);
+            if (in) {
+                const int pos = nb + __popc(mask & ((1u << lane) - 1u));
+                list[(size_t)b * nsets + pos] = si;
+                pref[(size_t)b * (nsets + 1) + pos] = cb + ib - n;
+            }
+            const long long tb = __shfl_sync(kFull, ib, 31);
+            if (lane == b) {
+                nsb += __popc(mask);
+                cnt += tb;
+            }
+        }
+    }
+    valid = valid && total == nitems;
+    if (lane < kMixBuckets) {
+        pl->nsb[lane] = nsb;
+        pl->count[lane] = cnt;
+        pref[(size_t)lane * (nsets + 1) + nsb] = cnt;
+    }
+    if (lane == 0) pl->valid = valid ? 1 : 0;
+}
+
 // 64 registers (4 blocks of 8 warps): the 2D path needs no more, and residency bounds this kernel
-template <int VAR>
+template <int VAR, int KIND>
 __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     k_eval_mixed(MixedSrc src, DevParams p2, DevParams p3, long long nitems, int stride2, int stride3, float *out,
-                 unsigned long long *times, int *status, unsigned long long *queue, int chunk)
+                 unsigned long long *times, int *status, unsigned long long *queue, int chunk,
+                 const unsigned char *plan_raw, int bucket)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // with a plan: a class launch (bucket >= 0) takes its class's items and runs only if the plan is
+    // valid; the single launch (bucket < 0) runs only if it is not
+    long long nloc = nitems;
+    const int *blist = nullptr;
+    const long long *bpref = nullptr;
+    int nsb = 0;
+    if (plan_raw) {
+        const MixedPlan *pl = reinterpret_cast<const MixedPlan *>(plan_raw);
+        const bool valid = pl->valid != 0;
+        if (bucket < 0 ? valid : !valid) return;
+        if (bucket >= 0) {
+            nloc = pl->count[bucket];
+            nsb = pl->nsb[bucket];
+            blist = reinterpret_cast<const int *>(plan_raw + sizeof(MixedPlan)) + (size_t)bucket * src.nsets;
+            bpref = reinterpret_cast<const long long *>(plan_raw + sizeof(MixedPlan) + plan_list_bytes(src.nsets)) +
+                    (size_t)bucket * (src.nsets + 1);
+        }
+    }
     // block: the RLE kernel table of the 3D parameters; then each warp's arrays, used by either kind
     RleBlock rb;
     rb.ts = table_spec(p3);
@@ -75,8 +218,26 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     rb.base = base;
     if (times && threadIdx.x == 0) atomicMin(times, global_ns());
     const int lane = lane_id();
-    for_each_item(nitems, queue, chunk, [&](long long item) {
-        const int si = mixed_set_of(src.sets, src.nsets, item);
+    for_each_item(nloc, queue, chunk, [&](long long li) {
+        int si;
+        long long item = li;
+        if (blist) {  // the listed set holding class item li: the last with pref <= li
+            int lo = 0, len = nsb + 1;
+            while (len > 0) {
+                const int half = len >> 1;
+                if (bpref[lo + half] <= li) {
+                    lo += half + 1;
+                    len -= half + 1;
+                } else {
+                    len = half;
+                }
+            }
+            const int idx = min(lo - 1, nsb - 1);
+            si = idx >= 0 ? blist[idx] : -1;
+            if (si >= 0) item = src.sets[si].out_offset + (li - bpref[idx]);  // inside [0, nitems): planned
+        } else {
+            si = mixed_set_of(src.sets, src.nsets, item);
+        }
         fsmi_set st{};
         bool ok = si >= 0;
         if (ok) st = src.sets[si];
@@ -86,7 +247,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
         const long long pi = st.pose_offset + (ok ? k / st.ndir : 0), di = st.dir_offset + (ok ? k % st.ndir : 0);
         float I = __int_as_float(0x7fc00000);
         int bad = 0;
-        if (ok && st.kind == FSMI_SET_2D && src.has2d && pi < src.P2 && di < src.B2 && st.max_range > 0.0f &&
+        if (KIND != kMix3DOther && KIND != kMix3DThm5 && ok && st.kind == FSMI_SET_2D && src.has2d && pi < src.P2 && di < src.B2 && st.max_range > 0.0f &&
             st.max_range <= p2.rmax) {
             const long long rfix = __double2ll_rn((double)st.max_range * 65536.0);
             const float rend = (float)((double)rfix * (1.0 / 65536.0));
@@ -99,12 +260,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
                 I = beam_sum<VAR>(p2, n, sl, sc, sp, sx);
             else
                 bad = FSMI_STATUS_BEAM_OVERFLOW;
-        } else if (ok && st.kind == FSMI_SET_3D && src.has3d && pi < src.P3 && di < src.R3 && st.volume >= 0 &&
+        } else if (KIND != kMix2D && ok && st.kind == FSMI_SET_3D && src.has3d && pi < src.P3 && di < src.R3 && st.volume >= 0 &&
                    st.volume < src.nvol && st.max_range >= 1.0f && st.max_range <= (float)p3.nmax) {
             const fsmi_volume v = src.vols[st.volume];
             int nr = 0;
-            I = ray_mi_fused<kRay3dAny>(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range, p3,
-                             rb.tab, rb.gtab, rb.ts.K, base, &nr);
+            constexpr int kMode = KIND == kMix3DOther ? kRay3dOther : KIND == kMix3DThm5 ? kRay3dThm5 : kRay3dAny;
+            I = ray_mi_fused<kMode>(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range,
+                                    p3, rb.tab, rb.gtab, rb.ts.K, base, &nr);
         } else {
             bad = FSMI_STATUS_BAD_BEAM;  // a malformed descriptor is never used to index
         }
@@ -117,19 +279,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     });
 }
 
-template <int VAR>
+template <int VAR, int KIND = kMixAny>
 cudaError_t launch_mixed_variant(const MixedSrc &src, const DevParams &p2, const DevParams &p3, long long nitems,
                                  float *out, unsigned long long *times, int *status, unsigned long long *queue,
-                                 cudaStream_t s)
+                                 cudaStream_t s, const unsigned char *plan = nullptr, int bucket = -1)
 {
-    const Schedule &sc = current_schedule(FSMI_KIND_2D);
+    // a 3D class runs under the RLE family's schedule, like fsmi_eval_3d; everything else the 2D one
+    const Schedule &sc = current_schedule(KIND == kMix3DOther || KIND == kMix3DThm5 ? FSMI_KIND_RLE : FSMI_KIND_2D);
     const int stride2 = stride_2d(p2.nmax);
     const int stride3 = ((p3.nmax + 2 * p3.K + 4) + 3) & ~3;
     const size_t per_warp = (size_t)max(warp_floats_2d(stride2), ray3d_warp_floats(p3)) * sizeof(float);
     const size_t table = rle_table_bytes(table_spec(p3).K);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, table);
     const size_t smem = table + (size_t)wpb * per_warp;
-    auto kern = k_eval_mixed<VAR>;
+    auto kern = k_eval_mixed<VAR, KIND>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -143,13 +306,60 @@ cudaError_t launch_mixed_variant(const MixedSrc &src, const DevParams &p2, const
         e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    if (times) {
-        e = cudaMemsetAsync(times, 0xFF, sizeof(unsigned long long), s);  // start = min over blocks
+    if (times && !plan) {  // start = min over blocks (with a plan, the caller resets it once)
+        e = cudaMemsetAsync(times, 0xFF, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
     kern<<<(unsigned)grid, wpb * 32, smem, s>>>(src, p2, p3, nitems, stride2, stride3, out, times, status, queue,
-                                                sc.queue_chunk > 0 ? sc.queue_chunk : 1);
+                                                sc.queue_chunk > 0 ? sc.queue_chunk : 1, plan, bucket);
     return cudaGetLastError();
+}
+
+// The call with a plan: the pre-pass, one launch per range class that can hold sets (each sized
+// for its class's bound), then the single launch, which returns at once unless the plan failed.
+template <int VAR>
+cudaError_t launch_mixed_planned(const MixedSrc &src, const DevParams &d2, const DevParams &d3, long long nitems,
+                                 float *out, unsigned long long *times, int *status, unsigned long long *queue,
+                                 unsigned char *plan, cudaStream_t s)
+{
+    k_mixed_plan<<<1, 32, 0, s>>>(src, d2, d3, nitems, plan);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (times) {
+        e = cudaMemsetAsync(times, 0xFF, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
+    DevParams n2{}, n3{};  // inert parameters for the kind a class launch does not run
+    n2.variant = FSMI_EXACT;
+    n2.nmax = 1;
+    n3.variant = FSMI_UNIFORM;
+    n3.nmax = 1;
+    n3.K = 0;
+    n3.cell_runlen = 1;
+    for (int c = 0; c < kMixClasses; ++c) {
+        const float lo = c == 0 ? 0.0f : (float)mix_bound(c - 1);
+        if (src.has2d && lo < d2.rmax) {
+            DevParams p = d2;
+            const double rb = fmin((double)mix_bound(c), (double)d2.rmax);
+            p.nmax = (int)(rb * 1.41421357) + 3;  // as make_params: every beam of the class fits
+            MixedSrc sc2 = src;
+            sc2.has3d = false;
+            e = launch_mixed_variant<VAR, kMix2D>(sc2, p, n3, nitems, out, times, status, queue, s, plan, c);
+            if (e != cudaSuccess) return e;
+        }
+        if (src.has3d && lo < (float)d3.nmax) {
+            DevParams p = d3;
+            p.nmax = min(mix_bound(c), d3.nmax);
+            MixedSrc sc3 = src;
+            sc3.has2d = false;
+            e = thm5_of(p) ? launch_mixed_variant<VAR, kMix3DThm5>(sc3, n2, p, nitems, out, times, status, queue, s,
+                                                                  plan, kMixClasses + c)
+                           : launch_mixed_variant<VAR, kMix3DOther>(sc3, n2, p, nitems, out, times, status, queue, s,
+                                                                   plan, kMixClasses + c);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return launch_mixed_variant<VAR>(src, d2, d3, nitems, out, times, status, queue, s, plan, -1);
 }
 
 }  // namespace
@@ -158,7 +368,7 @@ cudaError_t launch_eval_mixed(const float *map, int W, int H, const float4 *gain
                               const int32_t *dirs2, int B2, const DevParams *p2, const fsmi_volume *vols, int nvol,
                               const int32_t *poses3, int P3, const int32_t *dirs3, int R3, const DevParams *p3,
                               const fsmi_set *sets, int nsets, long long nitems, float *out, unsigned long long *times,
-                              int *status, unsigned long long *queue, cudaStream_t s)
+                              int *status, unsigned long long *queue, unsigned char *plan, cudaStream_t s)
 {
     if (nitems <= 0) return cudaSuccess;
     // a kind without parameters gets inert ones sized for nothing
@@ -173,6 +383,17 @@ cudaError_t launch_eval_mixed(const float *map, int W, int H, const float4 *gain
     if (p3) d3 = *p3;
     MixedSrc src{map, W, H, gains, poses2, P2, dirs2, B2, p2 != nullptr, vols, nvol, poses3, P3, dirs3, R3,
                  p3 != nullptr, sets, nsets};
+    if (plan) {
+        switch (d2.variant) {
+            case FSMI_EXACT:
+                if (d2.flags & FSMI_FLAG_FULL_SWEEP)
+                    return launch_mixed_planned<kExactFullSweep>(src, d2, d3, nitems, out, times, status, queue, plan, s);
+                return launch_mixed_planned<FSMI_EXACT>(src, d2, d3, nitems, out, times, status, queue, plan, s);
+            case FSMI_APPROX:
+                return launch_mixed_planned<FSMI_APPROX>(src, d2, d3, nitems, out, times, status, queue, plan, s);
+            default: return launch_mixed_planned<FSMI_UNIFORM>(src, d2, d3, nitems, out, times, status, queue, plan, s);
+        }
+    }
     switch (d2.variant) {
         case FSMI_EXACT:
             if (d2.flags & FSMI_FLAG_FULL_SWEEP)
@@ -183,13 +404,30 @@ cudaError_t launch_eval_mixed(const float *map, int W, int H, const float4 *gain
     }
 }
 
+template <int VAR>
+static cudaError_t prepare_mixed_var()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_mixed<VAR, kMixAny>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_mixed<VAR, kMix2D>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_mixed<VAR, kMix3DOther>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_mixed<VAR, kMix3DThm5>);
+    return e;
+}
+
+size_t mixed_plan_bytes(int nsets)
+{
+    return sizeof(MixedPlan) + plan_list_bytes(nsets) + (size_t)kMixBuckets * (nsets + 1) * sizeof(long long);
+}
+
 cudaError_t prepare_mixed()
 {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_mixed<FSMI_EXACT>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_mixed<kExactFullSweep>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_mixed<FSMI_APPROX>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_mixed<FSMI_UNIFORM>);
+    cudaError_t e = cudaFuncGetAttributes(&a, k_mixed_plan);
+    if (e == cudaSuccess) e = prepare_mixed_var<FSMI_EXACT>();
+    if (e == cudaSuccess) e = prepare_mixed_var<kExactFullSweep>();
+    if (e == cudaSuccess) e = prepare_mixed_var<FSMI_APPROX>();
+    if (e == cudaSuccess) e = prepare_mixed_var<FSMI_UNIFORM>();
     return e;
 }
 

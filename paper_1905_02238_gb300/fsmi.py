@@ -178,6 +178,7 @@ def load():
             "fsmi_probe": [i, ll, p, sz, p],
             "fsmi_probe_threads": [i],
             "fsmi_set_wait_limit": [ll],
+            "fsmi_mixed_workspace_size": [ll, i, ctypes.POINTER(ctypes.c_size_t)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -825,10 +826,17 @@ def make_volumes(volumes, device=None):
     return t.to(device) if device is not None else t
 
 
+def mixed_workspace_size(map_cells: int, nsets: int) -> int:
+    """fsmi_mixed_workspace_size: bytes of fsmi_eval_mixed's workspace with the range-class plan."""
+    b = ctypes.c_size_t(0)
+    _raise(load().fsmi_mixed_workspace_size(map_cells, nsets, ctypes.byref(b)), "fsmi_mixed_workspace_size")
+    return int(b.value)
+
+
 def eval_mixed(sets, nitems: int, out=None, times=None, ws=None, grid=None, poses2=None, dirs2=None,
                prm2: Params | None = None, volumes=None, poses3=None, dirs3=None, prm3: Params | None = None):
-    """fsmi_eval_mixed: 2D and 3D candidate sets (make_sets) in one persistent launch -> float32
-    [nitems]. volumes: int32 [nvol, 6] from make_volumes (the tensors must stay alive). times
+    """fsmi_eval_mixed: 2D and 3D candidate sets (make_sets) in one call -> float32 [nitems]
+    (without `ws`, a workspace with the range-class plan is allocated). volumes: int32 [nvol, 6] from make_volumes (the tensors must stay alive). times
     (optional) uint64-as-int64 [nitems + 1] receives the block start and per-item completion times."""
     lib = load()
     st = _dev_tensor(sets, torch.int32, "sets")
@@ -842,7 +850,7 @@ def eval_mixed(sets, nitems: int, out=None, times=None, ws=None, grid=None, pose
     if ws is None:
         if _capturing():
             raise FsmiError("inside a graph capture pass a preallocated workspace")
-        nb = workspace_size(FN_EVAL_2D, grid.numel()) if grid is not None else QUEUE_BYTES
+        nb = mixed_workspace_size(grid.numel() if prm2 is not None and grid is not None else 0, st.shape[0])
         ws = torch.empty(nb, dtype=torch.uint8, device=dev)
     wp, wb = _ws_args(ws)
     c2 = prm2.c() if prm2 is not None else None

@@ -88,6 +88,52 @@ def test_mixed_sets_equal_separate_calls(variant2):
     # completion times: after the start, one per item
     t = times.cpu().numpy().view(np.uint64)
     assert np.all(t[1:] >= t[0]) and t[0] > 0
+    # the same call without room for the range-class plan: one launch, the same floats
+    ws1 = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device="cuda")
+    assert ws1.numel() < fsmi.mixed_workspace_size(g.numel(), st.shape[0])
+    one = fsmi.eval_mixed(st, n, ws=ws1, grid=g, poses2=p2, dirs2=d2, prm2=fsmi.Params(**b2), volumes=vd, poses3=p3,
+                          dirs3=d3, prm3=fsmi.Params(**b3)).cpu().numpy()
+    np.testing.assert_array_equal(_bits(one), _bits(out))
+
+
+def test_mixed_plan_over_every_range_class():
+    # sets in every 2D and 3D range class (up to 64 ... 1024 cells), interleaved in the stream: the
+    # planned call (one launch per class) equals the single launch bit for bit, and the separate calls
+    grid = synth.office_grid(512, n_obst=60, seed=44)
+    poses2 = synth.free_cell_poses_2d(grid, 24, seed=45)
+    dirs2 = synth.beam_dirs_2d(90)
+    vol = synth.voxel_world(96, 80, 48, n_boxes=16, seed=9, noise_seed=10, noise_frac=0.05)
+    poses3 = synth.free_voxel_poses(vol, 6, seed=11, zlo=6, zhi=40)
+    dirs3 = synth.pinhole_dirs(12, 10, 100.0)
+    g, p2, d2, p3, d3 = (_cuda(x) for x in (grid, poses2, dirs2, poses3, dirs3))
+    vt = [_cuda(vol)]
+    vd = fsmi.make_volumes(vt, "cuda")
+    b2 = dict(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=1000.0)
+    b3 = dict(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=1000.0, run_cap=64)
+    sets = [(fsmi.SET_2D, 0, 2, 0, 90, 700.0), (fsmi.SET_3D, 0, 2, 0, 120, 20.0, 0), (fsmi.SET_2D, 2, 3, 0, 90, 40.0),
+            (fsmi.SET_3D, 2, 1, 0, 120, 300.0, 0), (fsmi.SET_2D, 5, 2, 0, 90, 100.0), (fsmi.SET_3D, 3, 1, 0, 120, 900.0, 0),
+            (fsmi.SET_2D, 7, 2, 0, 90, 250.0), (fsmi.SET_3D, 4, 1, 0, 120, 100.0, 0), (fsmi.SET_2D, 9, 2, 0, 90, 400.0),
+            (fsmi.SET_3D, 5, 1, 0, 120, 200.0, 0), (fsmi.SET_2D, 11, 2, 0, 90, 64.0), (fsmi.SET_3D, 0, 1, 0, 120, 64.0, 0)]
+    st, n = fsmi.make_sets(sets, "cuda")
+    kw = dict(grid=g, poses2=p2, dirs2=d2, prm2=fsmi.Params(**b2), volumes=vd, poses3=p3, dirs3=d3,
+              prm3=fsmi.Params(**b3))
+    fsmi.device_status()
+    planned = fsmi.eval_mixed(st, n, **kw).cpu().numpy()
+    ws1 = torch.empty(fsmi.workspace_size(fsmi.FN_EVAL_2D, g.numel()), dtype=torch.uint8, device="cuda")
+    single = fsmi.eval_mixed(st, n, ws=ws1, **kw).cpu().numpy()
+    assert fsmi.device_status() == 0
+    np.testing.assert_array_equal(_bits(planned), _bits(single))
+    at = 0
+    for s in sets:
+        kind, po, npose, do, ndir, rng = s[:6]
+        if kind == fsmi.SET_2D:
+            sep = fsmi.eval_2d(g, p2[po:po + npose], d2[do:do + ndir], fsmi.Params(**dict(b2, max_range=rng)))
+        else:
+            sep = fsmi.eval_3d(vt[0], p3[po:po + npose], d3[do:do + ndir], fsmi.Params(**dict(b3, max_range=rng)))
+        sep = sep.cpu().numpy().reshape(-1)
+        np.testing.assert_array_equal(_bits(planned[at:at + sep.size]), _bits(sep), err_msg=str(s))
+        at += sep.size
+    assert at == n
 
 
 def test_mixed_malformed_sets_and_single_kind():
