@@ -26,6 +26,13 @@
 
 namespace fsmi {
 
+// Per-cell gain f(delta_occ, r) (which = 0) or f(delta_emp, r) (which = 1) of the RLE kernels: the
+// host-fitted Chebyshev series when it is accurate for these deltas, else the closed form.
+__device__ __forceinline__ float rle_gain(const DevParams &p, int which, float o)
+{
+    return p.gain_fit ? gain_series(p.gfit[which], o) : cell_gain(which ? p.demp : p.docc, o);
+}
+
 // ---- noise-kernel prefix tables --------------------------------------------------------------
 
 // tab[i] = (Psi(m), Psi1(m)) for m = i - K - 1, i in [0, 2K + 1]; Psi(-K-1) = 0, Psi(K) = total.
@@ -136,7 +143,7 @@ static __device__ void run_starts(const RunSmem &r, int nr, bool have_s)
 
 // Run prefixes (Algorithms for P_E(u) and D_E(v)): P_E(u) = prod_{i<u} (1 - o_i)^{L_i},
 // D_E(u) = sum_{i<u} L_i f(delta_emp, r_i). On entry O, L and S are set.
-static __device__ void run_prefixes(const RunSmem &r, int nr, float docc, float demp)
+static __device__ void run_prefixes(const RunSmem &r, int nr, const DevParams &p)
 {
     const int lane = lane_id();
     const int K = (nr + 31) >> 5;
@@ -146,7 +153,7 @@ static __device__ void run_prefixes(const RunSmem &r, int nr, float docc, float 
         const float o = r.O[u];
         const int L = r.L[u];
         prod *= ipowf(1.0f - o, L);
-        sum = fmaf((float)L, cell_gain(demp, o), sum);
+        sum = fmaf((float)L, rle_gain(p, 1, o), sum);
     }
     const float ip = warp_incl_mul(prod);
     const float is = warp_incl_add(sum);
@@ -160,10 +167,10 @@ static __device__ void run_prefixes(const RunSmem &r, int nr, float docc, float 
         const float o = r.O[u];
         const int L = r.L[u];
         const float x = 1.0f - o;
-        const float fe = cell_gain(demp, o);
+        const float fe = rle_gain(p, 1, o);
         r.X[u] = x;
         r.F[u] = fe;
-        r.A[u] = D + cell_gain(docc, o);
+        r.A[u] = D + rle_gain(p, 0, o);
         r.O[u] = E * o;
         E *= ipowf(x, L);
         D = fmaf((float)L, fe, D);
@@ -302,8 +309,8 @@ static __device__ float ray_mi_cells(float *base, int stride, int nr, int n, con
     float *CF = base + 5 * stride, *CC = base + 6 * stride;
     for (int u = lane; u < nr; u += 32) {
         const float o = O[u];
-        RFO[u] = cell_gain(p.docc, o);
-        RFE[u] = cell_gain(p.demp, o);
+        RFO[u] = rle_gain(p, 0, o);
+        RFE[u] = rle_gain(p, 1, o);
     }
     for (int i = lane; i < K; i += 32) {
         CC[i] = 0.0f;
@@ -333,7 +340,7 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
     if (!thm5 && n < p.cell_runlen * nr) {
         v = ray_mi_cells(base, stride, nr, n, p, gtab, K);
     } else {
-        run_prefixes(r, nr, p.docc, p.demp);
+        run_prefixes(r, nr, p);
         if (p.variant == FSMI_APPROX && p.approx_reading == 0)
             v = pairs_thm5(r, nr, tab, K, p.trunc);
         else
@@ -355,7 +362,7 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
 // stored; *n_out receives n.
 static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, int Y, int Z, const int32_t *pose,
                                         const int32_t *u, int nsamp, int cap, float *O, int *S, int nrcap, int *n_out,
-                                        float *CP, float *CCk, float *CF, float docc, float demp)
+                                        float *CP, float *CCk, float *CF, const DevParams *gp)
 {
     const int lane = lane_id();
     float carried_fo = 0.0f, carried_fe = 0.0f;
@@ -410,8 +417,8 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         if (CP) {
             float fo = 0.0f, fe = 0.0f;
             if (newval) {
-                fo = cell_gain(docc, val);
-                fe = cell_gain(demp, val);
+                fo = rle_gain(*gp, 0, val);
+                fe = rle_gain(*gp, 1, val);
             }
             const int src = st - base;  // lane where this cell's run of equal values starts, if in this chunk
             const float so = __shfl_sync(kFull, fo, src >= 0 ? src : 0);
@@ -441,7 +448,7 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
                                         const int32_t *u, int nsamp, int cap, float *O, int *S)
 {
     return sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, cap, O, S, nsamp + 1, nullptr, nullptr, nullptr, nullptr,
-                             0.0f, 0.0f);
+                             nullptr);
 }
 
 // ---- the fused 3D ray (sampling and evaluation in one warp) --------------------------------------
@@ -482,7 +489,7 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
     const RunSmem r = run_smem(w + (thm5 ? 0 : 3 * cst), ray3d_run_stride(p));
     int n = 0;
     const int nr = sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, p.run_cap, r.O, r.S, ray3d_nrcap(p), &n, CP,
-                                     CC + K, CF, p.docc, p.demp);
+                                     CC + K, CF, &p);
     *nr_out = nr;
     if (nr <= 0) return 0.0f;
     float v;
@@ -497,7 +504,7 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
         v = band_conv<MODE == kRay3dOther>(CP, CC, gtab, K, n);
     } else {  // here n_r <= nrcap, so every run was stored
         run_starts(r, nr, true);
-        run_prefixes(r, nr, p.docc, p.demp);
+        run_prefixes(r, nr, p);
         v = thm5 ? pairs_thm5(r, nr, tab, K, p.trunc) : pairs_all(r, nr, tab, K);
     }
     return warp_sum(v);

@@ -1,6 +1,7 @@
 // C ABI of libfsmi (include/fsmi.h): argument checks on the host, derived constants, the
 // per-device status word, and dispatch to the kernel launchers.
 #include <math.h>
+#include <string.h>
 
 #include <mutex>
 #include <new>
@@ -64,6 +65,77 @@ int gauss_radius(float sigma) { return (int)ceilf(7.45f * sigma); }
 
 enum Use { kUse2D, kUseBeams, kUseRLE };
 
+// ---- the per-cell gain as a Chebyshev series (RLE kernels) --------------------------------------
+
+static double gain_exact(double d, double o)
+{
+    const double a = o * (d - 1.0), ria = 1.0 / (1.0 + a), omo = 1.0 - o, post = o * d * ria;
+    return post * log1p((d - 1.0) * omo * ria) - omo * ria * log1p(a);
+}
+
+// gain_series of fsmi_device.cuh, operation for operation in FP32 (explicit fmaf, nothing left to
+// contraction), so that the host sees exactly what the kernels compute
+static float gain_series_host(const float *c, float o)
+{
+    const float x2 = fmaf(4.0f, o, -2.0f);
+    float b1 = 0.0f, b2 = 0.0f;
+    for (int k = kGainFitTerms - 1; k >= 1; --k) {
+        const float t = c[k] - b2;
+        const float b0 = fmaf(x2, b1, t);
+        b2 = b1;
+        b1 = b0;
+    }
+    const float hx = 0.5f * x2;
+    const float t0 = c[0] - b2;
+    const float h = fmaf(hx, b1, t0);
+    const float om = 1.0f - o;
+    const float w = o * om;
+    return w * h;
+}
+
+// Fits h(o) = f(delta, o) / (o (1 - o)) for both deltas at Chebyshev nodes and keeps the series
+// only if, evaluated as the kernels do, it is within 1e-6 of f (relative) everywhere on a dense
+// grid of [0, 1] that includes points down to 1e-7 from either end; otherwise the kernels use the
+// closed form. The last fit is remembered per host thread.
+static void fit_gains(DevParams &d)
+{
+    thread_local float last_docc = -1.0f, last_demp = -1.0f, last_c[2][kGainFitTerms];
+    thread_local int last_ok = 0;
+    if (d.docc == last_docc && d.demp == last_demp) {
+        d.gain_fit = last_ok;
+        memcpy(d.gfit, last_c, sizeof(last_c));
+        return;
+    }
+    const int N = kGainFitTerms;
+    const double pi = 3.14159265358979323846;
+    bool ok = true;
+    for (int w = 0; w < 2; ++w) {
+        const double delta = w ? d.demp : d.docc;
+        double h[kGainFitTerms];
+        for (int j = 0; j < N; ++j) {
+            const double oj = 0.5 * (cos(pi * (j + 0.5) / N) + 1.0);
+            h[j] = gain_exact(delta, oj) / (oj * (1.0 - oj));
+        }
+        for (int k = 0; k < N; ++k) {
+            double c = 0.0;
+            for (int j = 0; j < N; ++j) c += h[j] * cos(pi * k * (j + 0.5) / N);
+            d.gfit[w][k] = (float)(c * (k == 0 ? 1.0 : 2.0) / N);
+        }
+        auto check = [&](float o) {
+            const double e = gain_exact(delta, (double)o);
+            const double g = (double)gain_series_host(d.gfit[w], o);
+            return e == 0.0 ? g == 0.0 : fabs(g - e) <= 1e-6 * fabs(e);
+        };
+        for (int i = 0; i <= 8192 && ok; ++i) ok = check((float)i / 8192.0f);
+        for (double t = 1e-7; t < 1e-2 && ok; t *= 1.25) ok = check((float)t) && check((float)(1.0 - t));
+    }
+    d.gain_fit = ok ? 1 : 0;
+    last_docc = d.docc;
+    last_demp = d.demp;
+    last_ok = d.gain_fit;
+    memcpy(last_c, d.gfit, sizeof(last_c));
+}
+
 fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
 {
     if (!prm) return FSMI_ERR_ARG;
@@ -95,6 +167,8 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     d.rfix = 0;
     d.rend = 0.0f;
     d.K = 0;
+    d.gain_fit = 0;
+    memset(d.gfit, 0, sizeof(d.gfit));
     if (use == kUse2D) {
         if (prm->max_range > FSMI_MAX_RANGE_2D) return FSMI_ERR_CAPACITY;
         d.rfix = llrint((double)prm->max_range * 65536.0);
@@ -117,6 +191,7 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
             if (prm->variant == FSMI_APPROX && prm->approx_reading == 1 && prm->trunc_delta < d.K) d.K = prm->trunc_delta;
         }
         if (d.K > FSMI_MAX_KERNEL_RADIUS) return FSMI_ERR_CAPACITY;
+        fit_gains(d);
     }
     return FSMI_OK;
 }

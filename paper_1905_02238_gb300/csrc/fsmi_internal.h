@@ -9,6 +9,8 @@
 namespace fsmi {
 
 // Host-validated parameters plus the derived constants every kernel needs.
+constexpr int kGainFitTerms = 14;  // terms of the Chebyshev series of the per-cell gain (degree 13)
+
 struct DevParams {
     int variant;        // FSMI_EXACT / FSMI_APPROX / FSMI_UNIFORM
     float sigma;        // cells
@@ -28,6 +30,10 @@ struct DevParams {
     int K;              // RLE kernel support radius (cells)
     int flags;          // FSMI_FLAG_* bits
     int cell_runlen;    // RLE: rays whose mean run length is below this take the cell-level form
+    // Chebyshev series of h(o) = f(delta, o) / (o (1 - o)) on [0, 1] for delta_occ ([0]) and
+    // delta_emp ([1]), used by the RLE kernels when gain_fit is set (see gain_series)
+    int gain_fit;
+    float gfit[2][kGainFitTerms];
 };
 
 constexpr int kMaxWarps = 8;  // most warps per block any evaluation kernel is launched with
