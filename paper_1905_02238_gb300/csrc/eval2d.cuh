@@ -108,13 +108,15 @@ __device__ __forceinline__ void build_pairs(float *sl, const float *sc, int n, f
         float4 v = make_float4(3.0e30f, 3.0e30f, 0.0f, 0.0f);
         if (P >= 0) {
             const int m = 2 * P;
-            if (m <= n) {
-                const float c0 = sc[m], cm = m > 0 ? sc[m - 1] : 0.0f;  // sc[n] = C_n = 0
-                v.x = sl[m] * cs;
-                v.z = c0 - cm;
+            if (m <= n) {  // l_m, l_{m+1} and C_m, C_{m+1} as 8-byte loads (m even); sc[n] = C_n = 0
+                const float2 l2 = *reinterpret_cast<const float2 *>(sl + m);
+                const float2 c2 = *reinterpret_cast<const float2 *>(sc + m);
+                const float cm = m > 0 ? sc[m - 1] : 0.0f;
+                v.x = l2.x * cs;
+                v.z = c2.x - cm;
                 if (m + 1 <= n) {
-                    v.y = sl[m + 1] * cs;
-                    v.w = sc[m + 1] - c0;
+                    v.y = l2.y * cs;
+                    v.w = c2.y - c2.x;
                 }
             }
         }
