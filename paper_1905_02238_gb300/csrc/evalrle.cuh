@@ -35,36 +35,15 @@ __device__ __forceinline__ float rle_gain(const DevParams &p, int which, float o
 
 // ---- noise-kernel prefix tables --------------------------------------------------------------
 
-// tab[i] = (Psi(m), Psi1(m)) for m = i - K - 1, i in [0, 2K + 1]; Psi(-K-1) = 0, Psi(K) = total.
-// kind: 0 Gaussian density (Theorem 3), 1 Gaussian cell mass, 2 box 1[|d| <= H] (Theorem 6).
-// band >= 0 zeroes |d| > band (strict-band reading of Approx-FSMI-RLE). The normalisation
-// (1/(sqrt(2 pi) sigma), 1 or 1/(2H+1)) is folded into g. Built in double, stored as float.
-static __device__ void build_table(float2 *tab, double *gs, float *gtab, int K, int kind, double sigma, int H, int band)
+// tab[i] = (Psi(m), Psi1(m)) for m = i - K - 1, i in [0, 2K + 1]; Psi(-K-1) = 0, Psi(K) = total;
+// gtab[K + d] = g(d). The host builds both once per launch (fill_rle_table: kind 0 Gaussian
+// density (Theorem 3), 1 Gaussian cell mass, 2 box 1[|d| <= H] (Theorem 6); band >= 0 zeroes
+// |d| > band, the strict-band reading of Approx-FSMI-RLE; normalisation folded into g; in double,
+// stored as float); each block copies them from the launch's parameters into shared memory.
+static __device__ void load_table(float2 *tab, float *gtab, int K, const RleTable &t)
 {
-    for (int a = threadIdx.x; a <= K; a += blockDim.x) {  // g(|d|), d = a
-        double g;
-        if (kind == 2)
-            g = (a <= H) ? 1.0 / (2.0 * H + 1.0) : 0.0;
-        else if (kind == 1)
-            g = 0.5 * (erfc(-(a + 0.5) / (sigma * 1.4142135623730951)) - erfc(-(a - 0.5) / (sigma * 1.4142135623730951)));
-        else
-            g = exp(-(double)a * a / (2.0 * sigma * sigma)) / (2.5066282746310002 * sigma);
-        if (band >= 0 && a > band) g = 0.0;
-        gs[a] = g;
-        gtab[K + a] = (float)g;  // gtab[K + d] = g(d), d in [-K, K]
-        gtab[K - a] = (float)g;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s0 = 0.0, s1 = 0.0;
-        tab[0] = make_float2(0.0f, 0.0f);
-        for (int d = -K; d <= K; ++d) {
-            const double g = gs[d < 0 ? -d : d];
-            s0 += g;
-            s1 += (double)d * g;
-            tab[d + K + 1] = make_float2((float)s0, (float)(d == K ? 0.0 : s1));
-        }
-    }
+    for (int i = threadIdx.x; i < 2 * K + 2; i += blockDim.x) tab[i] = t.tab[i];
+    for (int i = threadIdx.x; i < 2 * K + 1; i += blockDim.x) gtab[i] = t.gtab[i];
     __syncthreads();
 }
 
@@ -544,8 +523,7 @@ __host__ __device__ inline TabSpec table_spec(const DevParams &p)
 // shared memory: [table float2 (2K+2)] [g scratch double (K+1)] [g float (2K+1)] [per-warp arrays]
 __host__ __device__ inline size_t rle_table_bytes(int K)
 {
-    return (((size_t)(2 * K + 2) * sizeof(float2) + (size_t)(K + 1) * sizeof(double) +
-             (size_t)(2 * K + 1) * sizeof(float)) + 15) & ~(size_t)15;
+    return ((size_t)(2 * K + 2) * sizeof(float2) + (size_t)(2 * K + 1) * sizeof(float) + 15) & ~(size_t)15;
 }
 
 // Shared-memory layout of the RLE evaluation kernels: the block's kernel table, then each warp's
@@ -557,14 +535,14 @@ struct RleBlock {
     float *base;
 };
 
-__device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const DevParams &p, int warp_floats)
+__device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const DevParams &p, const RleTable &t,
+                                              int warp_floats)
 {
     RleBlock rb;
     rb.ts = table_spec(p);
     rb.tab = (float2 *)smem_raw;
-    double *gs = (double *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
-    rb.gtab = (float *)(gs + rb.ts.K + 1);
-    build_table(rb.tab, gs, rb.gtab, rb.ts.K, rb.ts.kind, rb.ts.sigma, rb.ts.H, rb.ts.band);
+    rb.gtab = (float *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
+    load_table(rb.tab, rb.gtab, rb.ts.K, t);
     rb.base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * warp_floats;
     return rb;
 }

@@ -36,6 +36,15 @@ struct DevParams {
     float gfit[2][kGainFitTerms];
 };
 
+// Noise-kernel tables of the RLE kernels for radius K = table_spec(p).K (fill_rle_table, on the
+// host in double, once per launch): tab[d + K + 1] = (sum_{e <= d} g(e), sum_{e <= d} e g(e))
+// for d = -K-1..K (tab[0] = 0, the second sum 0 at d = K), gtab[K + d] = g(d), d = -K..K.
+struct RleTable {
+    float2 tab[2 * FSMI_MAX_KERNEL_RADIUS + 2];
+    float gtab[2 * FSMI_MAX_KERNEL_RADIUS + 1];
+};
+void fill_rle_table(const DevParams &p, RleTable &t);
+
 constexpr int kMaxWarps = 8;  // most warps per block any evaluation kernel is launched with
 constexpr int kWarpsRLE = 4;  // warps per block of the RLE encoder kernels
 

@@ -180,10 +180,20 @@ __global__ void __launch_bounds__(32) k_mixed_plan(MixedSrc src, DevParams p2, D
     if (lane == 0) pl->valid = valid ? 1 : 0;
 }
 
+// a warp's cached set (class launches): class items [lo, hi) belong to the set st
+struct SetCache {
+    long long lo, hi;
+    fsmi_set st;
+    fsmi_volume vol;
+};
+constexpr int kSetCacheFloats = 24;  // 96 bytes per warp, keeping the next warp's arrays 16-byte aligned
+static_assert(sizeof(SetCache) <= kSetCacheFloats * sizeof(float), "set cache slot");
+
 // 64 registers (4 blocks of 8 warps): the 2D path needs no more, and residency bounds this kernel
 template <int VAR, int KIND>
 __global__ void __launch_bounds__(kMaxWarps * 32, 4)
-    k_eval_mixed(MixedSrc src, DevParams p2, DevParams p3, long long nitems, int stride2, int stride3, float *out,
+    k_eval_mixed(MixedSrc src, DevParams p2, DevParams p3, const __grid_constant__ RleTable tbl, long long nitems,
+                 int stride2, int stride3, float *out,
                  unsigned long long *times, int *status, unsigned long long *queue, int chunk,
                  const unsigned char *plan_raw, int bucket)
 {
@@ -206,45 +216,84 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
                     (size_t)bucket * (src.nsets + 1);
         }
     }
+    if (nloc <= 0) return;  // a class without sets
     // block: the RLE kernel table of the 3D parameters; then each warp's arrays, used by either kind
     RleBlock rb;
     rb.ts = table_spec(p3);
     rb.tab = (float2 *)smem_raw;
-    double *gs = (double *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
-    rb.gtab = (float *)(gs + rb.ts.K + 1);
-    if (src.has3d) build_table(rb.tab, gs, rb.gtab, rb.ts.K, rb.ts.kind, rb.ts.sigma, rb.ts.H, rb.ts.band);
-    const int per_warp = max(warp_floats_2d(stride2), ray3d_warp_floats(p3));
-    float *base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * per_warp;
+    rb.gtab = (float *)(smem_raw + (size_t)(2 * rb.ts.K + 2) * sizeof(float2));
+    if (src.has3d) load_table(rb.tab, rb.gtab, rb.ts.K, tbl);
+    const int per_warp = max(warp_floats_2d(stride2), ray3d_warp_floats(p3));  // then the set cache
+    float *base = (float *)(smem_raw + rle_table_bytes(rb.ts.K)) + (size_t)(threadIdx.x >> 5) * (per_warp + kSetCacheFloats);
     rb.base = base;
     if (times && threadIdx.x == 0) atomicMin(times, global_ns());
     const int lane = lane_id();
+    // a class launch keeps, in the warp's cache slot, the listed set of its last item: class items
+    // [lo, hi) belong to it, with its descriptor and volume. A warp's items come in grabs of
+    // consecutive items in increasing order, so most items find their set there instead of
+    // searching the class's list and reading the descriptors from global memory (shared memory
+    // rather than registers: the 2D path needs all 64 of them).
+    SetCache *cache = reinterpret_cast<SetCache *>(base + per_warp);
+    if (lane == 0) {
+        cache->lo = 0;
+        cache->hi = 0;
+    }
+    __syncwarp();
     for_each_item(nloc, queue, chunk, [&](long long li) {
         int si;
         long long item = li;
+        fsmi_set st{};
+        fsmi_volume vol{};
         if (blist) {  // the listed set holding class item li: the last with pref <= li
-            int lo = 0, len = nsb + 1;
-            while (len > 0) {
-                const int half = len >> 1;
-                if (bpref[lo + half] <= li) {
-                    lo += half + 1;
-                    len -= half + 1;
-                } else {
-                    len = half;
+            long long lo_i = cache->lo;
+            if (li < lo_i || li >= cache->hi) {
+                int lo = 0, len = nsb + 1;
+                while (len > 0) {
+                    const int half = len >> 1;
+                    if (bpref[lo + half] <= li) {
+                        lo += half + 1;
+                        len -= half + 1;
+                    } else {
+                        len = half;
+                    }
                 }
+                const int idx = min(lo - 1, nsb - 1);
+                si = idx >= 0 ? blist[idx] : -1;
+                lo_i = idx >= 0 ? bpref[idx] : 0;
+                if (si >= 0) st = src.sets[si];
+                if (si >= 0 && st.kind == FSMI_SET_3D && st.volume >= 0 && st.volume < src.nvol) vol = src.vols[st.volume];
+                __syncwarp();
+                if (lane == 0) {
+                    cache->lo = lo_i;
+                    cache->hi = si >= 0 ? bpref[idx + 1] : 0;  // an empty cache without a set
+                    cache->st = st;
+                    cache->vol = vol;
+                }
+                __syncwarp();
+            } else {
+                si = 0;  // a hit: the cached set is a listed one
+                st = cache->st;
+                vol = cache->vol;
             }
-            const int idx = min(lo - 1, nsb - 1);
-            si = idx >= 0 ? blist[idx] : -1;
-            if (si >= 0) item = src.sets[si].out_offset + (li - bpref[idx]);  // inside [0, nitems): planned
+            if (si >= 0) item = st.out_offset + (li - lo_i);  // inside [0, nitems): planned
         } else {
             si = mixed_set_of(src.sets, src.nsets, item);
+            if (si >= 0) st = src.sets[si];
+            if (si >= 0 && st.kind == FSMI_SET_3D && st.volume >= 0 && st.volume < src.nvol) vol = src.vols[st.volume];
         }
-        fsmi_set st{};
         bool ok = si >= 0;
-        if (ok) st = src.sets[si];
         const long long k = item - st.out_offset;
         ok = ok && st.npose >= 0 && st.ndir > 0 && k >= 0 && k < (long long)st.npose * st.ndir && st.pose_offset >= 0 &&
              st.dir_offset >= 0;
-        const long long pi = st.pose_offset + (ok ? k / st.ndir : 0), di = st.dir_offset + (ok ? k % st.ndir : 0);
+        long long kp = 0, kd = 0;  // pose and direction of item k (32-bit division when k fits)
+        if (ok && k <= 0x7fffffffLL) {
+            kp = (unsigned)k / (unsigned)st.ndir;
+            kd = k - kp * st.ndir;
+        } else if (ok) {
+            kp = k / st.ndir;
+            kd = k % st.ndir;
+        }
+        const long long pi = st.pose_offset + kp, di = st.dir_offset + kd;
         float I = __int_as_float(0x7fc00000);
         int bad = 0;
         if (KIND != kMix3DOther && KIND != kMix3DThm5 && ok && st.kind == FSMI_SET_2D && src.has2d && pi < src.P2 && di < src.B2 && st.max_range > 0.0f &&
@@ -262,7 +311,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
                 bad = FSMI_STATUS_BEAM_OVERFLOW;
         } else if (KIND != kMix2D && ok && st.kind == FSMI_SET_3D && src.has3d && pi < src.P3 && di < src.R3 && st.volume >= 0 &&
                    st.volume < src.nvol && st.max_range >= 1.0f && st.max_range <= (float)p3.nmax) {
-            const fsmi_volume v = src.vols[st.volume];
+            const fsmi_volume &v = vol;
             int nr = 0;
             constexpr int kMode = KIND == kMix3DOther ? kRay3dOther : KIND == kMix3DThm5 ? kRay3dThm5 : kRay3dAny;
             I = ray_mi_fused<kMode>(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range,
@@ -288,7 +337,7 @@ cudaError_t launch_mixed_variant(const MixedSrc &src, const DevParams &p2, const
     const Schedule &sc = current_schedule(KIND == kMix3DOther || KIND == kMix3DThm5 ? FSMI_KIND_RLE : FSMI_KIND_2D);
     const int stride2 = stride_2d(p2.nmax);
     const int stride3 = ((p3.nmax + 2 * p3.K + 4) + 3) & ~3;
-    const size_t per_warp = (size_t)max(warp_floats_2d(stride2), ray3d_warp_floats(p3)) * sizeof(float);
+    const size_t per_warp = ((size_t)max(warp_floats_2d(stride2), ray3d_warp_floats(p3)) + kSetCacheFloats) * sizeof(float);
     const size_t table = rle_table_bytes(table_spec(p3).K);
     const int wpb = fit_warps(sc.warps_per_block, per_warp, table);
     const size_t smem = table + (size_t)wpb * per_warp;
@@ -310,7 +359,9 @@ cudaError_t launch_mixed_variant(const MixedSrc &src, const DevParams &p2, const
         e = cudaMemsetAsync(times, 0xFF, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(src, p2, p3, nitems, stride2, stride3, out, times, status, queue,
+    RleTable tbl{};
+    if (src.has3d) fill_rle_table(p3, tbl);
+    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(src, p2, p3, tbl, nitems, stride2, stride3, out, times, status, queue,
                                                 sc.queue_chunk > 0 ? sc.queue_chunk : 1, plan, bucket);
     return cudaGetLastError();
 }

@@ -1,4 +1,5 @@
 // RLE / 3D kernels and their launchers; the per-ray device code is in evalrle.cuh.
+#include <cmath>
 #include <mutex>
 
 #include "evalrle.cuh"
@@ -9,21 +10,21 @@ namespace fsmi {
 // picks by thm5_of(p)), so that each kernel holds only the paths it can take.
 template <int MODE>
 __global__ void __launch_bounds__(kMaxWarps * 32)
-    k_eval_3d(Vox3D vx, DevParams p, long long nrays, int warp_floats, float *__restrict__ out,
-              int32_t *__restrict__ nruns, unsigned long long *queue, int chunk)
+    k_eval_3d(Vox3D vx, DevParams p, const __grid_constant__ RleTable tbl, long long nrays, int warp_floats,
+              float *__restrict__ out, int32_t *__restrict__ nruns, unsigned long long *queue, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RleBlock rb = rle_block(smem_raw, p, warp_floats);
+    const RleBlock rb = rle_block(smem_raw, p, tbl, warp_floats);
     for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d<MODE>(vx, p, rb, ray, out, nruns); });
 }
 
 __global__ void __launch_bounds__(kMaxWarps * 32)
     k_eval_rle(const int32_t *__restrict__ off, const float *__restrict__ ro, const uint8_t *__restrict__ rl,
-               DevParams p, long long nrays, int stride, float *__restrict__ out, int *status,
-               unsigned long long *queue, int chunk)
+               DevParams p, const __grid_constant__ RleTable tbl, long long nrays, int stride, float *__restrict__ out,
+               int *status, unsigned long long *queue, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RleBlock rb = rle_block(smem_raw, p, kArraysRLE * stride);
+    const RleBlock rb = rle_block(smem_raw, p, tbl, kArraysRLE * stride);
     for_each_item(nrays, queue, chunk,
                   [&](long long ray) { eval_ray_rle(off, ro, rl, p, rb, stride, ray, out, status); });
 }
@@ -174,6 +175,38 @@ __global__ void k_scan_add(int32_t *a, long long n, const int32_t *tot)
 
 static int rle_stride(int nmax, int K) { return ((nmax + 2 * K + 4) + 3) & ~3; }  // cells + 2K padding
 
+// The noise-kernel tables of one launch (RleTable), from g(d) = (1/(sqrt(2 pi) sigma))
+// exp(-d^2 / (2 sigma^2)) (Theorem 3's density), the cell mass Phi((d + 1/2)/sigma) -
+// Phi((d - 1/2)/sigma), or 1[|d| <= H] / (2H + 1) (Theorem 6), zero beyond the strict band.
+void fill_rle_table(const DevParams &p, RleTable &t)
+{
+    const TabSpec ts = table_spec(p);
+    const int K = ts.K;
+    double g[FSMI_MAX_KERNEL_RADIUS + 1];
+    const double s2 = ts.sigma * 1.4142135623730951;
+    for (int a = 0; a <= K; ++a) {
+        double v;
+        if (ts.kind == 2)
+            v = (a <= ts.H) ? 1.0 / (2.0 * ts.H + 1.0) : 0.0;
+        else if (ts.kind == 1)
+            v = 0.5 * (std::erfc(-(a + 0.5) / s2) - std::erfc(-(a - 0.5) / s2));
+        else
+            v = std::exp(-(double)a * a / (2.0 * ts.sigma * ts.sigma)) / (2.5066282746310002 * ts.sigma);
+        if (ts.band >= 0 && a > ts.band) v = 0.0;
+        g[a] = v;
+        t.gtab[K + a] = (float)v;
+        t.gtab[K - a] = (float)v;
+    }
+    double c0 = 0.0, c1 = 0.0;
+    t.tab[0] = make_float2(0.0f, 0.0f);
+    for (int d = -K; d <= K; ++d) {
+        const double v = g[d < 0 ? -d : d];
+        c0 += v;
+        c1 += (double)d * v;
+        t.tab[d + K + 1] = make_float2((float)c0, (float)(d == K ? 0.0 : c1));
+    }
+}
+
 template <typename Kern>
 static cudaError_t grid_for(Kern k, size_t smem, long long nitems, int wpb, int bps, long long &grid)
 {
@@ -212,7 +245,9 @@ cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32
     cudaError_t e = grid_for(kern, smem, nrays, wpb, sc.blocks_per_sm, grid);
     if (e == cudaSuccess) e = reset_queue(queue, s);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(v, p, nrays, wf, out, nruns, queue,
+    RleTable tbl;
+    fill_rle_table(p, tbl);
+    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(v, p, tbl, nrays, wf, out, nruns, queue,
                                                 sc.queue_chunk > 0 ? sc.queue_chunk : 1);
     return cudaGetLastError();
 }
@@ -230,8 +265,10 @@ cudaError_t launch_eval_rle(const int32_t *run_off, const float *run_o, const ui
     cudaError_t e = grid_for(k_eval_rle, smem, nrays, wpb, sc.blocks_per_sm, grid);
     if (e == cudaSuccess) e = reset_queue(queue, s);
     if (e != cudaSuccess) return e;
-    k_eval_rle<<<(unsigned)grid, wpb * 32, smem, s>>>(run_off, run_o, run_len, p, nrays, stride, out, status, queue,
-                                                      sc.queue_chunk > 0 ? sc.queue_chunk : 1);
+    RleTable tbl;
+    fill_rle_table(p, tbl);
+    k_eval_rle<<<(unsigned)grid, wpb * 32, smem, s>>>(run_off, run_o, run_len, p, tbl, nrays, stride, out, status,
+                                                      queue, sc.queue_chunk > 0 ? sc.queue_chunk : 1);
     return cudaGetLastError();
 }
 
