@@ -180,14 +180,23 @@ __global__ void __launch_bounds__(32) k_mixed_plan(MixedSrc src, DevParams p2, D
     if (lane == 0) pl->valid = valid ? 1 : 0;
 }
 
-// a warp's cached set (class launches): class items [lo, hi) belong to the set st
-struct SetCache {
-    long long lo, hi;
-    fsmi_set st;
-    fsmi_volume vol;
+// A class launch's per-warp record of the set its items come from: class items [lo, hi) belong to
+// it, class item lo is output item0, its poses and directions start at pose / dir with ndir
+// directions per pose, and the last item taken (class item next - 1) was pose kp, direction kd.
+// The plan checked every descriptor (index ranges, ranges within bounds, volume index), so a
+// class launch reads them once per set rather than once per item.
+struct ClassCache {
+    long long lo, hi, item0, next;
+    const int32_t *pose, *dir;
+    const float *vox;  // 3D: the set's volume
+    long long rfix;    // 2D: Q16 range
+    float rend;        // 2D: the range as float
+    int X, Y, Z;       // 3D: the volume's extent
+    int nsamp;         // 3D: virtual cells per ray
+    int ndir, kp, kd;
 };
-constexpr int kSetCacheFloats = 24;  // 96 bytes per warp, keeping the next warp's arrays 16-byte aligned
-static_assert(sizeof(SetCache) <= kSetCacheFloats * sizeof(float), "set cache slot");
+constexpr int kSetCacheFloats = 32;  // 128 bytes per warp, keeping the next warp's arrays 16-byte aligned
+static_assert(sizeof(ClassCache) <= kSetCacheFloats * sizeof(float), "class cache slot");
 
 // 64 registers (4 blocks of 8 warps): the 2D path needs no more, and residency bounds this kernel
 template <int VAR, int KIND>
@@ -201,20 +210,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     // with a plan: a class launch (bucket >= 0) takes its class's items and runs only if the plan is
     // valid; the single launch (bucket < 0) runs only if it is not
     long long nloc = nitems;
-    const int *blist = nullptr;
-    const long long *bpref = nullptr;
-    int nsb = 0;
     if (plan_raw) {
         const MixedPlan *pl = reinterpret_cast<const MixedPlan *>(plan_raw);
         const bool valid = pl->valid != 0;
         if (bucket < 0 ? valid : !valid) return;
-        if (bucket >= 0) {
-            nloc = pl->count[bucket];
-            nsb = pl->nsb[bucket];
-            blist = reinterpret_cast<const int *>(plan_raw + sizeof(MixedPlan)) + (size_t)bucket * src.nsets;
-            bpref = reinterpret_cast<const long long *>(plan_raw + sizeof(MixedPlan) + plan_list_bytes(src.nsets)) +
-                    (size_t)bucket * (src.nsets + 1);
-        }
+        if (bucket >= 0) nloc = pl->count[bucket];
     }
     if (nloc <= 0) return;  // a class without sets
     // block: the RLE kernel table of the 3D parameters; then each warp's arrays, used by either kind
@@ -228,25 +228,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
     rb.base = base;
     if (times && threadIdx.x == 0) atomicMin(times, global_ns());
     const int lane = lane_id();
-    // a class launch keeps, in the warp's cache slot, the listed set of its last item: class items
-    // [lo, hi) belong to it, with its descriptor and volume. A warp's items come in grabs of
-    // consecutive items in increasing order, so most items find their set there instead of
-    // searching the class's list and reading the descriptors from global memory (shared memory
-    // rather than registers: the 2D path needs all 64 of them).
-    SetCache *cache = reinterpret_cast<SetCache *>(base + per_warp);
-    if (lane == 0) {
-        cache->lo = 0;
-        cache->hi = 0;
-    }
-    __syncwarp();
-    for_each_item(nloc, queue, chunk, [&](long long li) {
-        int si;
-        long long item = li;
-        fsmi_set st{};
-        fsmi_volume vol{};
-        if (blist) {  // the listed set holding class item li: the last with pref <= li
-            long long lo_i = cache->lo;
-            if (li < lo_i || li >= cache->hi) {
+    if (KIND != kMixAny) {  // a class launch of a valid plan: one kind, descriptors checked by the plan
+        ClassCache *cc = reinterpret_cast<ClassCache *>(base + per_warp);
+        if (lane == 0) {
+            cc->lo = 0;
+            cc->hi = 0;
+        }
+        __syncwarp();
+        for_each_item(nloc, queue, chunk, [&](long long li) {
+            long long kp, kd;
+            if (li < cc->lo || li >= cc->hi) {  // the listed set holding class item li: the last with pref <= li
+                // (the plan's lists are read here, not held in registers across the items)
+                const MixedPlan *pl = reinterpret_cast<const MixedPlan *>(plan_raw);
+                const int nsb = pl->nsb[bucket];
+                const int *blist = reinterpret_cast<const int *>(plan_raw + sizeof(MixedPlan)) + (size_t)bucket * src.nsets;
+                const long long *bpref = reinterpret_cast<const long long *>(plan_raw + sizeof(MixedPlan) +
+                                                                             plan_list_bytes(src.nsets)) +
+                                         (size_t)bucket * (src.nsets + 1);
                 int lo = 0, len = nsb + 1;
                 while (len > 0) {
                     const int half = len >> 1;
@@ -257,46 +255,94 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
                         len = half;
                     }
                 }
-                const int idx = min(lo - 1, nsb - 1);
-                si = idx >= 0 ? blist[idx] : -1;
-                lo_i = idx >= 0 ? bpref[idx] : 0;
-                if (si >= 0) st = src.sets[si];
-                if (si >= 0 && st.kind == FSMI_SET_3D && st.volume >= 0 && st.volume < src.nvol) vol = src.vols[st.volume];
+                const int idx = min(lo - 1, nsb - 1);  // >= 0: li >= pref[0] = 0
+                const fsmi_set st = src.sets[blist[idx]];
+                const long long k = li - bpref[idx];
+                kp = k / st.ndir;
+                kd = k - kp * st.ndir;
                 __syncwarp();
                 if (lane == 0) {
-                    cache->lo = lo_i;
-                    cache->hi = si >= 0 ? bpref[idx + 1] : 0;  // an empty cache without a set
-                    cache->st = st;
-                    cache->vol = vol;
+                    cc->lo = bpref[idx];
+                    cc->hi = bpref[idx + 1];
+                    cc->item0 = st.out_offset;
+                    cc->ndir = st.ndir;
+                    if (KIND == kMix2D) {
+                        cc->pose = src.poses2 + 4 * (size_t)st.pose_offset;
+                        cc->dir = src.dirs2 + 2 * (size_t)st.dir_offset;
+                        cc->rfix = __double2ll_rn((double)st.max_range * 65536.0);
+                        cc->rend = (float)((double)cc->rfix * (1.0 / 65536.0));
+                    } else {
+                        const fsmi_volume v = src.vols[st.volume];
+                        cc->pose = src.poses3 + 12 * (size_t)st.pose_offset;
+                        cc->dir = src.dirs3 + 3 * (size_t)st.dir_offset;
+                        cc->vox = v.vox;
+                        cc->X = v.X;
+                        cc->Y = v.Y;
+                        cc->Z = v.Z;
+                        cc->nsamp = (int)st.max_range;
+                    }
                 }
                 __syncwarp();
+            } else if (li == cc->next) {  // the item after the last one: the next direction
+                kp = cc->kp;
+                kd = cc->kd + 1;
+                if (kd == cc->ndir) {
+                    kd = 0;
+                    ++kp;
+                }
             } else {
-                si = 0;  // a hit: the cached set is a listed one
-                st = cache->st;
-                vol = cache->vol;
+                const long long k = li - cc->lo;
+                const int nd = cc->ndir;
+                kp = k <= 0x7fffffffLL ? (long long)((unsigned)k / (unsigned)nd) : k / nd;
+                kd = k - kp * nd;
             }
-            if (si >= 0) item = st.out_offset + (li - lo_i);  // inside [0, nitems): planned
-        } else {
-            si = mixed_set_of(src.sets, src.nsets, item);
-            if (si >= 0) st = src.sets[si];
-            if (si >= 0 && st.kind == FSMI_SET_3D && st.volume >= 0 && st.volume < src.nvol) vol = src.vols[st.volume];
-        }
+            const long long item = cc->item0 + (li - cc->lo);
+            float I;
+            int bad = 0;
+            if (KIND == kMix2D) {
+                float *sl, *sc, *sp, *sx;
+                carve_2d(base, stride2, sl, sc, sp, sx);
+                const int32_t *d = cc->dir + 2 * kd;
+                const int n = beam_cells<false>(src.map, src.W, src.H, src.gains, cc->pose + 4 * kp, d[0], d[1], cc->rfix,
+                                                cc->rend, p2.nmax, p2, 0, nullptr, sl, sc, sp, sx, status);
+                if (n >= 0) {
+                    I = beam_sum<VAR>(p2, n, sl, sc, sp, sx);
+                } else {
+                    I = __int_as_float(0x7fc00000);
+                    bad = FSMI_STATUS_BEAM_OVERFLOW;
+                }
+            } else {
+                int nr = 0;
+                constexpr int kMode = KIND == kMix3DThm5 ? kRay3dThm5 : kRay3dOther;
+                I = ray_mi_fused<kMode>(cc->vox, cc->X, cc->Y, cc->Z, cc->pose + 12 * kp, cc->dir + 3 * kd, cc->nsamp, p3,
+                                        rb.tab, rb.gtab, rb.ts.K, base, &nr);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                out[item] = I;
+                if (bad) set_status(status, bad);
+                if (times) times[1 + item] = global_ns();
+                cc->next = li + 1;
+                cc->kp = (int)kp;
+                cc->kd = (int)kd;
+            }
+            __syncwarp();
+        });
+        return;
+    }
+    // the single launch: every item's descriptor checked before it is used
+    for_each_item(nloc, queue, chunk, [&](long long item) {
+        const int si = mixed_set_of(src.sets, src.nsets, item);
+        fsmi_set st{};
         bool ok = si >= 0;
+        if (ok) st = src.sets[si];
         const long long k = item - st.out_offset;
         ok = ok && st.npose >= 0 && st.ndir > 0 && k >= 0 && k < (long long)st.npose * st.ndir && st.pose_offset >= 0 &&
              st.dir_offset >= 0;
-        long long kp = 0, kd = 0;  // pose and direction of item k (32-bit division when k fits)
-        if (ok && k <= 0x7fffffffLL) {
-            kp = (unsigned)k / (unsigned)st.ndir;
-            kd = k - kp * st.ndir;
-        } else if (ok) {
-            kp = k / st.ndir;
-            kd = k % st.ndir;
-        }
-        const long long pi = st.pose_offset + kp, di = st.dir_offset + kd;
+        const long long pi = st.pose_offset + (ok ? k / st.ndir : 0), di = st.dir_offset + (ok ? k % st.ndir : 0);
         float I = __int_as_float(0x7fc00000);
         int bad = 0;
-        if (KIND != kMix3DOther && KIND != kMix3DThm5 && ok && st.kind == FSMI_SET_2D && src.has2d && pi < src.P2 && di < src.B2 && st.max_range > 0.0f &&
+        if (ok && st.kind == FSMI_SET_2D && src.has2d && pi < src.P2 && di < src.B2 && st.max_range > 0.0f &&
             st.max_range <= p2.rmax) {
             const long long rfix = __double2ll_rn((double)st.max_range * 65536.0);
             const float rend = (float)((double)rfix * (1.0 / 65536.0));
@@ -309,13 +355,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 4)
                 I = beam_sum<VAR>(p2, n, sl, sc, sp, sx);
             else
                 bad = FSMI_STATUS_BEAM_OVERFLOW;
-        } else if (KIND != kMix2D && ok && st.kind == FSMI_SET_3D && src.has3d && pi < src.P3 && di < src.R3 && st.volume >= 0 &&
+        } else if (ok && st.kind == FSMI_SET_3D && src.has3d && pi < src.P3 && di < src.R3 && st.volume >= 0 &&
                    st.volume < src.nvol && st.max_range >= 1.0f && st.max_range <= (float)p3.nmax) {
-            const fsmi_volume &v = vol;
+            const fsmi_volume v = src.vols[st.volume];
             int nr = 0;
-            constexpr int kMode = KIND == kMix3DOther ? kRay3dOther : KIND == kMix3DThm5 ? kRay3dThm5 : kRay3dAny;
-            I = ray_mi_fused<kMode>(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range,
-                                    p3, rb.tab, rb.gtab, rb.ts.K, base, &nr);
+            I = ray_mi_fused<kRay3dAny>(v.vox, v.X, v.Y, v.Z, src.poses3 + 12 * pi, src.dirs3 + 3 * di, (int)st.max_range,
+                                        p3, rb.tab, rb.gtab, rb.ts.K, base, &nr);
         } else {
             bad = FSMI_STATUS_BAD_BEAM;  // a malformed descriptor is never used to index
         }
