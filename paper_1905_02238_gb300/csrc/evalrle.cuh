@@ -22,6 +22,7 @@
 
 #include "../../include/fsmi.h"
 #include "fsmi_device.cuh"
+#include "gauss_tail.cuh"
 #include "fsmi_internal.h"
 
 namespace fsmi {
@@ -31,6 +32,30 @@ namespace fsmi {
 __device__ __forceinline__ float rle_gain(const DevParams &p, int which, float o)
 {
     return p.gain_fit ? gain_series(p.gfit[which], o) : cell_gain(which ? p.demp : p.docc, o);
+}
+
+// Both gains of one o: the two series evaluated together in packed FP32 (each half of an f32x2
+// operation rounds as the scalar one does, so fo and fe equal rle_gain(p, 0, o) and
+// rle_gain(p, 1, o) bit for bit), or the closed forms.
+__device__ __forceinline__ void rle_gains(const DevParams &p, float o, float &fo, float &fe)
+{
+    if (!p.gain_fit) {
+        fo = cell_gain(p.docc, o);
+        fe = cell_gain(p.demp, o);
+        return;
+    }
+    const float x2 = __fmaf_rn(4.0f, o, -2.0f);  // 2x, x = 2o - 1
+    const f32x2 X2 = pack2(x2, x2);
+    f32x2 b1 = pack2(0.0f, 0.0f), b2 = b1;
+#pragma unroll
+    for (int k = kGainFitTerms - 1; k >= 1; --k) {
+        const f32x2 b0 = fma2(X2, b1, sub2(pack2(p.gfit2[k][0], p.gfit2[k][1]), b2));
+        b2 = b1;
+        b1 = b0;
+    }
+    const f32x2 h = fma2(mul2(pack2(0.5f, 0.5f), X2), b1, sub2(pack2(p.gfit2[0][0], p.gfit2[0][1]), b2));
+    const float w = __fmul_rn(o, __fsub_rn(1.0f, o));
+    unpack2(mul2(pack2(w, w), h), fo, fe);
 }
 
 // ---- noise-kernel prefix tables --------------------------------------------------------------
@@ -287,9 +312,10 @@ static __device__ float ray_mi_cells(float *base, int stride, int nr, int n, con
     const int *S = (const int *)(base + 4 * stride);
     float *CF = base + 5 * stride, *CC = base + 6 * stride;
     for (int u = lane; u < nr; u += 32) {
-        const float o = O[u];
-        RFO[u] = rle_gain(p, 0, o);
-        RFE[u] = rle_gain(p, 1, o);
+        float fo, fe;
+        rle_gains(p, O[u], fo, fe);
+        RFO[u] = fo;
+        RFE[u] = fe;
     }
     for (int i = lane; i < K; i += 32) {
         CC[i] = 0.0f;
@@ -395,10 +421,7 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         }
         if (CP) {
             float fo = 0.0f, fe = 0.0f;
-            if (newval) {
-                fo = rle_gain(*gp, 0, val);
-                fe = rle_gain(*gp, 1, val);
-            }
+            if (newval) rle_gains(*gp, val, fo, fe);
             const int src = st - base;  // lane where this cell's run of equal values starts, if in this chunk
             const float so = __shfl_sync(kFull, fo, src >= 0 ? src : 0);
             const float se = __shfl_sync(kFull, fe, src >= 0 ? src : 0);

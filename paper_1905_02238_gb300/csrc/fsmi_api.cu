@@ -104,6 +104,10 @@ static void fit_gains(DevParams &d)
     if (d.docc == last_docc && d.demp == last_demp) {
         d.gain_fit = last_ok;
         memcpy(d.gfit, last_c, sizeof(last_c));
+        for (int k = 0; k < kGainFitTerms; ++k) {
+            d.gfit2[k][0] = d.gfit[0][k];
+            d.gfit2[k][1] = d.gfit[1][k];
+        }
         return;
     }
     const int N = kGainFitTerms;
@@ -130,6 +134,10 @@ static void fit_gains(DevParams &d)
         for (double t = 1e-7; t < 1e-2 && ok; t *= 1.25) ok = check((float)t) && check((float)(1.0 - t));
     }
     d.gain_fit = ok ? 1 : 0;
+    for (int k = 0; k < N; ++k) {
+        d.gfit2[k][0] = d.gfit[0][k];
+        d.gfit2[k][1] = d.gfit[1][k];
+    }
     last_docc = d.docc;
     last_demp = d.demp;
     last_ok = d.gain_fit;
@@ -169,6 +177,7 @@ fsmi_status make_params(const fsmi_params *prm, Use use, DevParams &d)
     d.K = 0;
     d.gain_fit = 0;
     memset(d.gfit, 0, sizeof(d.gfit));
+    memset(d.gfit2, 0, sizeof(d.gfit2));
     if (use == kUse2D) {
         if (prm->max_range > FSMI_MAX_RANGE_2D) return FSMI_ERR_CAPACITY;
         d.rfix = llrint((double)prm->max_range * 65536.0);

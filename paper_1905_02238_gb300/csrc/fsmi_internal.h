@@ -34,6 +34,7 @@ struct DevParams {
     // delta_emp ([1]), used by the RLE kernels when gain_fit is set (see gain_series)
     int gain_fit;
     float gfit[2][kGainFitTerms];
+    float gfit2[kGainFitTerms][2];  // the same coefficients interleaved (delta_occ, delta_emp) per term
 };
 
 // Noise-kernel tables of the RLE kernels for radius K = table_spec(p).K (fill_rle_table, on the
