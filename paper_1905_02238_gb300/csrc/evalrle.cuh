@@ -386,6 +386,7 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
 #pragma unroll
     for (int a = 0; a < 3; ++a) q[a] = o[a] + (2LL * lane + 1) * d[a];
     const float inv_cap = 1.0f / (float)cap;
+    const unsigned lane_le = 0xffffffffu >> (31 - lane);  // lanes 0 .. lane
     for (int base = 0; base < nsamp; base += 32) {
         const int i = base + lane;
         bool inb = false;
@@ -405,8 +406,10 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         unsigned pbits = __shfl_up_sync(kFull, bits, 1);
         if (lane == 0) pbits = prev_bits;
         const bool newval = valid && (i == 0 || bits != pbits);
-        int st = warp_incl_max_int(newval ? i : -1);
-        st = max(st, carried);
+        // start of this cell's span of equal values: the last lane at or before this one where a new
+        // value begins, else the span carried over from the previous chunk
+        const unsigned nle = __ballot_sync(kFull, newval) & lane_le;
+        const int st = nle ? base + 31 - __clz(nle) : carried;
         // a run of equal values splits every cap samples: (i - st) a multiple of cap, found with a
         // rounded quotient (exact: i - st < 2^20 and cap <= 255) instead of an integer remainder
         const int rel = i - st;

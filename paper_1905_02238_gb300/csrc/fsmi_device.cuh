@@ -55,16 +55,6 @@ __device__ __forceinline__ int warp_incl_add_int(int v)
     return v;
 }
 
-__device__ __forceinline__ int warp_incl_max_int(int v)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(kFull, v, o);
-        if (lane_id() >= o) v = max(v, t);
-    }
-    return v;
-}
-
 // Information gain of one cell whose odds are multiplied by delta (Section 2.2). Written as the
 // Bernoulli KL divergence between posterior o' = o delta / (1 + a), a = o (delta - 1), and prior
 // o, which equals the printed f(delta, r) and stays accurate as o -> 0 or 1:
