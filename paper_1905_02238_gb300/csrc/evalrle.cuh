@@ -361,16 +361,16 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
 // first sample outside the grid. Runs are maximal spans of bit-identical values split every `cap`
 // cells from the span's start. Writes O[u] = value, S[u] = first cell, S[nr] = n; returns nr.
 //
-// Fused form (CP != nullptr): also writes every virtual cell's o (CP), f(delta_occ, o) (CCk) and
-// f(delta_emp, o) (CF); the gains are evaluated once per run of equal values, by the lane where the
-// run starts, and passed to the run's other cells by shuffles. Runs past nrcap are counted but not
-// stored; *n_out receives n.
+// Fused form (CP != nullptr): also writes every virtual cell's o (CP) and, in SP[k], the value of
+// the k-th span of equal values (k counted over the ray; *nspan_out receives their number), from
+// which span_gains fills in the cells' gains. Runs past nrcap are counted but not stored; *n_out
+// receives n.
 static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, int Y, int Z, const int32_t *pose,
                                         const int32_t *u, int nsamp, int cap, float *O, int *S, int nrcap, int *n_out,
-                                        float *CP, float *CCk, float *CF, const DevParams *gp)
+                                        float *CP, float *SP, int *nspan_out)
 {
     const int lane = lane_id();
-    float carried_fo = 0.0f, carried_fe = 0.0f;
+    int nspan = 0;
     long long d[3], o[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -408,7 +408,8 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         const bool newval = valid && (i == 0 || bits != pbits);
         // start of this cell's span of equal values: the last lane at or before this one where a new
         // value begins, else the span carried over from the previous chunk
-        const unsigned nle = __ballot_sync(kFull, newval) & lane_le;
+        const unsigned mnew = __ballot_sync(kFull, newval);
+        const unsigned nle = mnew & lane_le;
         const int st = nle ? base + 31 - __clz(nle) : carried;
         // a run of equal values splits every cap samples: (i - st) a multiple of cap, found with a
         // rounded quotient (exact: i - st < 2^20 and cap <= 255) instead of an integer remainder
@@ -423,19 +424,9 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
             }
         }
         if (CP) {
-            float fo = 0.0f, fe = 0.0f;
-            if (newval) rle_gains(*gp, val, fo, fe);
-            const int src = st - base;  // lane where this cell's run of equal values starts, if in this chunk
-            const float so = __shfl_sync(kFull, fo, src >= 0 ? src : 0);
-            const float se = __shfl_sync(kFull, fe, src >= 0 ? src : 0);
-            const float go = src >= 0 ? so : carried_fo, ge = src >= 0 ? se : carried_fe;
-            if (valid) {
-                CP[i] = val;
-                CCk[i] = go;
-                CF[i] = ge;
-            }
-            carried_fo = __shfl_sync(kFull, go, 31);
-            carried_fe = __shfl_sync(kFull, ge, 31);
+            if (valid) CP[i] = val;
+            if (newval) SP[nspan + __popc(nle) - 1] = val;  // span index <= cell index
+            nspan += __popc(mnew);
         }
         nrun += __popc(mb);
         n += nvalid;
@@ -445,6 +436,7 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
     }
     if (lane == 0 && nrun <= nrcap) S[nrun] = n;
     if (n_out) *n_out = n;
+    if (nspan_out) *nspan_out = nspan;
     __syncwarp();
     return nrun;
 }
@@ -452,8 +444,7 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
 static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, int Y, int Z, const int32_t *pose,
                                         const int32_t *u, int nsamp, int cap, float *O, int *S)
 {
-    return sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, cap, O, S, nsamp + 1, nullptr, nullptr, nullptr, nullptr,
-                             nullptr);
+    return sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, cap, O, S, nsamp + 1, nullptr, nullptr, nullptr, nullptr);
 }
 
 // ---- the fused 3D ray (sampling and evaluation in one warp) --------------------------------------
@@ -480,6 +471,45 @@ __host__ __device__ inline int ray3d_warp_floats(const DevParams &p)
 // Theorem 5's sub-blocks only, or the others (cell-level convolution and all run pairs) only.
 enum { kRay3dAny = 0, kRay3dThm5 = 1, kRay3dOther = 2 };
 
+// The cells' gains f(delta_occ, o) (Gk) and f(delta_emp, o) (Gf) of a sampled ray: the nspan spans
+// of equal values (their values in Gf[0 .. nspan), from sampling) get both gains once, stored in
+// place at Gk[k] and Gf[k]; then every cell takes its span's pair, the chunks of 32 cells from the
+// last down, each reading before any lane writes: cell i's span index is at most i, so a chunk
+// only overwrites entries that no cell below it reads. A cell starts a span where its value's bits
+// differ from the previous cell's, as in the sampling.
+__device__ __forceinline__ void span_gains(const DevParams &p, const float *CP, float *Gk, float *Gf, int n, int nspan)
+{
+    const int lane = lane_id();
+    for (int k = lane; k < nspan; k += 32) {
+        float fo, fe;
+        rle_gains(p, Gf[k], fo, fe);
+        Gk[k] = fo;
+        Gf[k] = fe;
+    }
+    __syncwarp();
+    const unsigned lane_le = 0xffffffffu >> (31 - lane);
+    int above = nspan;  // spans that start in the chunks above the current one, counted from the end
+    for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
+        const int i = base + lane;
+        const bool in = i < n;
+        const bool start = in && (i == 0 || __float_as_uint(CP[i]) != __float_as_uint(CP[i - 1]));
+        const unsigned m = __ballot_sync(kFull, start);
+        above -= __popc(m);  // now: spans that start before this chunk
+        const int k = above + __popc(m & lane_le) - 1;
+        float go = 0.0f, ge = 0.0f;
+        if (in) {
+            go = Gk[k];
+            ge = Gf[k];
+        }
+        __syncwarp();
+        if (in) {
+            Gk[i] = go;
+            Gf[i] = ge;
+        }
+        __syncwarp();
+    }
+}
+
 // Samples, encodes and evaluates one ray into the warp's region `w` (ray3d_warp_floats floats);
 // returns the MI (warp-reduced) and the run count in *nr_out. MODE must agree with thm5_of(p).
 template <int MODE>
@@ -492,9 +522,9 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
     const int cst = ray3d_cell_stride(p);
     float *CP = thm5 ? nullptr : w, *CF = w + cst, *CC = w + 2 * cst;
     const RunSmem r = run_smem(w + (thm5 ? 0 : 3 * cst), ray3d_run_stride(p));
-    int n = 0;
-    const int nr = sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, p.run_cap, r.O, r.S, ray3d_nrcap(p), &n, CP,
-                                     CC + K, CF, &p);
+    int n = 0, nspan = 0;
+    const int nr = sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, p.run_cap, r.O, r.S, ray3d_nrcap(p), &n, CP, CF,
+                                     &nspan);
     *nr_out = nr;
     if (nr <= 0) return 0.0f;
     float v;
@@ -504,7 +534,7 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
             CC[i] = 0.0f;
             CC[K + n + i] = 0.0f;
         }
-        __syncwarp();
+        span_gains(p, CP, CC + K, CF, n, nspan);
         cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
         v = band_conv<MODE == kRay3dOther>(CP, CC, gtab, K, n);
     } else {  // here n_r <= nrcap, so every run was stored
