@@ -545,10 +545,23 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
     return warp_sum(v);
 }
 
+// pose and ray of batch item `ray` = pose * R + r (a 32-bit division when ray fits, the common case)
+__device__ __forceinline__ void split_ray(long long ray, int R, int &pi, int &ri)
+{
+    if (ray <= 0x7fffffffLL) {
+        pi = (int)((unsigned)ray / (unsigned)R);
+        ri = (int)((unsigned)ray - (unsigned)pi * (unsigned)R);
+    } else {
+        pi = (int)(ray / R);
+        ri = (int)(ray % R);
+    }
+}
+
 // ray = pose * R + r of a batch
 __device__ __forceinline__ int sample_encode(const Vox3D &v, long long ray, int nsamp, int cap, float *O, int *S)
 {
-    const int pi = (int)(ray / v.R), ri = (int)(ray % v.R);
+    int pi, ri;
+    split_ray(ray, v.R, pi, ri);
     return sample_encode_ray(v.vox, v.X, v.Y, v.Z, v.poses + 12 * (size_t)pi, v.dirs + 3 * (size_t)ri, nsamp, cap, O,
                              S);
 }
@@ -603,12 +616,20 @@ __device__ __forceinline__ RleBlock rle_block(unsigned char *smem_raw, const Dev
     return rb;
 }
 
-// sampling, encoding and evaluation of one 3D ray (= pose * R + r), fused layout
-template <int MODE>
+// sampling, encoding and evaluation of one 3D ray (= pose * R + r), fused layout; WIDE: the batch
+// has more than 2^31 - 1 rays (64-bit index division), else a 32-bit one
+template <int MODE, bool WIDE>
 __device__ __forceinline__ void eval_ray_3d(const Vox3D &vx, const DevParams &p, const RleBlock &rb,
                                             long long ray, float *__restrict__ out, int32_t *__restrict__ nruns)
 {
-    const int pi = (int)(ray / vx.R), ri = (int)(ray % vx.R);
+    int pi, ri;
+    if (WIDE) {
+        pi = (int)(ray / vx.R);
+        ri = (int)(ray % vx.R);
+    } else {
+        pi = (int)((unsigned)ray / (unsigned)vx.R);
+        ri = (int)((unsigned)ray - (unsigned)pi * (unsigned)vx.R);
+    }
     int nr = 0;
     const float I = ray_mi_fused<MODE>(vx.vox, vx.X, vx.Y, vx.Z, vx.poses + 12 * (size_t)pi, vx.dirs + 3 * (size_t)ri, p.nmax,
                                  p, rb.tab, rb.gtab, rb.ts.K, rb.base, &nr);

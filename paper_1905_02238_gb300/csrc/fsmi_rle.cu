@@ -7,15 +7,16 @@
 namespace fsmi {
 
 // MODE: kRay3dThm5 for Theorem 5's sub-blocks, kRay3dOther for every other variant (the launcher
-// picks by thm5_of(p)), so that each kernel holds only the paths it can take.
-template <int MODE>
+// picks by thm5_of(p)), so that each kernel holds only the paths it can take; WIDE for batches of
+// more than 2^31 - 1 rays (a 64-bit ray index division, which costs the others registers).
+template <int MODE, bool WIDE>
 __global__ void __launch_bounds__(kMaxWarps * 32)
     k_eval_3d(Vox3D vx, DevParams p, const __grid_constant__ RleTable tbl, long long nrays, int warp_floats,
               float *__restrict__ out, int32_t *__restrict__ nruns, unsigned long long *queue, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RleBlock rb = rle_block(smem_raw, p, tbl, warp_floats);
-    for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d<MODE>(vx, p, rb, ray, out, nruns); });
+    for_each_item(nrays, queue, chunk, [&](long long ray) { eval_ray_3d<MODE, WIDE>(vx, p, rb, ray, out, nruns); });
 }
 
 __global__ void __launch_bounds__(kMaxWarps * 32)
@@ -241,7 +242,9 @@ cudaError_t launch_eval_3d(const Vox3D &v, const DevParams &p, float *out, int32
     const int wpb = fit_warps(sc.warps_per_block, per_warp, rle_table_bytes(p.K));
     const size_t smem = rle_table_bytes(p.K) + (size_t)wpb * per_warp;
     long long grid;
-    auto kern = thm5_of(p) ? k_eval_3d<kRay3dThm5> : k_eval_3d<kRay3dOther>;
+    const bool wide = nrays > 0x7fffffffLL;
+    auto kern = thm5_of(p) ? (wide ? k_eval_3d<kRay3dThm5, true> : k_eval_3d<kRay3dThm5, false>)
+                           : (wide ? k_eval_3d<kRay3dOther, true> : k_eval_3d<kRay3dOther, false>);
     cudaError_t e = grid_for(kern, smem, nrays, wpb, sc.blocks_per_sm, grid);
     if (e == cudaSuccess) e = reset_queue(queue, s);
     if (e != cudaSuccess) return e;
@@ -322,8 +325,10 @@ cudaError_t encode_scratch_ptr(int32_t **ptr);
 cudaError_t prepare_rle()
 {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dThm5>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dOther>);
+    cudaError_t e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dThm5, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dOther, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dThm5, true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_3d<kRay3dOther, true>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_eval_rle);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_rle_count);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_rle_write);
