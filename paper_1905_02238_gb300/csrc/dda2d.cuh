@@ -68,14 +68,20 @@ __device__ __forceinline__ int minor_before(const Geo &g, int k)
 
 // Walks intervals k0..k1 from minor crossing i0 = minor_before(k0), writing (WRITE) its cells
 // from index `base`; cnt = cells entered, ties = minor crossings that coincided with a major one
-// (diagonal steps) before the walk ended.
-template <bool WRITE>
+// (diagonal steps) before the walk ended. CHECK: skip writes at indices >= cap (not needed when
+// every index the walk can reach is below cap). The current cell's id advances with its
+// coordinates (by stepM per major step, stepm per minor step) rather than being recomputed.
+template <bool WRITE, bool CHECK = true>
 __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int base, int cap, int *ids, float *l,
                                      int &cnt, int &ties, bool &ended, float &endl, bool &by_range)
 {
     int cM = g.cM0 + g.sM * (k0 + 1);
     int i = i0;
     int cm = g.cm0 + g.sm * i;
+    const int stepM = g.xmaj ? g.sM : g.sM * g.W, stepm = g.xmaj ? g.sm * g.W : g.sm;
+    int id = g.xmaj ? (cm * g.W + cM) : (cM * g.W + cm);
+    int *ip = ids + base;
+    float *lp = l + base;
     cnt = 0;
     ties = 0;
     ended = false;
@@ -83,13 +89,12 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int b
     by_range = false;
 #define FSMI_EMIT(lam_)                                                              \
     do {                                                                             \
-        if (WRITE) {                                                                 \
-            const int pos_ = base + cnt;                                             \
-            if (pos_ < cap) {                                                        \
-                ids[pos_] = g.xmaj ? (cm * g.W + cM) : (cM * g.W + cm);              \
-                l[pos_] = (lam_);                                                    \
-            }                                                                        \
+        if (WRITE && (!CHECK || base + cnt < cap)) {                                 \
+            *ip = id;                                                                \
+            *lp = (lam_);                                                            \
         }                                                                            \
+        ++ip;                                                                        \
+        ++lp;                                                                        \
         ++cnt;                                                                       \
     } while (0)
     // crossings are compared as nm(i) aM against nM(k + 1) am; both products advance by constant
@@ -109,6 +114,7 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int b
         }
         if (minor) {  // no branch inside: the lanes stay together whichever of them cross
             cm += g.sm;
+            id += stepm;
             FSMI_EMIT((float)nmi * g.rm);
             ++i;
             nmi += 65536u;
@@ -122,8 +128,10 @@ __device__ __forceinline__ void walk(const Geo &g, int k0, int k1, int i0, int b
         }
         const bool tie = g.am && pm == pM;
         cM += g.sM;
+        id += stepM;
         if (tie) {
             cm += g.sm;
+            id += stepm;
             ++i;
             nmi += 65536u;
             pm += dm;
@@ -195,7 +203,15 @@ static __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, lon
     int pred = 0;
     if (k0 <= k1) pred = (k1 - k0 + 1) + iend - i0;
     const int pinc = warp_incl_add_int(pred);
-    if (k0 <= k1) walk<true>(g, k0, k1, i0, pinc - pred, cap, ids, l, cnt, ties, ended, endl, rng);
+    // a lane writes at most its predicted count from its offset, so every index stays below the
+    // predicted total: within cap, the writes need no check
+    const bool fits = __shfl_sync(kFull, pinc, 31) <= cap;
+    if (k0 <= k1) {
+        if (fits)
+            walk<true, false>(g, k0, k1, i0, pinc - pred, cap, ids, l, cnt, ties, ended, endl, rng);
+        else
+            walk<true, true>(g, k0, k1, i0, pinc - pred, cap, ids, l, cnt, ties, ended, endl, rng);
+    }
     const unsigned eb = __ballot_sync(kFull, ended);
     const int first = eb ? __ffs(eb) - 1 : 31;
     const float lend = __shfl_sync(kFull, endl, first);
@@ -209,7 +225,7 @@ static __device__ int dda_warp(int W, int H, int ox, int oy, int dx, int dy, lon
         n = __shfl_sync(kFull, inc, 31);
         if (n > cap) return -1;
         __syncwarp();
-        if (lane <= first && k0 <= k1) walk<true>(g, k0, k1, i0, inc - c, cap, ids, l, cnt, ties, ended, endl, rng);
+        if (lane <= first && k0 <= k1) walk<true, false>(g, k0, k1, i0, inc - c, cap, ids, l, cnt, ties, ended, endl, rng);
     } else {
         // every lane before the first that ended walked its whole block without a diagonal step,
         // so its predicted count was exact: n = that lane's offset + its count
