@@ -387,10 +387,10 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
     for (int a = 0; a < 3; ++a) q[a] = o[a] + (2LL * lane + 1) * d[a];
     const float inv_cap = 1.0f / (float)cap;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);  // lanes 0 .. lane
-    for (int base = 0; base < nsamp; base += 32) {
-        const int i = base + lane;
-        bool inb = false;
-        float val = 0.0f;
+    // this lane's sample of the chunk at `base`: whether it lies in the grid, and its voxel value
+    auto fetch = [&](int i, bool &inb, float &val) {
+        inb = false;
+        val = 0.0f;
         if (i < nsamp) {
             const long long px = q[0] >> 31, py = q[1] >> 31, pz = q[2] >> 31;
             inb = (unsigned long long)px < (unsigned long long)X && (unsigned long long)py < (unsigned long long)Y &&
@@ -399,6 +399,16 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) q[a] += 64 * d[a];
+    };
+    // the next chunk's gathers are issued before the current chunk is encoded
+    bool inb_next;
+    float val_next;
+    fetch(lane, inb_next, val_next);
+    for (int base = 0; base < nsamp; base += 32) {
+        const int i = base + lane;
+        const bool inb = inb_next;
+        const float val = val_next;
+        if (__all_sync(kFull, inb)) fetch(i + 32, inb_next, val_next);  // a chunk with a sample outside is the last
         const unsigned m_in = __ballot_sync(kFull, inb);
         const int nvalid = (m_in == kFull) ? 32 : (__ffs(~m_in) - 1);
         const bool valid = lane < nvalid;

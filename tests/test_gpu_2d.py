@@ -100,6 +100,31 @@ def test_trace_lattice_diagonals_bit_exact():
     _trace_compare(W, H, poses, dirs, 9.0)
 
 
+def test_trace_tight_capacity():
+    # capacity exactly the beam's cell count, and one less: along lattice diagonals the lanes'
+    # predicted counts include the diagonal steps, so their total exceeds the capacity and the
+    # traversal writes with its capacity checks; one cell short, the beam reports the overflow (-1)
+    W, H = 64, 48
+    p = synth.pose_2d(0, 0, 0.0)
+    p[0], p[1] = int(30.5 * 65536), int(20.5 * 65536)
+    poses = p[None, :]
+    c = int(round(2 ** 30 / np.sqrt(2.0)))
+    dirs = np.array([[c, c], [-c, c], [2 * int(round(2 ** 30 / np.sqrt(5.0))), int(round(2 ** 30 / np.sqrt(5.0)))],
+                     [2 ** 30, 0]], np.int32)
+    R = 40.0
+    for b in range(dirs.shape[0]):
+        d = oracle.beam_dir_2d(poses[0], dirs[b])
+        rc, rl = oracle.trace_2d(W, H, int(poses[0, 0]), int(poses[0, 1]), int(d[0]), int(d[1]), R, 4096)
+        m = len(rc)
+        cells, l, n = fsmi.trace_2d(W, H, _cuda(poses), _cuda(dirs[b:b + 1]), R, m)
+        n = n.cpu().numpy()
+        assert n[0] == m, (b, n[0], m)
+        np.testing.assert_array_equal(cells.cpu().numpy()[0, :m], rc)
+        np.testing.assert_allclose(l.cpu().numpy()[0, :m + 1], rl, rtol=4e-7, atol=1e-6)
+        _, _, n = fsmi.trace_2d(W, H, _cuda(poses), _cuda(dirs[b:b + 1]), R, m - 1)
+        assert int(n.cpu().numpy()[0]) == -1, b
+
+
 def test_trace_office_map_sampled():
     grid, poses, dirs = synth.config2(n_poses=16, size=512)
     _trace_compare(512, 512, poses, dirs, 256.0)
