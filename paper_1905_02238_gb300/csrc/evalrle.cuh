@@ -392,10 +392,12 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
         inb = false;
         val = 0.0f;
         if (i < nsamp) {
-            const long long px = q[0] >> 31, py = q[1] >> 31, pz = q[2] >> 31;
-            inb = (unsigned long long)px < (unsigned long long)X && (unsigned long long)py < (unsigned long long)Y &&
-                  (unsigned long long)pz < (unsigned long long)Z;
-            if (inb) val = __ldg(vox + ((pz * Y + py) * X + px));
+            // voxel = position >> 31; positions stay far below 2^62, so the low 32 bits of the
+            // shifted value are the voxel when it is in the grid and a value >= the extent (as
+            // unsigned) when it is not, negative positions included
+            const unsigned px = (unsigned)(q[0] >> 31), py = (unsigned)(q[1] >> 31), pz = (unsigned)(q[2] >> 31);
+            inb = px < (unsigned)X && py < (unsigned)Y && pz < (unsigned)Z;
+            if (inb) val = __ldg(vox + ((size_t)(pz * (unsigned)Y + py) * (unsigned)X + px));
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) q[a] += 64 * d[a];
