@@ -154,7 +154,7 @@ def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
 def workload(rank: int, n_poses: int = N_POSES):
     from paper_1905_02238_gb300 import synth
 
-    grid, poses, dirs = synth.config2(n_poses=n_poses, pose_seed=1 + rank)
+    grid, poses, dirs = synth.office_scene(n_poses=n_poses, pose_seed=1 + rank)
     return grid, poses, dirs
 
 
@@ -467,19 +467,19 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
                 "(traversal, gathers, scans), not by either pipe")
     if terms:
         res["exact_fsmi_window_terms"] = terms
-    # config 1 (correctness configuration, launch-latency bound): one pose x 360 beams, R = 64
-    g1, p1, d1 = (torch.from_numpy(x).to(g.device) for x in synth.config1())
+    # the 200x200 random grid (correctness workload, launch-latency bound): one pose x 360 beams, R = 64
+    g1, p1, d1 = (torch.from_numpy(x).to(g.device) for x in synth.random_grid_200())
     o1 = torch.empty((1, 360), dtype=torch.float32, device=g.device)
     prm1 = fsmi.Params(variant=fsmi.EXACT, sigma=1.5, delta_occ=DOCC, delta_emp=DEMP, max_range=64.0)
     ws1 = torch.empty(fsmi.QUEUE_BYTES, dtype=torch.uint8, device=g.device)
     graph1 = fsmi.Graph(lambda: fsmi.eval_2d(g1, p1, d1, prm1, out=o1, ws=ws1))
-    res["config1_exact"] = {"us_per_launch_graph": 1e3 * _time_ms(graph1.replay, reps=200),
+    res["grid200_exact"] = {"us_per_launch_graph": 1e3 * _time_ms(graph1.replay, reps=200),
                             "us_per_call": 1e3 * _time_ms(lambda: fsmi.eval_2d(g1, p1, d1, prm1, out=o1, ws=ws1),
                                                           reps=200),
                             "workload": "200x200 grid, 1 pose x 360 beams, R = 64, sigma = 1.5; per call = "
                                         "through the Python binding (host launch overhead included)"}
     graph1.close()
-    vox, vp, vd = synth.config3()
+    vox, vp, vd = synth.voxel_scene()
     v, vp, vd = (torch.from_numpy(x).to(g.device) for x in (vox, vp, vd))
     nr = vp.shape[0] * vd.shape[0]
     out3 = torch.empty((vp.shape[0], vd.shape[0]), dtype=torch.float32, device=g.device)
@@ -533,7 +533,7 @@ PRESCREEN_MIN_RANGE = 96.0  # shorter beams are cheap to evaluate exactly; the n
 
 
 def surrogate_leg(dev, steps: int = 2500):
-    """Config 4: train the surrogate on 10.3 M beams that exact FSMI labels (7 office maps x 4096
+    """Surrogate prescreen: train the surrogate on 10.3 M beams that exact FSMI labels (7 office maps x 4096
     poses x 360 beams), then select the best 10 of 4096 candidate poses on a held-out map by
     surrogate prescreen + exact rerank of the top 64, against exact FSMI of every beam. Both
     selections run as CUDA-graph replays. Returns (result, network)."""
@@ -555,7 +555,7 @@ def surrogate_leg(dev, steps: int = 2500):
     losses = net.train(maps, d, steps=steps, batch=4096, lr=2e-3, log_every=steps // 4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    grid, poses, _ = synth.config2(n_poses=4096, seed=200, pose_seed=201)
+    grid, poses, _ = synth.office_scene(n_poses=4096, seed=200, pose_seed=201)
     g, p = torch.from_numpy(grid).to(dev), torch.from_numpy(poses).to(dev)
     ex = sg.ExactAll(g, p, d, prm)
     pre = sg.Prescreen(net, g, p, d, prm, k=64)
@@ -620,7 +620,7 @@ def surrogate_leg(dev, steps: int = 2500):
 
 def surrogate_stream_leg(dev, net, k: int = 64, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512),
                          len_range=(8, 512, 8, 256)):
-    """Config 5 with the surrogate: each 2D set of the stream whose range the network covers
+    """The mixed candidate-set stream with the surrogate: each 2D set of the stream whose range the network covers
     (R <= 256) and that has more than k poses selects its best 10 poses by surrogate prescreen
     (profiles cut at the set's range, which the network reads as the map ending there; it is
     trained at R = 256 only) + exact rerank of the top k, against exact FSMI of all its beams, and
@@ -683,7 +683,7 @@ def surrogate_stream_leg(dev, net, k: int = 64, nsets: int = 32, seed: int = 5, 
 
 
 def stream_sets(nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512), len_range=(8, 512, 8, 256)):
-    """The config-5 stream: a 4096x4096 office map with 16384 free-cell poses and 360 beams, two
+    """The mixed candidate-set stream: a 4096x4096 office map with 16384 free-cell poses and 360 beams, two
     256x256x64 voxel submaps with 512 poses each and 64x64 rays, and nsets candidate sets: 3 in 4
     are 2D (pose_range[0]-[1] poses, log-uniform; range len_range[0]-[1] cells), the rest 3D
     (pose_range[2]-[3] poses; len_range[2]-[3] virtual cells), as fsmi.make_sets tuples."""
@@ -713,7 +713,7 @@ def stream_sets(nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512), 
 
 
 def mixed_leg(dev, nsets: int = 32, seed: int = 5, pose_range=(16, 8192, 16, 512), len_range=(8, 512, 8, 256)):
-    """Config 5: a stream of candidate sets on a 4096x4096 office map and two 256x256x64 voxel
+    """Mixed candidate sets: a stream of candidate sets on a 4096x4096 office map and two 256x256x64 voxel
     submaps, evaluated exactly (2D FSMI, sigma 2; 3D FSMI-RLE, sigma 2, run cap 64) in one
     persistent launch (fsmi_eval_mixed), against the same sets launched one after the other.
     Sets (default): 3 in 4 are 2D (16-8192 poses, log-uniform; 360 beams; range 8-512 cells), the

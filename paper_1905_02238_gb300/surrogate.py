@@ -50,13 +50,13 @@ class TrainingMap:
 
 def label_maps(n_maps: int, poses_per_map: int, dirs, prm: fsmi.Params, seed: int = 100, size: int = 2048,
                ranges=None):
-    """Config-2 style maps (office generator, seeds seed, seed+1, ...) with every beam of every pose
+    """Office maps as in the 2048x2048 benchmark (office generator, seeds seed, seed+1, ...) with every beam of every pose
     labelled by exact FSMI on the GPU, at prm.max_range or, with `ranges`, map k at ranges[k % len]
     (ranges up to 256, the samples of a profile)."""
     out = []
     d = dirs if isinstance(dirs, torch.Tensor) else torch.from_numpy(dirs).cuda()
     for k in range(n_maps):
-        grid, poses, _ = synth.config2(n_poses=poses_per_map, size=size, seed=seed + k, pose_seed=seed + 1000 + k)
+        grid, poses, _ = synth.office_scene(n_poses=poses_per_map, size=size, seed=seed + k, pose_seed=seed + 1000 + k)
         g = torch.from_numpy(grid).cuda()
         p = torch.from_numpy(poses).cuda()
         r = float(ranges[k % len(ranges)]) if ranges else float(prm.max_range)
@@ -254,7 +254,7 @@ def _main():
     from . import build
 
     build.build()
-    grid, poses, _ = synth.config2(n_poses=args.poses, seed=200, pose_seed=201)
+    grid, poses, _ = synth.office_scene(n_poses=args.poses, seed=200, pose_seed=201)
     g, p = torch.from_numpy(grid).cuda(), torch.from_numpy(poses).cuda()
     d = torch.from_numpy(synth.beam_dirs_2d(args.beams)).cuda()
     net = Surrogate(seed=0, scale=0.01, shift=0.06)

@@ -11,12 +11,12 @@ Fixed-point conventions shared by every input:
 
 Workloads (sizes from the benchmark configurations; the paper's own timing experiments use random
 occupancies, Section 5.1 and Section 5.4, and private robot logs that are not reproduced here):
-  * ``config1``: 200x200 grid, o ~ U(0.05, 0.95) iid, one pose at the centre of cell (100, 100),
+  * ``random_grid_200``: 200x200 grid, o ~ U(0.05, 0.95) iid, one pose at the centre of cell (100, 100),
     360 beams at 1 degree, range 64 cells.
-  * ``config2``: 2048x2048 grid, background 0.1, 400 rectangles (sides 8..64) at 0.9, then
+  * ``office_scene``: 2048x2048 grid, background 0.1, 400 rectangles (sides 8..64) at 0.9, then
     unknown (0.5) rectangles (sides 64..512) painted until they cover >= 40%; poses at centres of
     free (0.1) cells, yaw 0, 360 beams, range 256.
-  * ``config3``: 512x512x128 voxels, background 0.1, 200 boxes (sides 8..64) at 0.9, half-space
+  * ``voxel_scene``: 512x512x128 voxels, background 0.1, 200 boxes (sides 8..64) at 0.9, half-space
     x >= 256 at 0.5, then 10% of voxels replaced by U(0.3, 0.7); 64 poses in free voxels with
     z in [32, 96), random yaw, pitch 0; 128x128 pinhole rays over a 90x90 degree field of view;
     range 384 virtual cells.
@@ -52,7 +52,7 @@ def random_dirs_2d(n: int, rng: np.random.Generator) -> np.ndarray:
     return np.stack([q30(np.cos(a)), q30(np.sin(a))], axis=1)
 
 
-def config1(seed: int = 0):
+def random_grid_200(seed: int = 0):
     """Returns (grid float32 [200, 200], poses int32 [1, 4], dirs int32 [360, 2])."""
     rng = np.random.default_rng(seed)
     grid = rng.uniform(0.05, 0.95, size=(200, 200)).astype(np.float32)
@@ -116,7 +116,7 @@ def frontier_poses_2d(grid: np.ndarray, n: int, seed: int = 1, rmin: float = 2.0
     return poses
 
 
-def config2(n_poses: int = 1024, size: int = 2048, seed: int = 0, pose_seed: int = 1):
+def office_scene(n_poses: int = 1024, size: int = 2048, seed: int = 0, pose_seed: int = 1):
     """Returns (grid float32 [size, size], poses int32 [P, 4], dirs int32 [360, 2])."""
     grid = office_grid(size, 400 if size >= 1024 else max(8, 400 * size * size // (2048 * 2048)), 0.40, seed)
     poses = free_cell_poses_2d(grid, n_poses, pose_seed)
@@ -182,7 +182,7 @@ def free_voxel_poses(vox: np.ndarray, n: int, seed: int = 3, zlo: int = 32, zhi:
                      for k, i in enumerate(idx)])
 
 
-def config3(n_poses: int = 64, X: int = 512, Y: int = 512, Z: int = 128, rays: int = 128):
+def voxel_scene(n_poses: int = 64, X: int = 512, Y: int = 512, Z: int = 128, rays: int = 128):
     """Returns (vox float32 [Z, Y, X], poses int32 [P, 12], dirs int32 [rays*rays, 3])."""
     scale = (X * Y * Z) / (512 * 512 * 128)
     vox = voxel_world(X, Y, Z, n_boxes=max(4, int(round(200 * scale))))

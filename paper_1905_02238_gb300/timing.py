@@ -29,7 +29,7 @@ def main() -> None:
     var = {"exact": dict(variant=fsmi.EXACT), "approx": dict(variant=fsmi.APPROX),
            "approx_band": dict(variant=fsmi.APPROX, approx_reading=1), "uniform": dict(variant=fsmi.UNIFORM)}[args.variant]
     if args.path == "2d":
-        grid, poses, dirs = synth.config2(n_poses=args.poses or 1024)
+        grid, poses, dirs = synth.office_scene(n_poses=args.poses or 1024)
         g, p, d = (torch.from_numpy(x).to(dev) for x in (grid, poses, dirs))
         prm = fsmi.Params(sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0, trunc_delta=6, uniform_h=4, **var)
         out = torch.empty((p.shape[0], d.shape[0]), dtype=torch.float32, device=dev)
@@ -39,7 +39,7 @@ def main() -> None:
             fsmi.eval_2d(g, p, d, prm, out=out, ws=ws)
         what = f"eval_2d {args.variant} {p.shape[0]} x {d.shape[0]} beams"
     elif args.path == "3d":
-        vox, vp, vd = synth.config3(n_poses=args.poses or 64)
+        vox, vp, vd = synth.voxel_scene(n_poses=args.poses or 64)
         v, p, d = (torch.from_numpy(x).to(dev) for x in (vox, vp, vd))
         prm = fsmi.Params(sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=384.0, run_cap=64, trunc_delta=6,
                           uniform_h=4, **var)
@@ -52,7 +52,7 @@ def main() -> None:
     else:
         from . import surrogate as sg
 
-        grid, poses, _ = synth.config2(n_poses=args.poses or 4096, seed=200, pose_seed=201)
+        grid, poses, _ = synth.office_scene(n_poses=args.poses or 4096, seed=200, pose_seed=201)
         g, p = torch.from_numpy(grid).to(dev), torch.from_numpy(poses).to(dev)
         d = torch.from_numpy(synth.beam_dirs_2d(360)).to(dev)
         net = sg.Surrogate(seed=0, scale=0.01, shift=0.06)

@@ -58,8 +58,8 @@ def _trace_compare(W, H, poses, dirs, R):
         np.testing.assert_allclose(l[i, :n[i] + 1], rl, rtol=4e-7, atol=1e-6)
 
 
-def test_trace_config1_bit_exact():
-    grid, poses, dirs = synth.config1()
+def test_trace_random_grid_bit_exact():
+    grid, poses, dirs = synth.random_grid_200()
     _trace_compare(200, 200, poses, dirs, 64.0)
 
 
@@ -126,7 +126,7 @@ def test_trace_tight_capacity():
 
 
 def test_trace_office_map_sampled():
-    grid, poses, dirs = synth.config2(n_poses=16, size=512)
+    grid, poses, dirs = synth.office_scene(n_poses=16, size=512)
     _trace_compare(512, 512, poses, dirs, 256.0)
 
 
@@ -181,17 +181,17 @@ def test_eval_beams_edge_cases():
 # ---- full 2D path -----------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("e0", [0, 1])
-def test_eval_2d_config1(e0):
-    grid, poses, dirs = synth.config1()
+def test_eval_2d_random_grid(e0):
+    grid, poses, dirs = synth.random_grid_200()
     for kw in _variants():
         gp, op = _prms(1.5, 64.0, e0, **kw)
         got = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy()
         ref = oracle.eval_2d(grid, poses, dirs, op)
-        assert_mi_close(got, ref, f"config1 {kw}")
+        assert_mi_close(got, ref, f"random grid {kw}")
 
 
 def test_eval_2d_office_midsize():
-    grid, poses, dirs = synth.config2(n_poses=12, size=512)
+    grid, poses, dirs = synth.office_scene(n_poses=12, size=512)
     for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
         gp, op = _prms(2.0, 256.0, 0, **kw)
         got = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy()
@@ -199,17 +199,17 @@ def test_eval_2d_office_midsize():
         assert_mi_close(got, ref, f"office512 {kw}")
 
 
-def test_eval_2d_config2_full_size_sampled():
+def test_eval_2d_office_full_size_sampled():
     # the benchmark's launch: 2048^2 map, 1024 poses x 360 beams, R = 256, sigma = 2; the oracle
     # checks every beam of four poses spread over the batch
-    grid, poses, dirs = synth.config2()
+    grid, poses, dirs = synth.office_scene()
     rows = [0, 341, 682, 1023]
     for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
         gp, op = _prms(2.0, 256.0, 0, **kw)
         got = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu().numpy()
         assert got.shape == (1024, 360) and np.all(np.isfinite(got))
         ref = oracle.eval_2d(grid, poses[rows], dirs, op)
-        assert_mi_close(got[rows], ref, f"config2 {kw}")
+        assert_mi_close(got[rows], ref, f"office {kw}")
     assert fsmi.device_status() == 0
 
 
@@ -226,7 +226,7 @@ def test_eval_2d_long_beams():
 
 
 def test_eval_2d_host_buffers_match_device():
-    grid, poses, dirs = synth.config1()
+    grid, poses, dirs = synth.random_grid_200()
     gp, _ = _prms(1.5, 64.0)
     dev = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp).cpu()
     host = fsmi.eval_2d(torch.from_numpy(grid).pin_memory(), torch.from_numpy(poses).pin_memory(),
@@ -236,7 +236,7 @@ def test_eval_2d_host_buffers_match_device():
 
 
 def test_invalid_arguments_launch_nothing():
-    grid, poses, dirs = synth.config1()
+    grid, poses, dirs = synth.random_grid_200()
     out = torch.full((1, 360), 7.0, device="cuda")
     for bad in (dict(sigma=0.0), dict(sigma=float("nan")), dict(delta_occ=-1.0), dict(max_range=2000.0),
                 dict(variant=7), dict(e0_mode=3)):
@@ -305,8 +305,8 @@ WINDOW_CASES = ((64.0, 1.5, 0), (256.0, 2.0, 24), (256.0, 0.4, 8), (256.0, 12.0,
 
 def _window_case(R, sigma, n_poses):
     if n_poses == 0:
-        return synth.config1()
-    return synth.config2(n_poses=n_poses, size=512)
+        return synth.random_grid_200()
+    return synth.office_scene(n_poses=n_poses, size=512)
 
 
 @pytest.mark.parametrize("e0", [0, 1])
@@ -378,7 +378,7 @@ def test_zero_length_cells():
 
 def test_map_gains_workspace_is_bit_identical():
     # per-map-cell gains (workspace) against per-visit gains (no workspace), all three variants
-    grid, poses, dirs = synth.config2(n_poses=64, size=1024)
+    grid, poses, dirs = synth.office_scene(n_poses=64, size=1024)
     for kw in (dict(variant=fsmi.EXACT), dict(variant=fsmi.APPROX, trunc_delta=6), dict(variant=fsmi.UNIFORM, uniform_h=4)):
         gp, _ = _prms(2.0, 256.0, 0, **kw)
         a = fsmi.eval_2d(_cuda(grid), _cuda(poses), _cuda(dirs), gp)

@@ -112,8 +112,8 @@ def test_encode_offsets_saturate_instead_of_wrapping_past_int32():
     np.testing.assert_array_equal(off.cpu().numpy().astype(np.int64), want)
 
 
-def test_encode_full_size_config3_sampled():
-    vox, poses, dirs = synth.config3()
+def test_encode_full_size_voxel_scene_sampled():
+    vox, poses, dirs = synth.voxel_scene()
     gp, _ = _prms()
     rng = np.random.default_rng(50)
     sel_p = rng.choice(64, 4, replace=False)
@@ -195,9 +195,9 @@ def test_eval_3d_small_world_all_variants():
         assert_mi_close(got.cpu().numpy(), ref, f"3d {kw}")
 
 
-def test_eval_3d_config3_full_size_sampled():
+def test_eval_3d_voxel_scene_full_size_sampled():
     # the benchmark's launch: 512x512x128 voxels, 64 poses x 128x128 rays, 384 virtual cells
-    vox, poses, dirs = synth.config3()
+    vox, poses, dirs = synth.voxel_scene()
     rng = np.random.default_rng(51)
     sel_p = rng.choice(64, 3, replace=False)
     sel_r = np.sort(rng.choice(dirs.shape[0], 96, replace=False))
@@ -209,7 +209,7 @@ def test_eval_3d_config3_full_size_sampled():
         assert np.all(np.isfinite(got))
         ref, nr_ref = oracle.eval_3d(vox, poses[sel_p], dirs[sel_r], op)
         np.testing.assert_array_equal(nr[np.ix_(sel_p, sel_r)], nr_ref)
-        assert_mi_close(got[np.ix_(sel_p, sel_r)], ref, f"config3 {kw}")
+        assert_mi_close(got[np.ix_(sel_p, sel_r)], ref, f"voxel scene {kw}")
     assert fsmi.device_status() == 0
 
 

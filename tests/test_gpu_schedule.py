@@ -238,10 +238,10 @@ def test_graph_replay_of_sets_and_3d():
 
 
 def test_benchmark_launch_configuration_against_oracle():
-    # exactly what the benchmark times: config 2 at full size with the per-cell gains workspace,
-    # the autotuned 2D schedule and one CUDA-graph replay per step; config 3 likewise for the 3D
+    # exactly what the benchmark times: the 2048x2048 office batch at full size with the per-cell gains workspace,
+    # the autotuned 2D schedule and one CUDA-graph replay per step; the 512x512x128 voxel batch likewise for the 3D
     # batch. The replayed results equal a plain call bit for bit and match the oracle on samples.
-    grid, poses, dirs = synth.config2()
+    grid, poses, dirs = synth.office_scene()
     g, p, d = _cuda(grid), _cuda(poses), _cuda(dirs)
     gp = fsmi.Params(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0)
     op = oracle.Params(variant=oracle.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0)
@@ -259,9 +259,9 @@ def test_benchmark_launch_configuration_against_oracle():
         plain = fsmi.eval_2d(g, p, d, gp)
         np.testing.assert_array_equal(_bits(out), _bits(plain))
         rows = [5, 517, 1000]
-        assert_mi_close(out.cpu().numpy()[rows], oracle.eval_2d(grid, poses[rows], dirs, op), "config2 graph")
+        assert_mi_close(out.cpu().numpy()[rows], oracle.eval_2d(grid, poses[rows], dirs, op), "office graph")
 
-        vox, vposes, vdirs = synth.config3()
+        vox, vposes, vdirs = synth.voxel_scene()
         v, vp, vd = _cuda(vox), _cuda(vposes), _cuda(vdirs)
         gp3 = fsmi.Params(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=384.0, run_cap=64)
         op3 = oracle.Params(variant=oracle.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=384.0, run_cap=64)
@@ -275,7 +275,7 @@ def test_benchmark_launch_configuration_against_oracle():
         np.testing.assert_array_equal(_bits(out3), _bits(fsmi.eval_3d(v, vp, vd, gp3)))
         sel_r = np.arange(0, vd.shape[0], 257)
         ref3, _ = oracle.eval_3d(vox, vposes[[3, 40]], vdirs[sel_r], op3)
-        assert_mi_close(out3.cpu().numpy()[np.ix_([3, 40], sel_r)], ref3, "config3 graph")
+        assert_mi_close(out3.cpu().numpy()[np.ix_([3, 40], sel_r)], ref3, "voxel scene graph")
     finally:
         fsmi.set_schedule(K2, saved2)
         fsmi.set_schedule(KR, saved3)

@@ -253,7 +253,7 @@ def test_trained_surrogate_prescreen_beats_exact_all():
     lab = torch.cat([m.labels for m in maps])
     net = sg.Surrogate(seed=0, scale=float(lab.std()), shift=float(lab.mean()))
     net.train(maps, d, steps=2500, batch=4096, lr=2e-3)
-    grid, poses, _ = synth.config2(n_poses=4096, seed=200, pose_seed=201)
+    grid, poses, _ = synth.office_scene(n_poses=4096, seed=200, pose_seed=201)
     g, p = _cuda(grid), _cuda(poses)
     ex = sg.ExactAll(g, p, d, prm)
     ex.run()

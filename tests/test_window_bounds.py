@@ -109,7 +109,7 @@ def replay(sl, e0, cut, pad, cs):
 @pytest.mark.parametrize("e0", [0, 1])
 def test_window_on_traversed_beams(sigma, e0):
     cut, full, pad = _consts()
-    grid, poses, dirs = synth.config1()
+    grid, poses, dirs = synth.random_grid_200()
     H, W = grid.shape
     cs = np.sqrt(np.log2(np.e)) / (sigma * np.sqrt(2.0))
     for b in range(0, dirs.shape[0], 23):

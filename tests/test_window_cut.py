@@ -46,7 +46,7 @@ def test_cut_constants():
 @pytest.mark.parametrize("sigma", [0.7, 2.0, 20.0])
 def test_skipped_terms_on_traversed_beams(sigma):
     cut, _ = _cuts()
-    grid, poses, dirs = synth.config1()
+    grid, poses, dirs = synth.random_grid_200()
     H, W = grid.shape
     cs = SQ / (sigma * np.sqrt(2.0))
     worst = 0.0
