@@ -43,10 +43,12 @@ OPS_PER_TERM = 10  # FP32 FMA-pipe operations per boundary tail term (csrc/gauss
 #                    square, 1 + p|d|, 4 Horner FMAs, two products, accumulate
 TAIL_CUT = 4.81  # scaled half-width of the exact kernel's default window (csrc/eval2d.cuh)
 
-# DRAM bytes (read + write) per launch of the exact 2D kernel on the benchmark workload, from an
-# ncu capture of one full-size launch (dram__bytes_read.sum + dram__bytes_write.sum), valid only
-# for the kernel sources whose hash is recorded with it; reported as null once those sources change.
-TRAFFIC = {"sources_sha1": "d04b34a3db90ae157f6964bfca6621c5e603dcaa", "bytes_per_launch": 111.34e6}
+# DRAM bytes (read + write) per launch of the 2D kernel on the benchmark workload (exact; the
+# Approx and Uniform legs by name), from an ncu capture of one full-size launch each
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources whose hash is
+# recorded with them; reported as null once those sources change.
+TRAFFIC = {"sources_sha1": "d04b34a3db90ae157f6964bfca6621c5e603dcaa", "bytes_per_launch": 111.34e6,
+           "approx_fsmi_delta6": 82.83e6, "uniform_fsmi_h4": 83.00e6}
 KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb300/csrc/eval2d.cuh",
                   "paper_1905_02238_gb300/csrc/dda2d.cuh", "paper_1905_02238_gb300/csrc/gauss_tail.cuh",
                   "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]
@@ -443,6 +445,7 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
                              ("approx_fsmi_delta6", dict(variant=fsmi.APPROX, trunc_delta=6), band),
                              ("uniform_fsmi_h4", dict(variant=fsmi.UNIFORM, uniform_h=4), None)):
         prm = fsmi.Params(sigma=SIGMA, delta_occ=DOCC, delta_emp=DEMP, max_range=R_MAX, **kw)
+        traffic = TRAFFIC.get(name) if TRAFFIC["sources_sha1"] == kernel_sources_sha1() else None
         ms = _time_ms(lambda: fsmi.eval_2d(g, p, d, prm, out=out, ws=gains_ws))
         res[name] = {"beams_per_s": nb / (ms * 1e-3), "ms": ms}
         if cells:
@@ -456,7 +459,8 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
                     "alu", (nterms + cells) / (ms * 1e-3) / 1e12, peak_terms / 1e12, "T tail-terms/s (SFU)",
                     "k_eval_2d<APPROX,map>",
                     f"{nterms + cells:.4g} boundary tails per launch (sum over first-hit cells j of the band "
-                    f"[j - 6, j + 6] clipped to the beam, plus one: its boundaries), one ex2 and one rcp each")
+                    f"[j - 6, j + 6] clipped to the beam, plus one: its boundaries), one ex2 and one rcp each",
+                    traffic=traffic)
         if name == "uniform_fsmi_h4" and cells and l2_gbs:
             # Algorithm 4 after the per-map-cell gains: per visited cell one 16-byte gather of
             # (o, f_occ, f_emp) from the L2-resident gains array, prefix sums and O(1) arithmetic
@@ -464,7 +468,7 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
                 "l2", 16 * cells / (ms * 1e-3) / 1e9, l2_gbs, "GB/s", "k_eval_2d<UNIFORM,map>",
                 f"{cells:.4g} visited cells per launch x 16 B gathered (per-map-cell gains, L2-resident) "
                 "against the measured L2 read bandwidth (pipe_rates); the kernel is bound by issue "
-                "(traversal, gathers, scans), not by either pipe")
+                "(traversal, gathers, scans), not by either pipe", traffic=traffic)
     if terms:
         res["exact_fsmi_window_terms"] = terms
     # the 200x200 random grid (correctness workload, launch-latency bound): one pose x 360 beams, R = 64
@@ -512,14 +516,15 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
         l2_bytes = 4 * wc["samples"] + 4 * nr
         if l2_gbs:
             fr_l2 = l2_bytes / sec / 1e9 / l2_gbs
+            # the kernel's DRAM bytes per launch (ncu), whichever roofline binds
+            traffic = TRAFFIC_3D.get(name) if TRAFFIC_3D.get("sources_sha1") == kernel_sources_sha1(
+                KERNEL_SOURCES_3D) else None
             rl2 = roofline("l2", l2_bytes / sec / 1e9, l2_gbs, "GB/s", f"k_eval_3d ({name})",
                            f"{wc['samples']:.4g} virtual-cell samples x 4 B gathered + 4 B out per ray, against the "
-                           "measured L2 read bandwidth (the 134 MB volume is mostly L2-served)",
-                           traffic=TRAFFIC_3D.get(name) if TRAFFIC_3D.get("sources_sha1") == kernel_sources_sha1(
-                               KERNEL_SOURCES_3D) else None)
+                           "measured L2 read bandwidth (the 134 MB volume is mostly L2-served)", traffic=traffic)
             rfma = roofline("alu", wc["fp32_ops"] / sec / 1e12, fma_peak / 1e12, "T FP32 ops/s", f"k_eval_3d ({name})",
                             f"{wc['cell_cells']:.4g} cells of cell-form rays x {2 * K + 2} FMAs (banded convolution, "
-                            f"K = {K}) + {wc['pair_terms']:.4g} run-pair A/B terms x 6 FP32 ops")
+                            f"K = {K}) + {wc['pair_terms']:.4g} run-pair A/B terms x 6 FP32 ops", traffic=traffic)
             res[name]["roofline"] = rl2 if fr_l2 >= fr_fma else rfma
             res[name]["roofline_other"] = rfma if fr_l2 >= fr_fma else rl2
     fsmi.set_schedule(fsmi.KIND_RLE, saved)
