@@ -20,6 +20,8 @@
 #include <cudaTypedefs.h>
 #include <float.h>
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "../../include/fsmi.h"
@@ -290,24 +292,175 @@ __global__ void k_dz4(const float *__restrict__ z4, const float *__restrict__ dp
     }
 }
 
-// column sums over the batch (one block per column, fixed order): out[j] = sum_r f(r, j)
-template <class F>
-__global__ void __launch_bounds__(256) k_colsum(int R, int C, F f, float *out)
+// ---- reductions over the batch rows, in a fixed order -------------------------------------------
+//
+// Sums over the R rows of a batch (bias gradients, conv weight gradients) run in two passes: block
+// b adds rows [b * rows, (b + 1) * rows) into part[b][...], then one thread per output adds the
+// blocks' partials in block order. The row split depends only on R, so a step's gradients are the
+// same floats on every run (and every GPU).
+constexpr int kRedMinRows = 512;   // rows per block, at least
+constexpr int kRedMaxBlocks = 2048;  // blocks per reduction, at most (bounds the partials)
+
+int red_rows(long long R)
 {
-    __shared__ float sh[8];
-    for (int j = blockIdx.x; j < C; j += gridDim.x) {
-        float a = 0.0f;
-        for (int r = threadIdx.x; r < R; r += blockDim.x) a += f(r, j);
-        a = warp_sum(a);
-        if (lane_id() == 0) sh[threadIdx.x >> 5] = a;
+    const long long per = (R + kRedMaxBlocks - 1) / kRedMaxBlocks;
+    return (int)std::max<long long>(kRedMinRows, (per + 31) / 32 * 32);
+}
+
+// part[b][c] = sum over the block's rows r of f(r, c), for C columns (C divides 256): the block's
+// 256 / C row lanes take every (256 / C)-th row, then their sums are added in lane order. A warp
+// reads consecutive columns of one row.
+template <class F>
+__global__ void __launch_bounds__(256) k_colsum_part(int R, int C, int rows, F f, float *__restrict__ part)
+{
+    __shared__ float sh[256];
+    const int rl = 256 / C;
+    const int c = threadIdx.x % C, rsub = threadIdx.x / C;
+    const int r0 = blockIdx.x * rows, r1 = min(R, r0 + rows);
+    float a = 0.0f;
+    if (rsub < rl)
+        for (int r = r0 + rsub; r < r1; r += rl) a += f(r, c);
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.0f;
+        for (int k = 0; k < rl; ++k) t += sh[k * C + threadIdx.x];
+        part[(size_t)blockIdx.x * C + threadIdx.x] = t;
+    }
+}
+
+// out[o] = sum over blocks b of part[b][o], in a fixed order: a block takes 32 outputs (one per lane),
+// its 8 warps the 8 contiguous eighths of the blocks, and the eighths' sums are added in order.
+__global__ void __launch_bounds__(256) k_part_final(int nblk, int O, const float *__restrict__ part,
+                                                    float *__restrict__ out)
+{
+    __shared__ float sh[8][32];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + lane;
+    const int b0 = (int)((long long)nblk * w / 8), b1 = (int)((long long)nblk * (w + 1) / 8);
+    float t = 0.0f;
+    if (o < O) {
+#pragma unroll 8
+        for (int b = b0; b < b1; ++b) t += part[(size_t)b * O + o];
+    }
+    sh[w][lane] = t;
+    __syncthreads();
+    if (w == 0 && o < O) {
+        float u = 0.0f;
+        for (int k = 0; k < 8; ++k) u += sh[k][lane];
+        out[o] = u;
+    }
+}
+
+// Conv weight gradient of a layer with CIN input channels, Lin input and Lout = Lin / 2 output
+// positions: gW[c][k * CIN + ci] = sum over rows r = (n, t) of dz[r][c] in[n][2t + k - 1][ci], with
+// `in` the layer input (relu(z) of the previous layer, or the profile x for the first). A block takes
+// `rows` consecutive rows in tiles of kWgTile (Lout is a multiple of kWgTile, so a tile lies in one
+// beam n, at positions t0 .. t0 + kWgTile - 1) and stages the tile's dz rows and the input positions
+// 2 t0 - 1 .. 2 t0 + 2 kWgTile - 1 that its im2col rows read: row i of the tile's im2col is then the
+// 3 CIN consecutive floats from offset 2 CIN i. Each thread adds its outputs over the block's rows in
+// row order into part[b][...] (k_part_final adds the blocks). CIN = 32: a thread holds 4 output
+// channels x 3 taps (one float4 of dz and three input values per row); CIN = 2: one output.
+constexpr int kWgTile = 32;
+
+template <int CIN>
+__global__ void __launch_bounds__(256) k_wgrad_part(int R, int rows, int Lin, const float *__restrict__ dz,
+                                                    const float *__restrict__ z, const __nv_bfloat162 *__restrict__ x,
+                                                    float *__restrict__ part)
+{
+    constexpr int kNKK = kK * CIN, kO = kCh * kNKK, kPos = 2 * kWgTile + 1;
+    __shared__ __align__(16) float sdz[kWgTile * kCh];
+    __shared__ __align__(16) float sin_[kPos * CIN];
+    const int Lout = Lin >> 1;
+    const int r0 = blockIdx.x * rows, r1 = min(R, r0 + rows);
+    const int tid = threadIdx.x;
+    float acc[4][3] = {};
+    for (int rt = r0; rt < r1; rt += kWgTile) {
+        const int n = rt / Lout, t0 = rt - n * Lout;
+        for (int e = tid; e < kWgTile * kCh / 4; e += 256)
+            reinterpret_cast<float4 *>(sdz)[e] = reinterpret_cast<const float4 *>(dz + (long long)rt * kCh)[e];
+        if (CIN == kCh) {
+            for (int e = tid; e < kPos * kCh / 4; e += 256) {
+                const int p = e / (kCh / 4), q = e % (kCh / 4);
+                const int sidx = 2 * t0 - 1 + p;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sidx >= 0 && sidx < Lin) {
+                    v = reinterpret_cast<const float4 *>(z + ((long long)n * Lin + sidx) * kCh)[q];
+                    v = make_float4(relu(v.x), relu(v.y), relu(v.z), relu(v.w));
+                }
+                reinterpret_cast<float4 *>(sin_)[e] = v;
+            }
+        } else {
+            for (int p = tid; p < kPos; p += 256) {
+                const int sidx = 2 * t0 - 1 + p;
+                float lo = 0.0f, hi = 0.0f;
+                if (sidx >= 0 && sidx < Lin) {
+                    const __nv_bfloat162 v = x[(long long)n * Lin + sidx];
+                    lo = __low2float(v);
+                    hi = __high2float(v);
+                }
+                sin_[2 * p] = lo;
+                sin_[2 * p + 1] = hi;
+            }
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float s = 0.0f;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-            out[j] = s;
+        if (CIN == kCh) {
+            const int cg = tid >> 5, kg = tid & 31;
+            for (int i = 0; i < kWgTile; ++i) {
+                const float4 d = reinterpret_cast<const float4 *>(sdz + i * kCh)[cg];
+                const float *a = sin_ + 2 * CIN * i + kg;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float v = a[32 * j];
+                    acc[0][j] = fmaf(d.x, v, acc[0][j]);
+                    acc[1][j] = fmaf(d.y, v, acc[1][j]);
+                    acc[2][j] = fmaf(d.z, v, acc[2][j]);
+                    acc[3][j] = fmaf(d.w, v, acc[3][j]);
+                }
+            }
+        } else if (tid < kO) {
+            const int c = tid / kNKK, kk = tid % kNKK;
+            for (int i = 0; i < kWgTile; ++i) acc[0][0] = fmaf(sdz[i * kCh + c], sin_[2 * CIN * i + kk], acc[0][0]);
         }
         __syncthreads();
     }
+    float *pb = part + (size_t)blockIdx.x * kO;
+    if (CIN == kCh) {
+        const int cg = tid >> 5, kg = tid & 31;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) pb[(4 * cg + a) * kNKK + 32 * j + kg] = acc[a][j];
+    } else if (tid < kO) {
+        pb[tid] = acc[0][0];
+    }
+}
+
+// out[c] = sum_r f(r, c) for C columns (C divides 256), in a fixed order (k_colsum_part, k_part_final)
+template <class F>
+cudaError_t colsum(int R, int C, F f, float *out, float *part, cudaStream_t s)
+{
+    const int rows = red_rows(R), nblk = (R + rows - 1) / rows;
+    k_colsum_part<<<nblk, 256, 0, s>>>(R, C, rows, f, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_part_final<<<(C + 31) / 32, 256, 0, s>>>(nblk, C, part, out);
+    return cudaGetLastError();
+}
+
+// out[c * 3 CIN + k * CIN + ci] = sum over rows of dz[r][c] in[n][2t + k - 1][ci] (R = N Lout rows),
+// in a fixed order (k_wgrad_part, k_part_final)
+template <int CIN>
+cudaError_t wgrad(int R, int Lin, const float *dz, const float *z, const __nv_bfloat162 *x, float *out, float *part,
+                  cudaStream_t s)
+{
+    const int rows = red_rows(R), nblk = (R + rows - 1) / rows;
+    k_wgrad_part<CIN><<<nblk, 256, 0, s>>>(R, rows, Lin, dz, z, x, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int O = kCh * kK * CIN;
+    k_part_final<<<(O + 31) / 32, 256, 0, s>>>(nblk, O, part, out);
+    return cudaGetLastError();
 }
 
 struct Store {
@@ -339,16 +492,6 @@ struct WRow {  // B(k, n) = W[k][n] (BF16 row-major [K][ld])
     const bf16 *w;
     int ld;
     __device__ float operator()(int k, int n) const { return bf(w, (long long)k * ld + n); }
-};
-// conv weight gradient: gW[c][kk] = sum_{r = (n, t)} dz[r][c] * im2col(in)[r][kk]
-struct DzT {  // A(c, r) = dz[r][c]
-    const float *dz;
-    __device__ float operator()(int c, int r) const { return dz[(long long)r * kCh + c]; }
-};
-template <class FA>
-struct Im2colT {  // B(r, kk) = im2col(in)[r][kk]
-    FA a;
-    __device__ float operator()(int r, int kk) const { return a(r, kk); }
 };
 // conv data gradient: da[n][s][ci] = sum_{k, c} dz[n][t][c] W[c][k][ci], t = (s + 1 - k) / 2
 struct DzGather {  // A(m = n * Lin + s, kk = k * 32 + c)
@@ -949,8 +1092,9 @@ size_t surrogate_train_floats(int N)
     const size_t n = (size_t)N;
     const size_t z = n * (128 + 64 + 32) * kCh + n * kHid;  // z1..z4
     const size_t g = n * 128 * kCh;                          // g1, g2: the largest gradient
-    const size_t part = (size_t)64 * kHid * kFlat;           // split-K partials (up to 64 x the largest output)
-    return z + 3 * n + 2 * g + part + 64;
+    const size_t part = (size_t)64 * kHid * kFlat;           // split-K partials (up to 64 x the largest output), also
+                                                             // the batch reductions' (<= kRedMaxBlocks x 3072)
+    return z + 3 * ((n + 3) & ~(size_t)3) + 2 * g + part + 64;  // pred, dpred, lossp each padded to 4 floats
 }
 
 cudaError_t launch_profiles(const float *map, int W, int H, const int32_t *poses, int P, const int32_t *dirs, int B,
@@ -969,15 +1113,20 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     const __nv_bfloat162 *xb = (const __nv_bfloat162 *)x;
     TrainBufs t;
     float *q = ws;
-    t.z1 = q, q += (size_t)N * 128 * kCh;
-    t.z2 = q, q += (size_t)N * 64 * kCh;
-    t.z3 = q, q += (size_t)N * 32 * kCh;
-    t.z4 = q, q += (size_t)N * kHid;
-    t.pred = q, q += N;
-    t.dpred = q, q += N;
-    t.lossp = q, q += N;
-    t.g1 = q, q += (size_t)N * 128 * kCh;
-    t.g2 = q, q += (size_t)N * 128 * kCh;
+    auto take = [&](size_t n) {  // every buffer 16-byte aligned (float4 loads)
+        float *r = q;
+        q += (n + 3) & ~(size_t)3;
+        return r;
+    };
+    t.z1 = take((size_t)N * 128 * kCh);
+    t.z2 = take((size_t)N * 64 * kCh);
+    t.z3 = take((size_t)N * 32 * kCh);
+    t.z4 = take((size_t)N * kHid);
+    t.pred = take(N);
+    t.dpred = take(N);
+    t.lossp = take(N);
+    t.g1 = take((size_t)N * 128 * kCh);
+    t.g2 = take((size_t)N * 128 * kCh);
     t.part = q;
     t.part_floats = (size_t)64 * kHid * kFlat;
     cudaError_t e;
@@ -1002,12 +1151,12 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     k_loss<<<1, 1024, 0, s>>>(t.lossp, N, loss);
     FSMI_TRY(cudaGetLastError());
     // backward: head
-    k_colsum<<<grid_cap(kHid), 256, 0, s>>>(N, kHid, W5Grad{t.dpred, t.z4}, grad + oW5);
-    k_colsum<<<1, 256, 0, s>>>(N, 1, B5Grad{t.dpred}, grad + oB5);
+    FSMI_TRY(colsum(N, kHid, W5Grad{t.dpred, t.z4}, grad + oW5, t.part, s));
+    FSMI_TRY(colsum(N, 1, B5Grad{t.dpred}, grad + oB5, t.part, s));
     float *dz4 = t.g1;  // [N][256]
     k_dz4<<<grid_cap(((long long)N * kHid + 255) / 256), 256, 0, s>>>(t.z4, t.dpred, w, N, dz4);
     FSMI_TRY(cudaGetLastError());
-    k_colsum<<<grid_cap(kHid), 256, 0, s>>>(N, kHid, SumDz{dz4, kHid}, grad + oB4);
+    FSMI_TRY(colsum(N, kHid, SumDz{dz4, kHid}, grad + oB4, t.part, s));
     // fc1: gW4[j][i] = sum_n dz4[n][j] relu(z3)[n][i]; dz3 = (dz4 W4) [z3 > 0]
     FSMI_TRY(gemm(kHid, kFlat, N, RowT{dz4, kHid}, ReluRow{t.z3, kFlat}, Store{grad + oW4, kFlat}, t.part,
                   t.part_floats, s));
@@ -1015,23 +1164,20 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     FSMI_TRY(gemm(N, kFlat, kHid, RowN{dz4, kHid}, WRow{w + oW4, kFlat}, StoreMask{dz3, t.z3, kFlat}, t.part,
                   t.part_floats, s));
     // conv3: weights from relu(z2); data gradient into dz2 = (...) [z2 > 0]
-    FSMI_TRY(gemm(kCh, kK * kCh, N * 32, DzT{dz3}, Im2colT<ConvA>{ConvA{t.z2, 64}}, Store{grad + oW3, kK * kCh},
-                  t.part, t.part_floats, s));
-    k_colsum<<<grid_cap(kCh), 256, 0, s>>>(N * 32, kCh, SumDz{dz3, kCh}, grad + oB3);
+    FSMI_TRY(wgrad<kCh>(N * 32, 64, dz3, t.z2, nullptr, grad + oW3, t.part, s));
+    FSMI_TRY(colsum(N * 32, kCh, SumDz{dz3, kCh}, grad + oB3, t.part, s));
     float *dz2 = t.g1;  // [N][64][32]
     FSMI_TRY(gemm(N * 64, kCh, kK * kCh, DzGather{dz3, 64}, WConvT{w + oW3}, StoreMask{dz2, t.z2, kCh}, t.part,
                   t.part_floats, s));
     // conv2
-    FSMI_TRY(gemm(kCh, kK * kCh, N * 64, DzT{dz2}, Im2colT<ConvA>{ConvA{t.z1, 128}}, Store{grad + oW2, kK * kCh},
-                  t.part, t.part_floats, s));
-    k_colsum<<<grid_cap(kCh), 256, 0, s>>>(N * 64, kCh, SumDz{dz2, kCh}, grad + oB2);
+    FSMI_TRY(wgrad<kCh>(N * 64, 128, dz2, t.z1, nullptr, grad + oW2, t.part, s));
+    FSMI_TRY(colsum(N * 64, kCh, SumDz{dz2, kCh}, grad + oB2, t.part, s));
     float *dz1 = t.g2;  // [N][128][32]
     FSMI_TRY(gemm(N * 128, kCh, kK * kCh, DzGather{dz2, 128}, WConvT{w + oW2}, StoreMask{dz1, t.z1, kCh}, t.part,
                   t.part_floats, s));
     // conv1
-    FSMI_TRY(gemm(kCh, kK * kCin, N * 128, DzT{dz1}, Im2colT<ConvA1>{ConvA1{xb}}, Store{grad + oW1, kK * kCin},
-                  t.part, t.part_floats, s));
-    k_colsum<<<grid_cap(kCh), 256, 0, s>>>(N * 128, kCh, SumDz{dz1, kCh}, grad + oB1);
+    FSMI_TRY(wgrad<kCin>(N * 128, kL, dz1, nullptr, xb, grad + oW1, t.part, s));
+    FSMI_TRY(colsum(N * 128, kCh, SumDz{dz1, kCh}, grad + oB1, t.part, s));
 #undef FSMI_TRY
     return cudaGetLastError();
 }

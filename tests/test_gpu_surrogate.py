@@ -63,8 +63,10 @@ def _profiles(grid, poses, dirs):
     return x, x.float().cpu().numpy().astype(np.float64)
 
 
-def test_loss_and_gradient_match_oracle():
-    grid, poses, dirs = _case(n_poses=3, nb=40)
+@pytest.mark.parametrize("nb", [40, 41])
+def test_loss_and_gradient_match_oracle(nb):
+    # 3 x 41 = 123 beams: a batch that is not a multiple of 4 (the workspace's buffers stay aligned)
+    grid, poses, dirs = _case(n_poses=3, nb=nb)
     x, xh = _profiles(grid, poses, dirs)
     N = x.shape[0]
     rng = np.random.default_rng(4)
