@@ -471,7 +471,11 @@ fsmi_status fsmi_surrogate_workspace_size(int mode, long long N, size_t *bytes);
 /* fsmi_surrogate_loss_grad - one training step's forward and backward on a batch of N profiles
  * x [N][256][2] (BF16) with targets y [N]: loss = mean (pred - y)^2 (device float) and its gradient
  * grad [FSMI_SURR_NPARAMS] with respect to the parameters (through the BF16 weights). Activations
- * are kept in FP32. pred (optional) receives the N predictions. 1 <= N <= 65536. Deterministic. */
+ * are kept in FP32; the layers' products run on the tensor cores with each FP32 operand split into
+ * BF16 terms (three in the forward pass, as accurate as FP32 arithmetic; two in the backward
+ * pass). pred (optional) receives the N predictions. On return the workspace begins with the FP32
+ * pre-activations z1 [N][128][32], z2 [N][64][32], z3 [N][32][32], z4 [N][256], in that order.
+ * 1 <= N <= 65536. Deterministic. */
 fsmi_status fsmi_surrogate_loss_grad(const float *params, const uint16_t *wbf16, const uint16_t *x,
                                      const float *y, int N, float *grad, float *loss, float *pred,
                                      void *ws, size_t ws_bytes, fsmi_stream_t stream);

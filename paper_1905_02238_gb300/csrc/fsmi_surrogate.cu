@@ -91,61 +91,10 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// ---- split-K SIMT GEMM with index functions ------------------------------------------------------
+// ---- split-K partial sums --------------------------------------------------------------------------
 //
-// C[m][n] = sum_k A(m, k) B(k, n); block tile 64 x 64, k-chunks of 16, 4 x 4 outputs per thread.
-// With splits > 1, block z sums k in [z * kper, (z+1) * kper) and writes its partial tile to
-// part[z][m][n]; k_split_reduce then adds the splits in order and applies the epilogue.
-
-constexpr int kTM = 64, kTN = 64, kTK = 16;
-
-template <class FA, class FB, class FE>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kper, FA fa, FB fb, FE fe, float *part)
-{
-    __shared__ float As[kTK][kTM + 4];
-    __shared__ float Bs[kTK][kTN + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-    const int kbeg = blockIdx.z * kper, kend = min(K, kbeg + kper);
-    float acc[4][4] = {};
-    for (int k0 = kbeg; k0 < kend; k0 += kTK) {
-        for (int e = threadIdx.x; e < kTK * kTM; e += 256) {
-            const int kk = e / kTM, mm = e % kTM;
-            const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < kend) ? fa(m, k) : 0.0f;
-        }
-        for (int e = threadIdx.x; e < kTK * kTN; e += 256) {
-            const int kk = e / kTN, nn = e % kTN;
-            const int n = n0 + nn, k = k0 + kk;
-            Bs[kk][nn] = (n < N && k < kend) ? fb(k, n) : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kTK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
-            if (m >= M || n >= N) continue;
-            if (gridDim.z > 1)
-                part[((size_t)blockIdx.z * M + m) * N + n] = acc[i][j];
-            else
-                fe(m, n, acc[i][j]);
-        }
-}
+// The training GEMMs (k_gemm_tc, below) may split K over blocks: block z writes its partial tile to
+// part[z][m][n] and k_split_reduce adds the splits in order and applies the epilogue.
 
 template <class FE>
 __global__ void k_split_reduce(int M, int N, int splits, const float *__restrict__ part, FE fe)
@@ -162,25 +111,6 @@ int grid_cap(long long want)
 {
     const long long cap = (long long)sm_count() * 32;
     return (int)(want < 1 ? 1 : (want > cap ? cap : want));
-}
-
-template <class FA, class FB, class FE>
-cudaError_t gemm(int M, int N, int K, FA fa, FB fb, FE fe, float *part, size_t part_floats, cudaStream_t s)
-{
-    const int gx = (N + kTN - 1) / kTN, gy = (M + kTM - 1) / kTM;
-    // split K when the output grid alone cannot fill the GPU and K is long
-    int splits = 1;
-    const long long blocks = (long long)gx * gy;
-    while (splits < 64 && blocks * splits < 2LL * sm_count() && K / (splits * 2) >= 256 &&
-           (size_t)(splits * 2) * M * N <= part_floats)
-        splits *= 2;
-    int kper = (K + splits - 1) / splits;
-    kper = (kper + kTK - 1) / kTK * kTK;
-    k_gemm<<<dim3(gx, gy, splits), 256, 0, s>>>(M, N, K, kper, fa, fb, fe, part);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || splits == 1) return e;
-    k_split_reduce<<<grid_cap(((long long)M * N + 255) / 256), 256, 0, s>>>(M, N, splits, part, fe);
-    return cudaGetLastError();
 }
 
 // ---- training: forward -------------------------------------------------------------------------
@@ -298,13 +228,13 @@ __global__ void k_dz4(const float *__restrict__ z4, const float *__restrict__ dp
 // b adds rows [b * rows, (b + 1) * rows) into part[b][...], then one thread per output adds the
 // blocks' partials in block order. The row split depends only on R, so a step's gradients are the
 // same floats on every run (and every GPU).
-constexpr int kRedMinRows = 512;   // rows per block, at least
 constexpr int kRedMaxBlocks = 2048;  // blocks per reduction, at most (bounds the partials)
 
-int red_rows(long long R)
+// rows per block: at least min_rows, a multiple of 32, and few enough blocks
+int red_rows(long long R, int min_rows)
 {
     const long long per = (R + kRedMaxBlocks - 1) / kRedMaxBlocks;
-    return (int)std::max<long long>(kRedMinRows, (per + 31) / 32 * 32);
+    return (int)std::max<long long>(min_rows, (per + 31) / 32 * 32);
 }
 
 // part[b][c] = sum over the block's rows r of f(r, c), for C columns (C divides 256): the block's
@@ -440,7 +370,7 @@ __global__ void __launch_bounds__(256) k_wgrad_part(int R, int rows, int Lin, co
 template <class F>
 cudaError_t colsum(int R, int C, F f, float *out, float *part, cudaStream_t s)
 {
-    const int rows = red_rows(R), nblk = (R + rows - 1) / rows;
+    const int rows = red_rows(R, 64), nblk = (R + rows - 1) / rows;
     k_colsum_part<<<nblk, 256, 0, s>>>(R, C, rows, f, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -454,7 +384,7 @@ template <int CIN>
 cudaError_t wgrad(int R, int Lin, const float *dz, const float *z, const __nv_bfloat162 *x, float *out, float *part,
                   cudaStream_t s)
 {
-    const int rows = red_rows(R), nblk = (R + rows - 1) / rows;
+    const int rows = red_rows(R, 512), nblk = (R + rows - 1) / rows;
     k_wgrad_part<CIN><<<nblk, 256, 0, s>>>(R, rows, Lin, dz, z, x, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -591,6 +521,146 @@ __device__ __forceinline__ void mma_bf16_k8(float (&c)[4], unsigned a0, unsigned
     asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
                  : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
                  : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// ---- training GEMMs on the tensor cores ----------------------------------------------------------
+//
+// C[m][n] = sum_k A(m, k) B(k, n) with FP32 operands given as index functions of (row, k), the
+// products on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation). An FP32
+// operand is split into BF16 terms, a_1 = bf16(a), a_2 = bf16(a - a_1), a_3 = bf16(a - a_1 - a_2),
+// whose sum is a (1 + d) with |d| <= 2^-18 for two terms and 2^-27 for three (the split-BF16
+// products of Henry, Tang and Heinecke, "Leveraging the bfloat16 artificial intelligence datatype
+// for higher-precision computations", 2019). AS = 3 (the forward pass, whose outputs feed the loss
+// and its derivative): A B = (A_1 + A_2 + A_3) B for a B of BF16 weights, exact in one term, as
+// accurate as FP32 arithmetic. AS = 2 (the backward pass): A_1 B + A_2 B, plus A_1 B_2 when B is
+// FP32 as well (BSPLIT; the A_2 B_2 term, below 2^-18 of the product, is left out). Block tile
+// TM x TN (TM TN = 4096: 8 warps of 32 x 16 outputs, 2 x 2 MMA tiles each), K in stages of kTrK,
+// staged as BF16 pairs in [row][k] order with a row pitch of kTrPitch elements (20 words: the
+// fragment loads of the eight row groups fall in distinct banks). AKF / BKF: the operand's index
+// function is contiguous in k (stage k-pairs across the threads) or in its row (stage rows across
+// them). With more than one K split, block z writes its partial tile to part[z][m][n] and
+// k_split_reduce adds the splits in order.
+constexpr int kTrK = 32, kTrPitch = kTrK + 8;
+
+// the BF16 terms of v0, v1 (t[0] = bf16(v), t[i] = bf16(v - t[0] - ... - t[i-1])) at `at` of each
+// of the first `terms` arrays
+__device__ __forceinline__ void split_store(bf16 *const *t, int terms, int at, float v0, float v1)
+{
+    for (int i = 0; i < terms; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        *reinterpret_cast<__nv_bfloat162 *>(t[i] + at) = h;
+        v0 -= __low2float(h);
+        v1 -= __high2float(h);
+    }
+}
+
+__device__ __forceinline__ unsigned lds32(const bf16 *p) { return *reinterpret_cast<const unsigned *>(p); }
+
+template <int TN, int AS, bool BSPLIT, bool AKF, bool BKF, class FA, class FB, class FE>
+__global__ void __launch_bounds__(256) k_gemm_tc(int M, int N, int K, int kper, FA fa, FB fb, FE fe, float *part)
+{
+    constexpr int TM = 4096 / TN, WN = TN / 16, KP = kTrK / 2;
+    static_assert(AS == 2 || AS == 3, "two or three BF16 terms of A");
+    __shared__ __align__(16) bf16 sA[AS][TM * kTrPitch];
+    __shared__ __align__(16) bf16 sB[BSPLIT ? 2 : 1][TN * kTrPitch];
+    bf16 *const ta[3] = {sA[0], sA[1], sA[AS - 1]};
+    bf16 *const tb[2] = {sB[0], sB[BSPLIT ? 1 : 0]};
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int wm = w / WN, wn = w % WN;  // the warp's outputs: rows 32 wm .., columns 16 wn ..
+    const int g = lane >> 2, tq = lane & 3;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int kbeg = blockIdx.z * kper, kend = min(K, kbeg + kper);
+    float acc[2][2][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += kTrK) {
+        for (int e = tid; e < TM * KP; e += 256) {
+            const int r = AKF ? e / KP : e % TM, kp = AKF ? e % KP : e / TM;
+            const int m = m0 + r, k = k0 + 2 * kp;
+            float v0 = 0.0f, v1 = 0.0f;
+            if (m < M) {
+                if (k < kend) v0 = fa(m, k);
+                if (k + 1 < kend) v1 = fa(m, k + 1);
+            }
+            split_store(ta, AS, r * kTrPitch + 2 * kp, v0, v1);
+        }
+        for (int e = tid; e < TN * KP; e += 256) {
+            const int r = BKF ? e / KP : e % TN, kp = BKF ? e % KP : e / TN;
+            const int n = n0 + r, k = k0 + 2 * kp;
+            float v0 = 0.0f, v1 = 0.0f;
+            if (n < N) {
+                if (k < kend) v0 = fb(k, n);
+                if (k + 1 < kend) v1 = fb(k + 1, n);
+            }
+            split_store(tb, BSPLIT ? 2 : 1, r * kTrPitch + 2 * kp, v0, v1);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kTrK; ks += 16) {
+            unsigned a[AS][2][4], b[2][2][2];
+#pragma unroll
+            for (int i = 0; i < AS; ++i)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const bf16 *p = sA[i] + (32 * wm + 16 * mt + g) * kTrPitch + ks + 2 * tq;
+                    a[i][mt][0] = lds32(p);
+                    a[i][mt][1] = lds32(p + 8 * kTrPitch);
+                    a[i][mt][2] = lds32(p + 8);
+                    a[i][mt][3] = lds32(p + 8 * kTrPitch + 8);
+                }
+#pragma unroll
+            for (int i = 0; i < (BSPLIT ? 2 : 1); ++i)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const bf16 *p = sB[i] + (16 * wn + 8 * nt + g) * kTrPitch + ks + 2 * tq;
+                    b[i][nt][0] = lds32(p);
+                    b[i][nt][1] = lds32(p + 8);
+                }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+#pragma unroll
+                    for (int i = 0; i < AS; ++i)
+                        mma_bf16(acc[mt][nt], a[i][mt][0], a[i][mt][1], a[i][mt][2], a[i][mt][3], b[0][nt][0],
+                                 b[0][nt][1]);
+                    if (BSPLIT)
+                        mma_bf16(acc[mt][nt], a[0][mt][0], a[0][mt][1], a[0][mt][2], a[0][mt][3], b[1][nt][0],
+                                 b[1][nt][1]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + 32 * wm + 16 * mt + g + 8 * (q >> 1), n = n0 + 16 * wn + 8 * nt + 2 * tq + (q & 1);
+                if (m >= M || n >= N) continue;
+                if (gridDim.z > 1)
+                    part[((size_t)blockIdx.z * M + m) * N + n] = acc[mt][nt][q];
+                else
+                    fe(m, n, acc[mt][nt][q]);
+            }
+}
+
+template <int TN, int AS, bool BSPLIT, bool AKF, bool BKF, class FA, class FB, class FE>
+cudaError_t gemm_tc(int M, int N, int K, FA fa, FB fb, FE fe, float *part, size_t part_floats, cudaStream_t s)
+{
+    constexpr int TM = 4096 / TN;
+    const int gx = (N + TN - 1) / TN, gy = (M + TM - 1) / TM;
+    int splits = 1;  // split K when the output grid alone cannot fill the GPU and K is long
+    const long long blocks = (long long)gx * gy;
+    while (splits < 64 && blocks * splits < 2LL * sm_count() && K / (splits * 2) >= 256 &&
+           (size_t)(splits * 2) * M * N <= part_floats)
+        splits *= 2;
+    int kper = (K + splits - 1) / splits;
+    kper = (kper + kTrK - 1) / kTrK * kTrK;
+    k_gemm_tc<TN, AS, BSPLIT, AKF, BKF><<<dim3(gx, gy, splits), 256, 0, s>>>(M, N, K, kper, fa, fb, fe, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    k_split_reduce<<<grid_cap(((long long)M * N + 255) / 256), 256, 0, s>>>(M, N, splits, part, fe);
+    return cudaGetLastError();
 }
 
 // Conv activations [rows][32 channels] (64 B per row) are kept in 128-byte lines of two rows;
@@ -1130,19 +1200,23 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     t.part = q;
     t.part_floats = (size_t)64 * kHid * kFlat;
     cudaError_t e;
-#define FSMI_TRY(x_)             \
+#define FSMI_TRY(...)            \
     do {                         \
-        e = (x_);                \
+        e = (__VA_ARGS__);       \
         if (e != cudaSuccess) return e; \
     } while (0)
     // forward
-    FSMI_TRY(gemm(N * 128, kCh, kK * kCin, ConvA1{xb}, WConv{w + oW1, kCin}, StoreBias{t.z1, params + oB1, kCh},
+    FSMI_TRY(gemm_tc<32, 3, false, true, true>(N * 128, kCh, kK * kCin, ConvA1{xb}, WConv{w + oW1, kCin},
+                                            StoreBias{t.z1, params + oB1, kCh},
                   t.part, t.part_floats, s));
-    FSMI_TRY(gemm(N * 64, kCh, kK * kCh, ConvA{t.z1, 128}, WConv{w + oW2, kCh}, StoreBias{t.z2, params + oB2, kCh},
+    FSMI_TRY(gemm_tc<32, 3, false, true, true>(N * 64, kCh, kK * kCh, ConvA{t.z1, 128}, WConv{w + oW2, kCh},
+                                            StoreBias{t.z2, params + oB2, kCh},
                   t.part, t.part_floats, s));
-    FSMI_TRY(gemm(N * 32, kCh, kK * kCh, ConvA{t.z2, 64}, WConv{w + oW3, kCh}, StoreBias{t.z3, params + oB3, kCh},
+    FSMI_TRY(gemm_tc<32, 3, false, true, true>(N * 32, kCh, kK * kCh, ConvA{t.z2, 64}, WConv{w + oW3, kCh},
+                                            StoreBias{t.z3, params + oB3, kCh},
                   t.part, t.part_floats, s));
-    FSMI_TRY(gemm(N, kHid, kFlat, ReluRow{t.z3, kFlat}, WT{w + oW4, kFlat}, StoreBias{t.z4, params + oB4, kHid},
+    FSMI_TRY(gemm_tc<64, 3, false, true, true>(N, kHid, kFlat, ReluRow{t.z3, kFlat}, WT{w + oW4, kFlat},
+                                            StoreBias{t.z4, params + oB4, kHid},
                   t.part, t.part_floats, s));
     float *pred = pred_out ? pred_out : t.pred;
     k_head<<<grid_cap((N + 7) / 8), 256, 0, s>>>(t.z4, w, params, y, N, pred, t.dpred, t.lossp);
@@ -1158,22 +1232,26 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     FSMI_TRY(cudaGetLastError());
     FSMI_TRY(colsum(N, kHid, SumDz{dz4, kHid}, grad + oB4, t.part, s));
     // fc1: gW4[j][i] = sum_n dz4[n][j] relu(z3)[n][i]; dz3 = (dz4 W4) [z3 > 0]
-    FSMI_TRY(gemm(kHid, kFlat, N, RowT{dz4, kHid}, ReluRow{t.z3, kFlat}, Store{grad + oW4, kFlat}, t.part,
+    FSMI_TRY(gemm_tc<64, 2, true, false, false>(kHid, kFlat, N, RowT{dz4, kHid}, ReluRow{t.z3, kFlat},
+                                             Store{grad + oW4, kFlat}, t.part,
                   t.part_floats, s));
     float *dz3 = t.g2;  // [N][32][32]
-    FSMI_TRY(gemm(N, kFlat, kHid, RowN{dz4, kHid}, WRow{w + oW4, kFlat}, StoreMask{dz3, t.z3, kFlat}, t.part,
+    FSMI_TRY(gemm_tc<64, 2, false, true, false>(N, kFlat, kHid, RowN{dz4, kHid}, WRow{w + oW4, kFlat},
+                                             StoreMask{dz3, t.z3, kFlat}, t.part,
                   t.part_floats, s));
     // conv3: weights from relu(z2); data gradient into dz2 = (...) [z2 > 0]
     FSMI_TRY(wgrad<kCh>(N * 32, 64, dz3, t.z2, nullptr, grad + oW3, t.part, s));
     FSMI_TRY(colsum(N * 32, kCh, SumDz{dz3, kCh}, grad + oB3, t.part, s));
     float *dz2 = t.g1;  // [N][64][32]
-    FSMI_TRY(gemm(N * 64, kCh, kK * kCh, DzGather{dz3, 64}, WConvT{w + oW3}, StoreMask{dz2, t.z2, kCh}, t.part,
+    FSMI_TRY(gemm_tc<32, 2, false, true, false>(N * 64, kCh, kK * kCh, DzGather{dz3, 64}, WConvT{w + oW3},
+                                             StoreMask{dz2, t.z2, kCh}, t.part,
                   t.part_floats, s));
     // conv2
     FSMI_TRY(wgrad<kCh>(N * 64, 128, dz2, t.z1, nullptr, grad + oW2, t.part, s));
     FSMI_TRY(colsum(N * 64, kCh, SumDz{dz2, kCh}, grad + oB2, t.part, s));
     float *dz1 = t.g2;  // [N][128][32]
-    FSMI_TRY(gemm(N * 128, kCh, kK * kCh, DzGather{dz2, 128}, WConvT{w + oW2}, StoreMask{dz1, t.z1, kCh}, t.part,
+    FSMI_TRY(gemm_tc<32, 2, false, true, false>(N * 128, kCh, kK * kCh, DzGather{dz2, 128}, WConvT{w + oW2},
+                                             StoreMask{dz1, t.z1, kCh}, t.part,
                   t.part_floats, s));
     // conv1
     FSMI_TRY(wgrad<kCin>(N * 128, kL, dz1, nullptr, xb, grad + oW1, t.part, s));

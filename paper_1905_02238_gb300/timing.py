@@ -3,10 +3,13 @@
     python -m paper_1905_02238_gb300.timing --path 3d --variant exact --poses 64 --repeat 4
     python -m paper_1905_02238_gb300.timing --path 2d --variant approx --poses 1024
     python -m paper_1905_02238_gb300.timing --path surrogate --poses 4096
+    python -m paper_1905_02238_gb300.timing --path train --repeat 50
 
 2d: the 2048x2048 office map (poses x 360 beams, R = 256, sigma = 2); 3d: the 512x512x128 voxel
 world (poses x 128x128 rays, 384 virtual cells, run cap 64); surrogate: inference on the office
-map. One untimed call, then `repeat` calls timed with CUDA events; prints ms per call.
+map; train: surrogate training steps (batch 4096) on one office map of `poses` poses (256) whose
+beams exact FSMI labels. One untimed call, then `repeat` calls timed with CUDA events; prints ms
+per call.
 """
 from __future__ import annotations
 
@@ -19,7 +22,7 @@ from . import build, fsmi, synth
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--path", choices=["2d", "3d", "surrogate"], default="2d")
+    ap.add_argument("--path", choices=["2d", "3d", "surrogate", "train"], default="2d")
     ap.add_argument("--variant", choices=["exact", "approx", "approx_band", "uniform"], default="exact")
     ap.add_argument("--poses", type=int, default=None)
     ap.add_argument("--repeat", type=int, default=4)
@@ -49,6 +52,20 @@ def main() -> None:
         def call():
             fsmi.eval_3d(v, p, d, prm, out=out, ws=ws)
         what = f"eval_3d {args.variant} {p.shape[0]} x {d.shape[0]} rays"
+    elif args.path == "train":
+        from . import surrogate as sg
+
+        # surrogate training steps of 4096 beams drawn from one exact-labelled office map
+        d = torch.from_numpy(synth.beam_dirs_2d(360)).to(dev)
+        prm = fsmi.Params(variant=fsmi.EXACT, sigma=2.0, delta_occ=1.5, delta_emp=0.67, max_range=256.0)
+        maps = sg.label_maps(1, args.poses or 256, d, prm, seed=100)
+        lab = maps[0].labels
+        net = sg.Surrogate(seed=0, scale=float(lab.std()), shift=float(lab.mean()))
+        net.train(maps, d, steps=3, batch=4096)
+
+        def call():
+            net.train(maps, d, steps=1, batch=4096)
+        what = "surrogate training step of 4096 beams"
     else:
         from . import surrogate as sg
 

@@ -79,19 +79,41 @@ def test_loss_and_gradient_match_oracle(nb):
     grad = torch.zeros(fsmi.SURR_NPARAMS, device="cuda")
     loss = torch.zeros(1, device="cuda")
     pred = torch.zeros(N, device="cuda")
-    fsmi.surrogate_loss_grad(params, wb, x, _cuda(y), grad, loss, pred=pred)
+    ws = torch.zeros(fsmi.surrogate_workspace_size(0, N), dtype=torch.uint8, device="cuda")
+    fsmi.surrogate_loss_grad(params, wb, x, _cuda(y), grad, loss, pred=pred, ws=ws)
     rpred, cache = S.forward(th, xh)
     rloss, dpred = S.mse(rpred, y)
-    rgrad = S.backward(cache, dpred)
     np.testing.assert_allclose(pred.cpu().numpy(), rpred, rtol=2e-5, atol=2e-5 * np.abs(rpred).max())
     assert abs(float(loss.item()) - rloss) <= 5e-5 * rloss
+    # The forward pass element by element: the step leaves its FP32 pre-activations z1, z2, z3, z4 at
+    # the start of the workspace; each lies within 1e-5 of the sum of its terms' absolute values (the
+    # oracle's forward on |weights| and |x|) of the oracle's, which covers FP32 accumulation of a
+    # conv's 96 terms in the worst case (96 x 2^-24 = 5.7e-6) and of fc1's 1024 as a random walk.
+    _, zabs = S.forward(np.abs(th), np.abs(xh))
+    zf = ws.view(torch.float32).cpu().numpy().astype(np.float64)
+    at = 0
+    gcache = dict(cache)
+    for k, shape in (("z1", (N, 128, 32)), ("z2", (N, 64, 32)), ("z3", (N, 32, 32)), ("z4", (N, 256))):
+        n = int(np.prod(shape))
+        zg = zf[at:at + n].reshape(shape)
+        at += n
+        assert np.all(np.abs(zg - cache[k]) <= 1e-5 * zabs[k]), k
+        gcache[k] = zg
+    # The backward pass is then compared at the step's own forward state: the oracle differentiates
+    # the GPU's pre-activations (ReLU masks included: a pre-activation within rounding of zero may
+    # take either side) with dpred = 2 (pred - y) / N of the GPU's predictions.
+    gcache["a1"], gcache["a2"], gcache["a3"] = (np.maximum(gcache[k], 0.0) for k in ("z1", "z2", "z3"))
+    gcache["h0"] = gcache["a3"].reshape(N, -1)
+    gcache["a4"] = np.maximum(gcache["z4"], 0.0)
+    _, dpred = S.mse(pred.cpu().numpy().astype(np.float64), y)
+    cache = gcache
+    rgrad = S.backward(cache, dpred)
     g = grad.cpu().numpy().astype(np.float64)
     # Element by element: each gradient entry is a sum of products (over beams, positions and the
     # layers above); the FP32 sums can cancel, so the bound scales with the sum of the absolute
     # values of those products, which the oracle's backward pass gives when it runs on |weights|,
     # |dpred| and the (non-negative) activations with the same ReLU masks. The bound, 2e-4 of that
-    # sum, covers FP32 accumulation and the FP32 forward values it multiplies (dpred = 2 (pred - y)
-    # / N cancels where pred is close to y, so its relative error can reach well above one ulp).
+    # sum, covers the backward pass's split-BF16 products (2^-17 per product) and FP32 accumulation.
     acache = dict(cache)
     acache["p"] = {k: np.abs(v) for k, v in cache["p"].items()}
     for k in ("a0", "a1", "a2", "a3", "a4", "h0"):
