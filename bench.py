@@ -975,6 +975,11 @@ def run_fsmi(args):
             line["pipe_rates"] = pipe_rates_leg(dev)
             line["variants"] = other_variants(g, p, d, out, cells=cells, terms=terms, band=band,
                                               peak_terms=peak_terms, pipes=line["pipe_rates"], sm_mhz=sm_max)
+            fw = line["variants"]["exact_fsmi_full_window"]
+            # beside the headline: the same batch with every non-zero term of Theorem 1's n(n+1) sum,
+            # bit-identical to the full sweep (FSMI_FLAG_FULL_WINDOW); 5 back-to-back calls, no graph
+            line["full_window"] = {"value": fw["beams_per_s"], "unit": "beams/s", "ms": fw["ms"],
+                                   "flag": "FSMI_FLAG_FULL_WINDOW"}
             line["rle_vs_cells"] = rle_crossover_leg(dev)
             net = None
             if not args.no_surrogate:
