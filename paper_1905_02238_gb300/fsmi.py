@@ -285,6 +285,58 @@ def eval_2d(grid: torch.Tensor, poses: torch.Tensor, dirs: torch.Tensor, prm: Pa
     return m.out(out)
 
 
+class Pipeline2D:
+    """Consecutive fsmi_eval_2d calls on host data with their copies overlapped: submit() copies its
+    host inputs (pinned, for the copies to be asynchronous) into one of two device buffer sets on a
+    copy stream, evaluates them on a compute stream once they have landed, and copies the result
+    into the given host tensor (pinned as well); the next submit's input copies then run while this
+    evaluation does. The host tensors must stay alive and unchanged until wait(). The results are
+    the floats eval_2d returns. wait() returns when every submitted result is on the host. Shapes
+    are fixed at construction: grid [H, W], poses [P, 4], dirs [B, 2]."""
+
+    def __init__(self, prm: Params, W: int, H: int, P: int, B: int):
+        load()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.prm = prm
+        self.copy = torch.cuda.Stream(dev)
+        self.comp = torch.cuda.Stream(dev)
+        self.bufs = [(torch.empty((H, W), dtype=torch.float32, device=dev),
+                      torch.empty((P, 4), dtype=torch.int32, device=dev),
+                      torch.empty((B, 2), dtype=torch.int32, device=dev),
+                      torch.empty((P, B), dtype=torch.float32, device=dev)) for _ in range(2)]
+        self.ws = torch.empty(workspace_size(FN_EVAL_2D, W * H), dtype=torch.uint8, device=dev)
+        self.free = [None, None]  # per buffer set: the event after which its last evaluation is done
+        self.k = 0
+
+    def submit(self, grid: torch.Tensor, poses: torch.Tensor, dirs: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+        for t, name in ((grid, "grid"), (poses, "poses"), (dirs, "dirs"), (out, "out")):
+            if t.is_cuda:
+                raise ValueError(f"{name} must be a host tensor")
+        g, ps, ds, o = self.bufs[self.k]
+        if out.shape != o.shape or out.dtype != torch.float32:
+            raise ValueError(f"out must be float32 {tuple(o.shape)}")
+        with torch.cuda.stream(self.copy):
+            if self.free[self.k] is not None:
+                self.copy.wait_event(self.free[self.k])  # the evaluation that last read these buffers
+            g.copy_(grid, non_blocking=True)
+            ps.copy_(poses, non_blocking=True)
+            ds.copy_(dirs, non_blocking=True)
+            landed = torch.cuda.Event()
+            landed.record(self.copy)
+        with torch.cuda.stream(self.comp):
+            self.comp.wait_event(landed)
+            eval_2d(g, ps, ds, self.prm, out=o, ws=self.ws)
+            out.copy_(o, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(self.comp)
+        self.free[self.k] = done
+        self.k ^= 1
+        return out
+
+    def wait(self) -> None:
+        self.comp.synchronize()
+
+
 def make_sets_2d(sets, device=None):
     """Packs candidate-set descriptors [(pose_offset, npose, dir_offset, nbeam, max_range), ...]
     into the fsmi_set_2d layout (int32 [nsets, 8] on `device`, consecutive output blocks in list

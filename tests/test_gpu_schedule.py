@@ -319,3 +319,26 @@ def test_autotune_skips_failing_candidates():
     with pytest.raises(fsmi.FsmiError):
         fsmi.autotune(K2, fn, cands[:1], reps=1)
     assert fsmi.get_schedule(K2) == fsmi.Schedule(8, 0, 1, 32)  # left as it was
+
+
+def test_pipeline_2d_equals_separate_calls():
+    # consecutive submits alternate between two device buffer sets; each result must be the floats
+    # of its own inputs (not of the batch before it), whatever the overlap of copies and evaluation
+    grid, _ = _office(size=256)
+    dirs = synth.beam_dirs_2d(90)
+    prm, _ = _prm2d(fsmi.EXACT, 96.0)
+    P = 12
+    batches = [synth.free_cell_poses_2d(grid, P, seed=20 + i) for i in range(5)]
+    hg = torch.from_numpy(grid).pin_memory()
+    hd = torch.from_numpy(dirs).pin_memory()
+    pipe = fsmi.Pipeline2D(prm, grid.shape[1], grid.shape[0], P, dirs.shape[0])
+    outs = [torch.empty((P, dirs.shape[0]), dtype=torch.float32).pin_memory() for _ in batches]
+    hp = [torch.from_numpy(b).pin_memory() for b in batches]  # alive until the copies have run
+    for p, o in zip(hp, outs):
+        pipe.submit(hg, p, hd, o)
+    pipe.wait()
+    for b, o in zip(batches, outs):
+        ref = fsmi.eval_2d(_cuda(grid), _cuda(b), _cuda(dirs), prm).cpu()
+        assert torch.equal(o, ref)
+    with pytest.raises(ValueError):
+        pipe.submit(hg.cuda(), torch.from_numpy(batches[0]), hd, outs[0])
