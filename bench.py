@@ -230,15 +230,17 @@ def work_counts(fsmi, grid, p, d, chunk=32768):
 def rle_work_counts(fsmi, v, vp, vd, prm, cell_runlen, K, poses_per_chunk=8):
     """Algorithmic work of one fused 3D launch, from the (bit-exact) encoder: virtual-cell samples
     (a 4-byte gather each), runs, and the FP32 work of the path each ray takes. Cell-level form
-    (rays with n < cell_runlen * n_r, not Theorem 5): 2K + 2 FMAs per cell (the 2K + 1 taps of
-    the banded convolution and the product with P(e_j)). Run pairs (the other rays, and every ray
-    under Theorem 5): the A/B terms of pair_AB (csrc/evalrle.cuh), 6 FP32 operations each
-    (window difference, weighted window, two accumulations, the power of x)."""
+    (rays with n < cell_runlen * n_r): 2K + 2 FMAs per cell (the 2K + 1 taps of the banded
+    convolution and the product with P(e_j)); under Theorem 5 the taps of each cell's window of
+    kept pairs (window_conv in csrc/evalrle.cuh) and the product. Run pairs (the other rays): the
+    A/B terms of pair_AB (csrc/evalrle.cuh), 6 FP32 operations each (window difference, weighted
+    window, two accumulations, the power of x)."""
     import torch
 
     thm5 = prm.variant == fsmi.APPROX and prm.approx_reading == 0
     D = prm.trunc_delta
-    tot = {"rays": 0, "samples": 0, "runs": 0, "cell_rays": 0, "cell_cells": 0, "pair_rays": 0, "pair_terms": 0}
+    tot = {"rays": 0, "samples": 0, "runs": 0, "cell_rays": 0, "cell_cells": 0, "pair_rays": 0, "pair_terms": 0,
+           "window_taps": 0}
 
     def terms(Lu, Lv, t):  # pair_AB iterations: j in [max(0, -K - t), min(Lu - 1, Lv - 1 + K - t)]
         lo = torch.clamp(-K - t, min=0)
@@ -257,7 +259,7 @@ def rle_work_counts(fsmi, v, vp, vd, prm, cell_runlen, K, poses_per_chunk=8):
         tot["rays"] += nrays
         tot["samples"] += int(n.sum())
         tot["runs"] += int(nr.sum())
-        cell = torch.zeros_like(n, dtype=torch.bool) if thm5 else (n < cell_runlen * nr)
+        cell = n < cell_runlen * nr
         tot["cell_rays"] += int(cell.sum())
         tot["cell_cells"] += int(n[cell].sum())
         pair = (~cell) & (nr > 0)
@@ -265,6 +267,21 @@ def rle_work_counts(fsmi, v, vp, vd, prm, cell_runlen, K, poses_per_chunk=8):
         ray = torch.repeat_interleave(torch.arange(nrays, device=L.device), nr)
         S = cum[:-1] - cum[off[:-1]][ray]  # run start within its ray
         keep = pair[ray]
+        if thm5 and bool(cell.any()):
+            # each cell j of run u keeps the cells [lo_j, hi_j): lo_j = max(s of the run holding
+            # j - D, s_u - D), hi_j = min(e_u + D, e of the run holding j + D); taps |k - j| <= K
+            crun = torch.repeat_interleave(torch.arange(L.numel(), device=L.device), L)  # run of each cell
+            cray = ray[crun]
+            base = cum[off[:-1]][cray]  # the ray's first cell
+            j = torch.arange(crun.numel(), device=L.device) - base
+            nc = n[cray]
+            ra = crun[base + torch.clamp(j - D, min=0)]
+            rb = crun[base + torch.minimum(j + D, nc - 1)]
+            lo = torch.maximum(S[ra], S[crun] - D)
+            hi = torch.minimum(S[crun] + L[crun] + D, S[rb] + L[rb])
+            taps = torch.clamp(torch.minimum(hi, j + K + 1) - torch.maximum(lo, j - K), min=0)
+            tot["window_taps"] += int(taps[cell[cray]].sum())
+            del crun, cray, base, j, nc, ra, rb, lo, hi, taps
         if thm5:
             tot["pair_terms"] += int(L[keep].sum())  # the diagonal blocks (theta, gamma): L_u terms
             for k in range(1, D + 2):  # runs within Delta of run u lie at most Delta + 1 runs away
@@ -292,7 +309,10 @@ def rle_work_counts(fsmi, v, vp, vd, prm, cell_runlen, K, poses_per_chunk=8):
             c = torch.where(valid[:, :, None] & valid[:, None, :], c, torch.zeros_like(c))
             tot["pair_terms"] += int(c.sum())
         del off, rl, L, cum
-    tot["fp32_ops"] = tot["cell_cells"] * (2 * K + 2) + 6 * tot["pair_terms"]
+    if thm5:
+        tot["fp32_ops"] = tot["window_taps"] + tot["cell_cells"] + 6 * tot["pair_terms"]
+    else:
+        tot["fp32_ops"] = tot["cell_cells"] * (2 * K + 2) + 6 * tot["pair_terms"]
     return tot
 
 
@@ -523,8 +543,12 @@ def other_variants(g, p, d, out, cells=None, terms=None, band=None, peak_terms=N
                            f"{wc['samples']:.4g} virtual-cell samples x 4 B gathered + 4 B out per ray, against the "
                            "measured L2 read bandwidth (the 134 MB volume is mostly L2-served)", traffic=traffic)
             rfma = roofline("alu", wc["fp32_ops"] / sec / 1e12, fma_peak / 1e12, "T FP32 ops/s", f"k_eval_3d ({name})",
-                            f"{wc['cell_cells']:.4g} cells of cell-form rays x {2 * K + 2} FMAs (banded convolution, "
-                            f"K = {K}) + {wc['pair_terms']:.4g} run-pair A/B terms x 6 FP32 ops", traffic=traffic)
+                            (f"{wc['cell_cells']:.4g} cells of cell-form rays: {wc['window_taps']:.4g} window taps "
+                             f"(Theorem 5's kept pairs, |k - j| <= {K}) + 1 FMA each"
+                             if wc["window_taps"] else
+                             f"{wc['cell_cells']:.4g} cells of cell-form rays x {2 * K + 2} FMAs (banded convolution, "
+                             f"K = {K})") + f" + {wc['pair_terms']:.4g} run-pair A/B terms x 6 FP32 ops",
+                            traffic=traffic)
             res[name]["roofline"] = rl2 if fr_l2 >= fr_fma else rfma
             res[name]["roofline_other"] = rfma if fr_l2 >= fr_fma else rl2
     fsmi.set_schedule(fsmi.KIND_RLE, saved)

@@ -299,13 +299,63 @@ __device__ __forceinline__ float band_conv(const float *CP, const float *CC, con
     return v;
 }
 
+// Theorem 5 at the cell level. The pairs (j, k) its sub-blocks keep (the whole diagonal block of
+// each run, and for runs u < v the cells j >= s_v - Delta of run u with the cells k < e_u + Delta
+// of run v, and the mirror image) are, for a first-hit cell j of run u, the contiguous cells
+// [lo_j, hi_j) with lo_j = max(s of the run holding j - Delta, s_u - Delta) and
+// hi_j = min(e_u + Delta, e of the run holding j + Delta) (cells clamped to [0, n); s, e a run's
+// first cell and one past its last). So Theorem 5 is sum_j P(e_j) sum_{k in [lo_j, hi_j)} g(k - j)
+// C_k, taken here with the taps |k - j| <= K of the banded convolution, in increasing k. RI holds
+// each cell's run index, S the run starts (S[nr] = n).
+__device__ __forceinline__ float window_conv(const float *CP, const float *CC, const float *gtab, int K, int n,
+                                             const int *S, const int *RI, int D)
+{
+    float v = 0.0f;
+    for (int j = lane_id(); j < n; j += 32) {
+        const int u = RI[j];
+        const int a = max(j - D, 0), b = min(j + D, n - 1);
+        const int lo = max(S[RI[a]], S[u] - D), hi = min(S[u + 1] + D, S[RI[b] + 1]);
+        const int d0 = max(lo - j, -K), d1 = min(hi - j, K + 1);
+        float acc = 0.0f;
+        for (int d = d0; d < d1; ++d) acc = fmaf(gtab[K + d], CC[K + j + d], acc);
+        v = fmaf(CP[j], acc, v);
+    }
+    return v;
+}
+
+// window_conv with a compile-time radius KK: the 2 KK + 1 kernel values in registers and every tap
+// predicated on the window, so that no lane waits for another's longer window; the same products
+// added in the same order (bit-identical).
+template <int KK>
+__device__ __forceinline__ float window_conv_k(const float *CP, const float *CC, const float *gtab, int n, const int *S,
+                                               const int *RI, int D)
+{
+    float g[2 * KK + 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * KK; ++d) g[d] = gtab[d];
+    float v = 0.0f;
+    for (int j = lane_id(); j < n; j += 32) {
+        const int u = RI[j];
+        const int a = max(j - D, 0), b = min(j + D, n - 1);
+        const int lo = max(S[RI[a]], S[u] - D), hi = min(S[u + 1] + D, S[RI[b] + 1]);
+        const int d0 = lo - j + KK, w = hi - lo;  // taps d0 .. d0 + w - 1 of 0 .. 2 KK
+        float acc = 0.0f;
+#pragma unroll
+        for (int d = 0; d <= 2 * KK; ++d)
+            if ((unsigned)(d - d0) < (unsigned)w) acc = fmaf(g[d], CC[j + d], acc);
+        v = fmaf(CP[j], acc, v);
+    }
+    return v;
+}
+
 // Cell-level evaluation (eq. eqn_from_fsmi) of one ray: decompress the runs into the n virtual
 // cells, form P(e_j) and C_k by warp scans (Algorithms 2 and 3), then
 // I = sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d} (FSMI-RLE, Uniform-FSMI-RLE, strict-band
-// Approx-FSMI-RLE; Theorem 5's sub-blocks stay on the run-pair path, which is O(n_r Delta)).
-// Arrays: 0 run o, 1 run f_occ, 2 run f_emp, 3 P, 4 run starts S, 5 f_emp per cell,
-// 6 C padded by K zeros on both sides.
-static __device__ float ray_mi_cells(float *base, int stride, int nr, int n, const DevParams &p, const float *gtab, int K)
+// Approx-FSMI-RLE), or for Theorem 5 the same sum over each first-hit cell's window of kept pairs
+// (window_conv). Arrays: 0 run o, 1 run f_occ (then, for Theorem 5, each cell's run index), 2 run
+// f_emp, 3 P, 4 run starts S, 5 f_emp per cell, 6 C padded by K zeros on both sides.
+static __device__ float ray_mi_cells(float *base, int stride, int nr, int n, const DevParams &p, const float *gtab, int K,
+                                     bool thm5)
 {
     const int lane = lane_id();
     float *O = base, *RFO = base + stride, *RFE = base + 2 * stride, *CP = base + 3 * stride;
@@ -330,6 +380,12 @@ static __device__ float ray_mi_cells(float *base, int stride, int nr, int n, con
     }
     __syncwarp();
     cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
+    if (thm5) {
+        int *RI = (int *)RFO;  // the run gains are spread to the cells by now
+        for (int i = lane; i < n; i += 32) RI[i] = run_of(S, nr, i);
+        __syncwarp();
+        return window_conv(CP, CC, gtab, K, n, S, RI, p.trunc);
+    }
     return band_conv<false>(CP, CC, gtab, K, n);
 }
 
@@ -342,8 +398,8 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
     const int n = r.S[nr];
     const bool thm5 = p.variant == FSMI_APPROX && p.approx_reading == 0;
     float v;
-    if (!thm5 && n < p.cell_runlen * nr) {
-        v = ray_mi_cells(base, stride, nr, n, p, gtab, K);
+    if (n < p.cell_runlen * nr) {
+        v = ray_mi_cells(base, stride, nr, n, p, gtab, K, thm5);
     } else {
         run_prefixes(r, nr, p);
         if (p.variant == FSMI_APPROX && p.approx_reading == 0)
@@ -474,9 +530,13 @@ __host__ __device__ inline int ray3d_nrcap(const DevParams &p)
     return thm5_of(p) ? p.nmax : min(p.nmax, p.nmax / T + 2);
 }
 __host__ __device__ inline int ray3d_run_stride(const DevParams &p) { return ((ray3d_nrcap(p) + 2) + 3) & ~3; }
+// Per-warp floats of the fused 3D path. The others: [CP | CF | CC | six run arrays]. Theorem 5 (all
+// runs stored): [S | O | four cell-stride arrays], the four holding CP, CF, CC and the cells' run
+// indices for the cell form, or the run arrays X, A, F, L for the run pairs.
 __host__ __device__ inline int ray3d_warp_floats(const DevParams &p)
 {
-    return (thm5_of(p) ? 0 : 3 * ray3d_cell_stride(p)) + 6 * ray3d_run_stride(p);
+    return thm5_of(p) ? 2 * ray3d_run_stride(p) + 4 * ray3d_cell_stride(p)
+                      : 3 * ray3d_cell_stride(p) + 6 * ray3d_run_stride(p);
 }
 
 // Which evaluation paths a fused-ray kernel is compiled with: both (the variant read at run time),
@@ -531,24 +591,53 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
 {
     const int lane = lane_id();
     const bool thm5 = MODE == kRay3dAny ? thm5_of(p) : MODE == kRay3dThm5;
-    const int cst = ray3d_cell_stride(p);
-    float *CP = thm5 ? nullptr : w, *CF = w + cst, *CC = w + 2 * cst;
-    const RunSmem r = run_smem(w + (thm5 ? 0 : 3 * cst), ray3d_run_stride(p));
+    const int cst = ray3d_cell_stride(p), rst = ray3d_run_stride(p);
+    float *CP, *CF, *CC;
+    int *RI = nullptr;
+    RunSmem r;
+    if (thm5) {
+        float *c4 = w + 2 * rst;
+        CP = c4;
+        CF = c4 + cst;
+        CC = c4 + 2 * cst;
+        RI = (int *)(c4 + 3 * cst);
+        r.S = (int *)w;
+        r.O = w + rst;
+        r.X = CP;
+        r.A = CF;
+        r.F = CC;
+        r.L = RI;
+    } else {
+        CP = w;
+        CF = w + cst;
+        CC = w + 2 * cst;
+        r = run_smem(w + 3 * cst, rst);
+    }
     int n = 0, nspan = 0;
     const int nr = sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, p.run_cap, r.O, r.S, ray3d_nrcap(p), &n, CP, CF,
                                      &nspan);
     *nr_out = nr;
     if (nr <= 0) return 0.0f;
     float v;
-    if (!thm5 && n < p.cell_runlen * nr) {
+    if (n < p.cell_runlen * nr) {
         // eq. eqn_from_fsmi on the virtual cells: Algorithms 2 and 3, then the banded convolution
-        for (int i = lane; i < K; i += 32) {
-            CC[i] = 0.0f;
-            CC[K + n + i] = 0.0f;
+        // (Theorem 5: over each first-hit cell's window of kept pairs)
+        if (!thm5) {
+            for (int i = lane; i < K; i += 32) {
+                CC[i] = 0.0f;
+                CC[K + n + i] = 0.0f;
+            }
         }
         span_gains(p, CP, CC + K, CF, n, nspan);
         cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
-        v = band_conv<MODE == kRay3dOther>(CP, CC, gtab, K, n);
+        if (thm5) {
+            for (int i = lane; i < n; i += 32) RI[i] = run_of(r.S, nr, i);
+            __syncwarp();
+            v = MODE == kRay3dThm5 && K == 15 ? window_conv_k<15>(CP, CC, gtab, n, r.S, RI, p.trunc)
+                                               : window_conv(CP, CC, gtab, K, n, r.S, RI, p.trunc);
+        } else {
+            v = band_conv<MODE == kRay3dOther>(CP, CC, gtab, K, n);
+        }
     } else {  // here n_r <= nrcap, so every run was stored
         run_starts(r, nr, true);
         run_prefixes(r, nr, p);
