@@ -58,8 +58,8 @@ KERNEL_SOURCES = ["paper_1905_02238_gb300/csrc/fsmi_2d.cu", "paper_1905_02238_gb
 # ncu capture each (valid for the sources hashed with them, like TRAFFIC)
 KERNEL_SOURCES_3D = ["paper_1905_02238_gb300/csrc/fsmi_rle.cu", "paper_1905_02238_gb300/csrc/evalrle.cuh",
                      "paper_1905_02238_gb300/csrc/fsmi_device.cuh"]
-TRAFFIC_3D = {"sources_sha1": "449b02747e9bd8acb6093a6d23ab8b7e7ffaaf96", "fsmi_rle_3d": 565.05e6, "approx_fsmi_rle_3d_delta6": 569.85e6,
-              "approx_fsmi_rle_3d_delta6_band": 564.18e6, "uniform_fsmi_rle_3d_h4": 564.30e6}
+TRAFFIC_3D = {"sources_sha1": "8140517dbdd4473d1c65def9bad5f71ddea9e91f", "fsmi_rle_3d": 563.77e6, "approx_fsmi_rle_3d_delta6": 566.51e6,
+              "approx_fsmi_rle_3d_delta6_band": 563.41e6, "uniform_fsmi_rle_3d_h4": 563.24e6}
 
 
 def kernel_sources_sha1(files=None) -> str:
