@@ -419,11 +419,11 @@ __device__ __forceinline__ float ray_mi(float *base, int stride, int nr, const D
 //
 // Fused form (CP != nullptr): also writes every virtual cell's o (CP) and, in SP[k], the value of
 // the k-th span of equal values (k counted over the ray; *nspan_out receives their number), from
-// which span_gains fills in the cells' gains. Runs past nrcap are counted but not stored; *n_out
-// receives n.
+// which span_gains fills in the cells' gains; with RI, every cell's run index. Runs past nrcap are
+// counted but not stored; *n_out receives n.
 static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, int Y, int Z, const int32_t *pose,
                                         const int32_t *u, int nsamp, int cap, float *O, int *S, int nrcap, int *n_out,
-                                        float *CP, float *SP, int *nspan_out)
+                                        float *CP, float *SP, int *nspan_out, int *RI = nullptr)
 {
     const int lane = lane_id();
     int nspan = 0;
@@ -491,6 +491,7 @@ static __device__ int sample_encode_ray(const float *__restrict__ vox, int X, in
                 S[k] = i;
             }
         }
+        if (RI && valid) RI[i] = nrun + __popc(mb & lane_le) - 1;  // the run this cell belongs to
         if (CP) {
             if (valid) CP[i] = val;
             if (newval) SP[nspan + __popc(nle) - 1] = val;  // span index <= cell index
@@ -615,7 +616,7 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
     }
     int n = 0, nspan = 0;
     const int nr = sample_encode_ray(vox, X, Y, Z, pose, u, nsamp, p.run_cap, r.O, r.S, ray3d_nrcap(p), &n, CP, CF,
-                                     &nspan);
+                                     &nspan, RI);
     *nr_out = nr;
     if (nr <= 0) return 0.0f;
     float v;
@@ -630,9 +631,7 @@ __device__ __forceinline__ float ray_mi_fused(const float *vox, int X, int Y, in
         }
         span_gains(p, CP, CC + K, CF, n, nspan);
         cell_prefixes(CP, CC + K, CF, n, false);  // CP = P(e_j), CC[K + k] = C_k, CC[K + n] = 0
-        if (thm5) {
-            for (int i = lane; i < n; i += 32) RI[i] = run_of(r.S, nr, i);
-            __syncwarp();
+        if (thm5) {  // RI was filled while sampling
             v = MODE == kRay3dThm5 && K == 15 ? window_conv_k<15>(CP, CC, gtab, n, r.S, RI, p.trunc)
                                                : window_conv(CP, CC, gtab, K, n, r.S, RI, p.trunc);
         } else {

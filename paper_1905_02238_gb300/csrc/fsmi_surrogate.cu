@@ -423,30 +423,6 @@ struct WRow {  // B(k, n) = W[k][n] (BF16 row-major [K][ld])
     int ld;
     __device__ float operator()(int k, int n) const { return bf(w, (long long)k * ld + n); }
 };
-// conv data gradient: da[n][s][ci] = sum_{k, c} dz[n][t][c] W[c][k][ci], t = (s + 1 - k) / 2
-struct DzGather {  // A(m = n * Lin + s, kk = k * 32 + c)
-    const float *dz;
-    int Lin;
-    __device__ float operator()(int m, int kk) const
-    {
-        const int Lout = Lin >> 1;
-        const int n = m / Lin, s = m % Lin, k = kk / kCh, c = kk % kCh;
-        const int u = s + 1 - k;
-        if (u < 0 || (u & 1)) return 0.0f;
-        const int t = u >> 1;
-        if (t >= Lout) return 0.0f;
-        return dz[((long long)n * Lout + t) * kCh + c];
-    }
-};
-struct WConvT {  // B(kk = k * 32 + c, ci) = W[c][k][ci]
-    const bf16 *w;
-    __device__ float operator()(int kk, int ci) const
-    {
-        const int k = kk / kCh, c = kk % kCh;
-        return bf(w, ((long long)c * kK + k) * kCh + ci);
-    }
-};
-
 struct SumDz {  // f(r, c) = dz[r][c]
     const float *dz;
     int ld;
@@ -660,6 +636,98 @@ cudaError_t gemm_tc(int M, int N, int K, FA fa, FB fb, FE fe, float *part, size_
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
     k_split_reduce<<<grid_cap(((long long)M * N + 255) / 256), 256, 0, s>>>(M, N, splits, part, fe);
+    return cudaGetLastError();
+}
+
+// Data gradient of a stride-2 conv layer (32 -> 32 channels) into the layer below, masked by its
+// ReLU: da[n][s][ci] = [z_prev[n][s][ci] > 0] sum over the taps k and positions t with
+// 2t + k - 1 = s of sum_c dz[n][t][c] W[c][k][ci]. An even s = 2u takes tap 1 at t = u, an odd
+// s = 2u + 1 taps 0 at t = u + 1 and 2 at t = u (the other taps fall between positions), so a
+// warp that takes the 16 positions t = u0 .. u0 + 15 of one beam (32 output positions) stages the
+// dz rows u0 .. u0 + 16 (two BF16 terms each, as k_gemm_tc's backward products; row u0 + 16 is
+// zero past the beam) and runs the even rows as a K = 32 product with tap 1 and the odd rows as a
+// K = 64 product with taps 0 and 2: half the products of the K = 96 im2col form, whose other half
+// are zeros. Weights are staged as [k][ci][c] BF16 (exact), row pitch kTrPitch.
+__global__ void __launch_bounds__(256) k_dgrad_conv(int N, int Lin, const float *__restrict__ dz,
+                                                    const bf16 *__restrict__ w, const float *__restrict__ zprev,
+                                                    float *__restrict__ out)
+{
+    __shared__ __align__(16) bf16 sW[kK * kCh * kTrPitch];
+    __shared__ __align__(16) bf16 sT[8][2][17 * kTrPitch];
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, g = lane >> 2, tq = lane & 3;
+    for (int e = tid; e < kK * kCh * kCh; e += 256) {
+        const int k = e / (kCh * kCh), ci = (e / kCh) % kCh, c = e % kCh;
+        sW[(k * kCh + ci) * kTrPitch + c] = w[(c * kK + k) * kCh + ci];
+    }
+    __syncthreads();
+    const int Lout = Lin >> 1, tpb = Lout / 16;
+    const long long ntiles = (long long)N * tpb;
+    bf16 *const T[2] = {sT[wp][0], sT[wp][1]};
+    for (long long tile = blockIdx.x * 8LL + wp; tile < ntiles; tile += gridDim.x * 8LL) {
+        const int n = (int)(tile / tpb), u0 = (int)(tile % tpb) * 16;
+        for (int e = lane; e < 17 * (kCh / 2); e += 32) {
+            const int r = e / (kCh / 2), cp = e % (kCh / 2);
+            float2 v = make_float2(0.0f, 0.0f);
+            if (u0 + r < Lout) v = *reinterpret_cast<const float2 *>(dz + ((long long)n * Lout + u0 + r) * kCh + 2 * cp);
+            split_store(T, 2, r * kTrPitch + 2 * cp, v.x, v.y);
+        }
+        __syncwarp();
+        float ev[4][4] = {}, od[4][4] = {};
+#pragma unroll
+        for (int ks = 0; ks < kCh; ks += 16) {
+            unsigned a[2][4], a1[2][4];  // rows u0 + g, + 8 (a) and u0 + g + 1, + 9 (a1)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const bf16 *p = T[i] + g * kTrPitch + ks + 2 * tq;
+                a[i][0] = lds32(p);
+                a[i][1] = lds32(p + 8 * kTrPitch);
+                a[i][2] = lds32(p + 8);
+                a[i][3] = lds32(p + 8 * kTrPitch + 8);
+                a1[i][0] = lds32(p + kTrPitch);
+                a1[i][1] = lds32(p + 9 * kTrPitch);
+                a1[i][2] = lds32(p + kTrPitch + 8);
+                a1[i][3] = lds32(p + 9 * kTrPitch + 8);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                unsigned b[3][2];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const bf16 *q = sW + (k * kCh + nt * 8 + g) * kTrPitch + ks + 2 * tq;
+                    b[k][0] = lds32(q);
+                    b[k][1] = lds32(q + 8);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    mma_bf16(ev[nt], a[i][0], a[i][1], a[i][2], a[i][3], b[1][0], b[1][1]);
+                    mma_bf16(od[nt], a1[i][0], a1[i][1], a1[i][2], a1[i][3], b[0][0], b[0][1]);
+                    mma_bf16(od[nt], a[i][0], a[i][1], a[i][2], a[i][3], b[2][0], b[2][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int ci = nt * 8 + 2 * tq;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // fragment rows g, g + 8
+                const int u = u0 + g + 8 * h;
+#pragma unroll
+                for (int odd = 0; odd < 2; ++odd) {
+                    const long long i = ((long long)n * Lin + 2 * u + odd) * kCh + ci;
+                    const float2 m = *reinterpret_cast<const float2 *>(zprev + i);
+                    const float v0 = odd ? od[nt][2 * h] : ev[nt][2 * h], v1 = odd ? od[nt][2 * h + 1] : ev[nt][2 * h + 1];
+                    *reinterpret_cast<float2 *>(out + i) = make_float2(m.x > 0.0f ? v0 : 0.0f, m.y > 0.0f ? v1 : 0.0f);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t dgrad_conv(int N, int Lin, const float *dz, const bf16 *w, const float *zprev, float *out, cudaStream_t s)
+{
+    const long long tiles = (long long)N * (Lin / 32);  // 16 output positions t per warp, 8 warps per block
+    k_dgrad_conv<<<grid_cap((tiles + 7) / 8), 256, 0, s>>>(N, Lin, dz, w, zprev, out);
     return cudaGetLastError();
 }
 
@@ -1243,16 +1311,12 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     FSMI_TRY(wgrad<kCh>(N * 32, 64, dz3, t.z2, nullptr, grad + oW3, t.part, s));
     FSMI_TRY(colsum(N * 32, kCh, SumDz{dz3, kCh}, grad + oB3, t.part, s));
     float *dz2 = t.g1;  // [N][64][32]
-    FSMI_TRY(gemm_tc<32, 2, false, true, false>(N * 64, kCh, kK * kCh, DzGather{dz3, 64}, WConvT{w + oW3},
-                                             StoreMask{dz2, t.z2, kCh}, t.part,
-                  t.part_floats, s));
+    FSMI_TRY(dgrad_conv(N, 64, dz3, w + oW3, t.z2, dz2, s));
     // conv2
     FSMI_TRY(wgrad<kCh>(N * 64, 128, dz2, t.z1, nullptr, grad + oW2, t.part, s));
     FSMI_TRY(colsum(N * 64, kCh, SumDz{dz2, kCh}, grad + oB2, t.part, s));
     float *dz1 = t.g2;  // [N][128][32]
-    FSMI_TRY(gemm_tc<32, 2, false, true, false>(N * 128, kCh, kK * kCh, DzGather{dz2, 128}, WConvT{w + oW2},
-                                             StoreMask{dz1, t.z1, kCh}, t.part,
-                  t.part_floats, s));
+    FSMI_TRY(dgrad_conv(N, 128, dz2, w + oW2, t.z1, dz1, s));
     // conv1
     FSMI_TRY(wgrad<kCin>(N * 128, kL, dz1, nullptr, xb, grad + oW1, t.part, s));
     FSMI_TRY(colsum(N * 128, kCh, SumDz{dz1, kCh}, grad + oB1, t.part, s));
