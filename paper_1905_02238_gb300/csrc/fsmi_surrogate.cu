@@ -11,10 +11,13 @@
 //   conv:  z[t][c] = b[c] + sum_{k<3} sum_ci W[c][k][ci] a[2t + k - 1][ci]
 //
 // Parameters are one flat FP32 vector (master copy, layout below); the weights are used as a BF16
-// copy of the same vector, accumulation is FP32. Training runs every layer, forward and backward,
-// through one split-K SIMT GEMM whose operands are read through index functions (convolutions
-// gather their im2col entries on the fly); every sum is taken in a fixed order, so a training
-// step gives the same floats on every run.
+// copy of the same vector, accumulation is FP32. Training keeps FP32 activations: the layers'
+// products run on the tensor cores with each FP32 operand split into BF16 terms (k_gemm_tc, whose
+// operands are read through index functions, convolutions gathering their im2col entries on the
+// fly; k_dgrad_conv for the convolutions' data gradients), the weight and bias gradients of the
+// convolutions as two-pass reductions over the batch rows (k_wgrad_part, k_colsum_part,
+// k_part_final); every sum is taken in a fixed order, so a training step gives the same floats
+// on every run.
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched through the runtime, no -lcuda)
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -1275,17 +1278,13 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     } while (0)
     // forward
     FSMI_TRY(gemm_tc<32, 3, false, true, true>(N * 128, kCh, kK * kCin, ConvA1{xb}, WConv{w + oW1, kCin},
-                                            StoreBias{t.z1, params + oB1, kCh},
-                  t.part, t.part_floats, s));
+                                            StoreBias{t.z1, params + oB1, kCh}, t.part, t.part_floats, s));
     FSMI_TRY(gemm_tc<32, 3, false, true, true>(N * 64, kCh, kK * kCh, ConvA{t.z1, 128}, WConv{w + oW2, kCh},
-                                            StoreBias{t.z2, params + oB2, kCh},
-                  t.part, t.part_floats, s));
+                                            StoreBias{t.z2, params + oB2, kCh}, t.part, t.part_floats, s));
     FSMI_TRY(gemm_tc<32, 3, false, true, true>(N * 32, kCh, kK * kCh, ConvA{t.z2, 64}, WConv{w + oW3, kCh},
-                                            StoreBias{t.z3, params + oB3, kCh},
-                  t.part, t.part_floats, s));
+                                            StoreBias{t.z3, params + oB3, kCh}, t.part, t.part_floats, s));
     FSMI_TRY(gemm_tc<64, 3, false, true, true>(N, kHid, kFlat, ReluRow{t.z3, kFlat}, WT{w + oW4, kFlat},
-                                            StoreBias{t.z4, params + oB4, kHid},
-                  t.part, t.part_floats, s));
+                                            StoreBias{t.z4, params + oB4, kHid}, t.part, t.part_floats, s));
     float *pred = pred_out ? pred_out : t.pred;
     k_head<<<grid_cap((N + 7) / 8), 256, 0, s>>>(t.z4, w, params, y, N, pred, t.dpred, t.lossp);
     FSMI_TRY(cudaGetLastError());
@@ -1301,12 +1300,10 @@ cudaError_t launch_surrogate_loss_grad(const float *params, const void *wbf16, c
     FSMI_TRY(colsum(N, kHid, SumDz{dz4, kHid}, grad + oB4, t.part, s));
     // fc1: gW4[j][i] = sum_n dz4[n][j] relu(z3)[n][i]; dz3 = (dz4 W4) [z3 > 0]
     FSMI_TRY(gemm_tc<64, 2, true, false, false>(kHid, kFlat, N, RowT{dz4, kHid}, ReluRow{t.z3, kFlat},
-                                             Store{grad + oW4, kFlat}, t.part,
-                  t.part_floats, s));
+                                             Store{grad + oW4, kFlat}, t.part, t.part_floats, s));
     float *dz3 = t.g2;  // [N][32][32]
     FSMI_TRY(gemm_tc<64, 2, false, true, false>(N, kFlat, kHid, RowN{dz4, kHid}, WRow{w + oW4, kFlat},
-                                             StoreMask{dz3, t.z3, kFlat}, t.part,
-                  t.part_floats, s));
+                                             StoreMask{dz3, t.z3, kFlat}, t.part, t.part_floats, s));
     // conv3: weights from relu(z2); data gradient into dz2 = (...) [z2 > 0]
     FSMI_TRY(wgrad<kCh>(N * 32, 64, dz3, t.z2, nullptr, grad + oW3, t.part, s));
     FSMI_TRY(colsum(N * 32, kCh, SumDz{dz3, kCh}, grad + oB3, t.part, s));
