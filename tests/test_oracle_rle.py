@@ -174,6 +174,35 @@ def test_theorem5_sub_blocks_keep_all_band_pairs(orc):
         assert got == pytest.approx(ref, rel=1e-12)
 
 
+def test_theorem5_equals_contiguous_cell_windows(orc):
+    # The form the CUDA path evaluates: for a first-hit cell j of run u, Theorem 5 keeps exactly the
+    # cells [lo_j, hi_j) with lo_j = max(s of the run holding j - Delta, s_u - Delta) and
+    # hi_j = min(e_u + Delta, e of the run holding j + Delta) (clamped to the ray; e one past a
+    # run's last cell). Checked against the oracle's Theorem 5 (pinned above to its sub-block mask)
+    # on random runs, Delta from 0 up to past the ray's length.
+    rng = np.random.default_rng(31)
+    sigma = 1.5
+    for _ in range(40):
+        nr = int(rng.integers(1, 9))
+        ro = rng.uniform(0.02, 0.98, nr).astype(np.float32)
+        rl = rng.integers(1, 12, nr)
+        D = int(rng.integers(0, 14))
+        s = np.concatenate([[0], np.cumsum(rl)])
+        run_of = np.repeat(np.arange(nr), rl)
+        n = int(s[-1])
+        pe, C = _pe_c(orc, _cells(ro, rl))
+        ref = 0.0
+        for j in range(n):
+            u = run_of[j]
+            lo = max(s[run_of[max(j - D, 0)]], s[u] - D)
+            hi = min(s[u + 1] + D, s[run_of[min(j + D, n - 1)] + 1])
+            k = np.arange(lo, hi)
+            g = np.exp(-(k - j) ** 2 / (2 * sigma * sigma)) / (math.sqrt(2 * math.pi) * sigma)
+            ref += pe[j] * float(g @ C[lo:hi])
+        got = orc.rle_beam(ro, rl, orc.Params(variant=orc.APPROX, sigma=sigma, trunc_delta=D, approx_reading=0))
+        assert got == pytest.approx(ref, rel=1e-12)
+
+
 # ---- A and B (Theorem 3) ---------------------------------------------------------------------------
 
 def _alpha(x, Lu, Lv, sigma, weight_k=False):
