@@ -265,9 +265,9 @@ __device__ __forceinline__ int run_of(const int *S, int nr, int i)
 // sum_j P(e_j) sum_{|d| <= K} g(d) C_{j+d} over j in this lane's cells (P in CP, C at CC[K + k],
 // zero-padded by K on both sides), the taps added in increasing d. A compile-time radius KK keeps
 // the 2 KK + 1 kernel values in registers for the whole ray (one shared load per tap instead of
-// two); both forms add the same products in the same order. Only kernels without Theorem 5's
-// run-pair path take the register form (FIXED): in a kernel that has both, the extra registers
-// slow the run pairs down.
+// two); both forms add the same products in the same order. Only the kernels of the other
+// variants take this register form (FIXED); the Theorem 5 kernel, whose rays mostly take its
+// windowed cell form, keeps the taps in registers in window_conv_k instead.
 template <int KK>
 __device__ __forceinline__ float band_conv_k(const float *CP, const float *CC, const float *gtab, int n)
 {
